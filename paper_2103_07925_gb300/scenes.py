@@ -1,0 +1,471 @@
+"""Seeded synthetic scene generators.
+
+This module builds the *inputs* of a simulation: lattice sites, particle
+masses assigned from a reference density and the lattice volume (the initial
+discretisation of Sec. 3.1.2), materials, wall shells and rigid-body
+membership.  It holds none of the SPH arithmetic (no kernel, no sums, no
+integration) and imports nothing else from this package, so that both the
+CUDA path and the FP64 CPU checker can be fed from it.
+
+A scene is a plain ``dict``::
+
+    {"params": {...}, "materials": [ {...}, ... ],
+     "particles": {"pos": (n,3) f64, "vel": (n,3), "mass": (n,), "density": (n,),
+                   "temperature": (n,), "material": (n,) i32, "body": (n,) i32,
+                   "wall_velocity": (n,3), "wall_temperature": (n,)},
+     "bodies": {"quat": (k,4), "vel": (k,3), "omega": (k,3)}}
+
+Positions are always stored with three components (z = 0 in 2D).
+Lattice sites sit at ``lo + (i + 1/2) dx`` (Sec. 3.1.2, Sec. 3.3.4 for the
+wall layers at distance dx/2 outside the fluid).
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+FLUID, RIGID, WALL = 0, 1, 2
+NAN = float("nan")
+
+
+def material(kind, rho0, c=0.0, eta=0.0, cp=1.0, kappa=0.0,
+             T_transition=NAN, transitions_to=-1, latent_heat=0.0, mushy_width=0.0):
+    """One material (phase) record; ``eta`` is the dynamic viscosity rho0*nu."""
+    return dict(kind=int(kind), rho0=float(rho0), c=float(c), eta=float(eta), cp=float(cp),
+                kappa=float(kappa), T_transition=float(T_transition),
+                transitions_to=int(transitions_to), latent_heat=float(latent_heat),
+                mushy_width=float(mushy_width))
+
+
+def default_params(dim, dx, box_min, box_max, **kw):
+    p = dict(dim=int(dim), dx=float(dx), h=float(dx), kernel_support=3.0,
+             box_min=[float(v) for v in box_min] + [0.0] * (3 - len(box_min)),
+             box_max=[float(v) for v in box_max] + [0.0] * (3 - len(box_max)),
+             periodic=[0, 0, 0], gravity=[0.0, 0.0, 0.0],
+             dt_mode=0, dt_fixed=1e-4, k_contact=0.0, d_contact=-1.0,
+             precision=64, rebin_interval=1, key_order=0, cells_per_group=0,
+             body_capacity=0,
+             src_power=0.0, src_radius=0.05, src_speed=[0.0, 0.0, 0.0],
+             src_origin=[0.0, 0.0, 0.0], src_depth=0.0, src_ztop=0.0)
+    if dim == 2:
+        p["box_min"][2] = 0.0
+        p["box_max"][2] = 0.0
+    p.update(kw)
+    return p
+
+
+# --------------------------------------------------------------------------- lattices
+
+def lattice(lo, n, dx):
+    """Sites lo + (i+1/2) dx for i in [0, n) per axis; returns (N, len(n)) array."""
+    axes = [lo[d] + (np.arange(n[d]) + 0.5) * dx for d in range(len(n))]
+    grids = np.meshgrid(*axes, indexing="ij")
+    return np.stack([g.ravel(order="F") for g in grids], axis=1)
+
+
+def _pad3(p):
+    if p.shape[1] == 3:
+        return p
+    out = np.zeros((p.shape[0], 3))
+    out[:, : p.shape[1]] = p
+    return out
+
+
+def wall_shell(dim, n_in, dx, layers=3, open_top=False, top_extra=0):
+    """Boundary particles in ``layers`` rows around the interior box of n_in sites.
+
+    The interior occupies [0, n_in*dx) per axis.  With ``open_top`` the shell has no
+    top layer on the last axis, and the side walls extend ``top_extra`` sites above
+    the interior.
+    """
+    lo_i = [-layers] * dim
+    hi_i = [n_in[d] + layers for d in range(dim)]
+    if open_top:
+        hi_i[-1] = n_in[-1] + top_extra
+    idx = [np.arange(lo_i[d], hi_i[d]) for d in range(dim)]
+    grids = np.meshgrid(*idx, indexing="ij")
+    ijk = np.stack([g.ravel(order="F") for g in grids], axis=1)
+    inside = np.ones(len(ijk), dtype=bool)
+    for d in range(dim):
+        hi_lim = n_in[d] if not (open_top and d == dim - 1) else hi_i[d]
+        inside &= (ijk[:, d] >= 0) & (ijk[:, d] < hi_lim)
+    ijk = ijk[~inside]
+    return (ijk + 0.5) * dx
+
+
+# --------------------------------------------------------------------------- assembly
+
+class _Builder:
+    def __init__(self, dim):
+        self.dim = dim
+        self.parts = []  # list of dict chunks
+        self.bodies = []
+
+    def add(self, pos, mat, mass, density, T, body=-1, vel=None, wall_T=NAN, wall_vel=None):
+        pos = np.asarray(pos, dtype=np.float64)
+        if pos.ndim == 1:
+            pos = pos.reshape(1, -1)
+        pos = _pad3(pos)
+        n = len(pos)
+        ch = dict(pos=pos,
+                  vel=np.zeros((n, 3)) if vel is None else np.broadcast_to(np.asarray(vel, float), (n, 3)).copy(),
+                  mass=np.full(n, float(mass)) if np.isscalar(mass) else np.asarray(mass, float),
+                  density=np.full(n, float(density)) if np.isscalar(density) else np.asarray(density, float),
+                  temperature=np.full(n, float(T)) if np.isscalar(T) else np.asarray(T, float),
+                  material=np.full(n, int(mat), dtype=np.int32),
+                  body=np.full(n, int(body), dtype=np.int32) if np.isscalar(body) else np.asarray(body, np.int32),
+                  wall_velocity=np.zeros((n, 3)) if wall_vel is None else np.broadcast_to(np.asarray(wall_vel, float), (n, 3)).copy(),
+                  wall_temperature=np.full(n, float(wall_T)) if np.isscalar(wall_T) else np.asarray(wall_T, float))
+        self.parts.append(ch)
+        return n
+
+    def add_body(self, vel=(0, 0, 0), omega=(0, 0, 0), quat=(1, 0, 0, 0)):
+        self.bodies.append((list(quat), list(vel), list(omega)))
+        return len(self.bodies) - 1
+
+    def finish(self, params, materials):
+        keys = ["pos", "vel", "mass", "density", "temperature", "material", "body",
+                "wall_velocity", "wall_temperature"]
+        parts = {k: np.concatenate([c[k] for c in self.parts], axis=0) for k in keys}
+        parts["material"] = parts["material"].astype(np.int32)
+        parts["body"] = parts["body"].astype(np.int32)
+        k = len(self.bodies)
+        bodies = dict(quat=np.array([b[0] for b in self.bodies], float).reshape(k, 4),
+                      vel=np.array([b[1] for b in self.bodies], float).reshape(k, 3),
+                      omega=np.array([b[2] for b in self.bodies], float).reshape(k, 3))
+        return dict(params=params, materials=materials, particles=parts, bodies=bodies)
+
+
+def _jitter(rng, pos, amp, dim):
+    if amp <= 0:
+        return pos
+    j = np.zeros_like(pos)
+    j[:, :dim] = rng.uniform(-amp, amp, size=(len(pos), dim))
+    return pos + j
+
+
+# --------------------------------------------------------------------------- workloads
+
+def tank2d_disc(dx=0.0125, seed=2103, steps_dt=None, jitter=1e-3, fill=0.65,
+                disc_center=(0.5, 0.4), disc_radius=0.1, disc_density=2.0,
+                c=10.0, rho0=1.0, eta=0.01, g=-1.0, precision=64):
+    """2D unit box, fluid to height ``fill``, one rigid disc, 3-layer closed wall shell.
+
+    Default sizes: 3,952 fluid, 208 rigid, 996 wall particles (dx = 0.0125).
+    dt from the CFL-type conditions of Eq. (timestep) (dt_mode = 1).
+    """
+    rng = np.random.default_rng(seed)
+    n = int(round(1.0 / dx))
+    nf = int(round(fill / dx))
+    sites = lattice([0.0, 0.0], [n, nf], dx)
+    dc = np.linalg.norm(sites - np.asarray(disc_center), axis=1)
+    in_disc = dc <= disc_radius
+    b = _Builder(2)
+    mats = [material(FLUID, rho0, c=c, eta=eta, cp=1.0, kappa=0.0),
+            material(WALL, rho0),
+            material(RIGID, disc_density)]
+    fl = _jitter(rng, _pad3(sites[~in_disc]), jitter * dx, 2)
+    b.add(fl, 0, rho0 * dx * dx, rho0, 300.0)
+    kb = b.add_body()
+    b.add(sites[in_disc], 2, disc_density * dx * dx, disc_density, 300.0, body=kb)
+    w = wall_shell(2, [n, n], dx, layers=3)
+    b.add(w, 1, rho0 * dx * dx, rho0, 300.0)
+    lo = -3 * dx
+    hi = n * dx + 3 * dx
+    p = default_params(2, dx, [lo, lo], [hi, hi], gravity=[0.0, g, 0.0], dt_mode=1,
+                       precision=precision)
+    return b.finish(p, mats)
+
+
+def tank3d_spheres(dx=0.01, n_spheres=64, seed=7925, r_range=(0.04, 0.08),
+                   dens_range=(1.5, 3.0), c=45.0, rho0=1.0, nu=1e-3, g=-9.81,
+                   size=(1.0, 1.0, 2.0), fill=1.0, gap=2.0, jitter=1e-3,
+                   precision=64, dt_mode=1):
+    """3D tank (1 x 1 x 2), fluid to z = 1, ``n_spheres`` rigid spheres, walls open-top.
+
+    At dx = 0.01: 1,000,000 fluid lattice sites minus the spheres, 280,908 wall
+    particles (floor and four sides up to z = 2, three layers).  Sphere radii are
+    uniform in ``r_range``, density ratios uniform in ``dens_range``,
+    centres seeded and non-overlapping with a surface gap of ``gap``*dx.
+    """
+    rng = np.random.default_rng(seed)
+    nx, ny, nz_tank = (int(round(s / dx)) for s in size)
+    nzf = int(round(fill / dx))
+    r_lo, r_hi = r_range
+    centers, radii = [], []
+    tries = 0
+    while len(centers) < n_spheres:
+        tries += 1
+        if tries > 200000:
+            raise RuntimeError("could not place spheres")
+        r = rng.uniform(r_lo, r_hi)
+        m = r + gap * dx
+        cpos = np.array([rng.uniform(m, nx * dx - m), rng.uniform(m, ny * dx - m),
+                         rng.uniform(m, nzf * dx - m)])
+        ok = all(np.linalg.norm(cpos - c2) >= r + r2 + gap * dx for c2, r2 in zip(centers, radii))
+        if ok:
+            centers.append(cpos)
+            radii.append(r)
+    dens = rng.uniform(dens_range[0], dens_range[1], size=n_spheres) * rho0
+    sites = lattice([0.0, 0.0, 0.0], [nx, ny, nzf], dx)
+    owner = np.full(len(sites), -1, dtype=np.int64)
+    for k, (cc, r) in enumerate(zip(centers, radii)):
+        # only test sites in the sphere's bounding box
+        lo = np.maximum(((cc - r) / dx - 1).astype(int), 0)
+        hi = np.minimum(((cc + r) / dx + 1).astype(int), [nx - 1, ny - 1, nzf - 1])
+        ii, jj, kk = np.meshgrid(np.arange(lo[0], hi[0] + 1), np.arange(lo[1], hi[1] + 1),
+                                 np.arange(lo[2], hi[2] + 1), indexing="ij")
+        lin = (ii + nx * (jj + ny * kk)).ravel()
+        d2 = np.sum((sites[lin] - cc) ** 2, axis=1)
+        owner[lin[d2 <= r * r]] = k
+    mats = [material(FLUID, rho0, c=c, eta=rho0 * nu, cp=1.0, kappa=0.0),
+            material(WALL, rho0),
+            material(RIGID, rho0 * 2.0)]
+    b = _Builder(3)
+    fl = _jitter(rng, sites[owner < 0], jitter * dx, 3)
+    b.add(fl, 0, rho0 * dx ** 3, rho0, 300.0)
+    for k in range(n_spheres):
+        kb = b.add_body()
+        s = sites[owner == k]
+        b.add(s, 2, dens[k] * dx ** 3, dens[k], 300.0, body=kb)
+    w = wall_shell(3, [nx, ny, nz_tank], dx, layers=3, open_top=True, top_extra=0)
+    b.add(w, 1, rho0 * dx ** 3, rho0, 300.0)
+    lo = [-3 * dx] * 3
+    hi = [nx * dx + 3 * dx, ny * dx + 3 * dx, nz_tank * dx]
+    p = default_params(3, dx, lo, hi, gravity=[0.0, 0.0, g], dt_mode=dt_mode, precision=precision)
+    return b.finish(p, mats)
+
+
+def periodic_box(dim=3, n=8, dx=0.1, seed=1, vel_amp=0.1, jitter=0.05, c=10.0, rho0=1.0,
+                 eta=0.01, bodies=0, body_radius=None, body_density=2.0, kappa=0.0, cp=1.0,
+                 T_amp=0.0, precision=64):
+    """Fully periodic box of n^dim lattice sites, seeded jitter and random velocities.
+
+    No walls and no gravity: the harness for linear-momentum conservation
+    (Eq. (conservlinmom)).  Optional spherical/disc rigid bodies carved out of the
+    lattice on a regular arrangement.
+    """
+    rng = np.random.default_rng(seed)
+    sites = lattice([0.0] * dim, [n] * dim, dx)
+    L = n * dx
+    owner = np.full(len(sites), -1)
+    centers = []
+    if bodies:
+        rad = body_radius if body_radius is not None else 1.6 * dx
+        per = int(math.ceil(bodies ** (1.0 / dim)))
+        for k in range(bodies):
+            idx = np.unravel_index(k, [per] * dim)
+            cc = np.array([(idx[d] + 0.5) * L / per for d in range(dim)])
+            centers.append(cc)
+            d2 = np.sum((sites - cc) ** 2, axis=1)
+            owner[(d2 <= rad * rad) & (owner < 0)] = k
+    mats = [material(FLUID, rho0, c=c, eta=eta, cp=cp, kappa=kappa),
+            material(RIGID, body_density, cp=cp, kappa=kappa)]
+    b = _Builder(dim)
+    fl = sites[owner < 0]
+    nfl = len(fl)
+    fl = _jitter(rng, _pad3(fl), jitter * dx, dim)
+    vel = np.zeros((nfl, 3))
+    vel[:, :dim] = rng.uniform(-vel_amp, vel_amp, size=(nfl, dim))
+    T = 300.0 + T_amp * rng.uniform(-1, 1, size=nfl)
+    b.add(fl, 0, rho0 * dx ** dim, rho0, T, vel=vel)
+    for k in range(len(centers)):
+        v = np.zeros(3)
+        v[:dim] = rng.uniform(-vel_amp, vel_amp, size=dim)
+        w = np.zeros(3)
+        if dim == 3:
+            w = rng.uniform(-1, 1, size=3)
+        else:
+            w[2] = rng.uniform(-1, 1)
+        kb = b.add_body(vel=v, omega=w)
+        s = sites[owner == k]
+        T = 300.0 + T_amp * rng.uniform(-1, 1, size=len(s))
+        b.add(s, 1, body_density * dx ** dim, body_density, T, body=kb)
+    p = default_params(dim, dx, [0.0] * dim, [L] * dim, periodic=[1] * dim + [0] * (3 - dim),
+                       dt_mode=0, dt_fixed=0.1 * dx / c, precision=precision)
+    if dim == 2:
+        p["periodic"] = [1, 1, 0]
+    return b.finish(p, mats)
+
+
+def cluster(dim=3, n=10, dx=0.1, seed=3, vel_amp=0.05, c=10.0, rho0=1.0, n_bodies=2,
+            body_radius=None, body_density=2.0, precision=64):
+    """Wall-free, non-periodic fluid block with spherical bodies, inviscid (eta = 0).
+
+    All pair forces are central, so total angular momentum is conserved by the
+    pair sums; the harness for the angular-momentum check.  Body centres sit on
+    lattice sites so that each body is symmetric under the cube group and its
+    inertia tensor is isotropic.
+    """
+    rng = np.random.default_rng(seed)
+    sites = lattice([0.0] * dim, [n] * dim, dx)
+    rad = body_radius if body_radius is not None else 1.6 * dx
+    owner = np.full(len(sites), -1)
+    centers = []
+    mid = (n // 2 + 0.5) * dx
+    for k in range(n_bodies):
+        cc = np.full(dim, mid)
+        cc[0] = (int(n * (k + 1) / (n_bodies + 1)) + 0.5) * dx
+        centers.append(cc)
+        d2 = np.sum((sites - cc) ** 2, axis=1)
+        owner[(d2 <= rad * rad) & (owner < 0)] = k
+    mats = [material(FLUID, rho0, c=c, eta=0.0), material(RIGID, body_density)]
+    b = _Builder(dim)
+    fl = sites[owner < 0]
+    vel = np.zeros((len(fl), 3))
+    vel[:, :dim] = rng.uniform(-vel_amp, vel_amp, size=(len(fl), dim))
+    b.add(_pad3(fl), 0, rho0 * dx ** dim, rho0, 300.0, vel=vel)
+    for k in range(n_bodies):
+        w = np.zeros(3)
+        w[2] = rng.uniform(-1, 1)
+        if dim == 3:
+            w = rng.uniform(-1, 1, size=3)
+        v = np.zeros(3)
+        v[:dim] = rng.uniform(-vel_amp, vel_amp, size=dim)
+        kb = b.add_body(vel=v, omega=w)
+        b.add(sites[owner == k], 1, body_density * dx ** dim, body_density, 300.0, body=kb)
+    pad = 4 * dx
+    L = n * dx
+    p = default_params(dim, dx, [-pad] * dim, [L + pad] * dim, dt_mode=0,
+                       dt_fixed=0.05 * dx / c, precision=precision)
+    return b.finish(p, mats)
+
+
+def hydrostatic_tank2d(dx=0.02, width=0.4, depth=0.4, c=10.0, rho0=1.0, eta=0.05, g=-1.0,
+                       closed=False, precision=64):
+    """2D tank at rest under gravity.
+
+    ``closed=False``: fluid of depth ``depth`` below a free surface, tank walls 4 rows
+    higher.  ``closed=True``: the fluid fills a closed box of height ``depth`` (no free
+    surface), walls on all four sides.
+    """
+    nx = int(round(width / dx))
+    nd = int(round(depth / dx))
+    ntank = nd if closed else nd + 4
+    b = _Builder(2)
+    mats = [material(FLUID, rho0, c=c, eta=eta), material(WALL, rho0)]
+    b.add(lattice([0.0, 0.0], [nx, nd], dx), 0, rho0 * dx * dx, rho0, 300.0)
+    b.add(wall_shell(2, [nx, ntank], dx, 3), 1, rho0 * dx * dx, rho0, 300.0)
+    p = default_params(2, dx, [-3 * dx, -3 * dx], [(nx + 3) * dx, (ntank + 3) * dx],
+                       gravity=[0.0, g, 0.0], dt_mode=1, precision=precision)
+    return b.finish(p, mats)
+
+
+def free_fall(dim=3, dx=0.1, radius=0.35, density=3.0, g=-9.81, omega=(0.0, 0.0, 0.0),
+              vel=(0.0, 0.0, 0.0), precision=64, dt=1e-3):
+    """A single rigid sphere (disc) alone in a large box: no fluid, no walls."""
+    n = int(math.ceil(2 * radius / dx)) + 2
+    sites = lattice([-(n * dx) / 2] * dim, [n] * dim, dx)
+    keep = np.sum(sites ** 2, axis=1) <= radius * radius
+    b = _Builder(dim)
+    mats = [material(FLUID, 1.0, c=1.0), material(RIGID, density)]
+    kb = b.add_body(vel=vel, omega=omega)
+    b.add(_pad3(sites[keep]), 1, density * dx ** dim, density, 300.0, body=kb)
+    L = 50.0
+    gv = [0.0, 0.0, 0.0]
+    gv[dim - 1] = g
+    p = default_params(dim, dx, [-L] * dim, [L] * dim, gravity=gv, dt_mode=0, dt_fixed=dt,
+                       precision=precision)
+    return b.finish(p, mats)
+
+
+def heat_slab(dim=2, n=(40, 4), dx=0.025, T0=300.0, A=10.0, kappa=1.0, cp=1.0, rho0=1.0,
+              c=1.0, precision=64, dt=None):
+    """Periodic fluid lattice at rest, T = T0 + A sin(2 pi x / Lx): 1D conduction check."""
+    sites = lattice([0.0] * dim, list(n), dx)
+    Lx = n[0] * dx
+    T = T0 + A * np.sin(2 * np.pi * sites[:, 0] / Lx)
+    b = _Builder(dim)
+    mats = [material(FLUID, rho0, c=c, eta=0.0, cp=cp, kappa=kappa)]
+    b.add(_pad3(sites), 0, rho0 * dx ** dim, rho0, T)
+    L = [n[d] * dx for d in range(dim)]
+    if dt is None:
+        dt = 0.05 * rho0 * cp * dx * dx / kappa
+    p = default_params(dim, dx, [0.0] * dim, L, periodic=[1] * dim + [0] * (3 - dim),
+                       dt_mode=0, dt_fixed=dt, precision=precision)
+    return b.finish(p, mats)
+
+
+def contact_pair(dim=2, dx=0.1, gap=-0.02, speed=0.5, density=2.0, k_contact=1e3,
+                 d_contact=1.0, precision=64, dt=1e-4):
+    """Two single-particle rigid bodies approaching head-on along x (no fluid)."""
+    b = _Builder(dim)
+    mats = [material(FLUID, 1.0, c=1.0), material(RIGID, density)]
+    x0 = -(dx + gap) / 2
+    k0 = b.add_body(vel=(speed, 0, 0))
+    b.add(np.array([[x0, 0.0, 0.0]]), 1, density * dx ** dim, density, 300.0, body=k0)
+    k1 = b.add_body(vel=(-speed, 0, 0))
+    b.add(np.array([[-x0, 0.0, 0.0]]), 1, density * dx ** dim, density, 300.0, body=k1)
+    p = default_params(dim, dx, [-2.0] * dim, [2.0] * dim, dt_mode=0, dt_fixed=dt,
+                       k_contact=k_contact, d_contact=d_contact, precision=precision)
+    return b.finish(p, mats)
+
+
+def random_cloud(dim=3, n=500, L=1.0, dx=0.1, seed=5, kinds=(0.6, 0.25, 0.15), n_bodies=3,
+                 periodic=False, precision=64):
+    """Random (non-lattice) particle cloud of mixed kinds, for brute-force neighbour checks."""
+    rng = np.random.default_rng(seed)
+    pos = np.zeros((n, 3))
+    pos[:, :dim] = rng.uniform(0, L, size=(n, dim))
+    u = rng.uniform(size=n)
+    kind = np.where(u < kinds[0], 0, np.where(u < kinds[0] + kinds[1], 1, 2))
+    mats = [material(FLUID, 1.0, c=5.0, eta=0.01, kappa=0.5, cp=1.0),
+            material(RIGID, 2.0, kappa=1.0, cp=0.5),
+            material(WALL, 1.0)]
+    b = _Builder(dim)
+    vel = np.zeros((n, 3))
+    vel[:, :dim] = rng.uniform(-0.1, 0.1, size=(n, dim))
+    T = 300.0 + 20.0 * rng.uniform(-1, 1, size=n)
+    body = np.full(n, -1, dtype=np.int32)
+    rig = np.nonzero(kind == 1)[0]
+    for k in range(n_bodies):
+        b.add_body(omega=(0, 0, 0.1 * (k + 1)))
+    if len(rig):
+        body[rig] = np.arange(len(rig)) % n_bodies
+    m = dx ** dim
+    mat = np.where(kind == 0, 0, np.where(kind == 1, 1, 2)).astype(np.int32)
+    dens = np.where(kind == 1, 2.0, 1.0)
+    mass = dens * m
+    wall_T = np.where(kind == 2, np.where(rng.uniform(size=n) < 0.5, 310.0, NAN), NAN)
+    # assemble directly (mixed kinds in one chunk, in random order)
+    ch = dict(pos=pos, vel=np.where((kind == 0)[:, None], vel, 0.0), mass=mass, density=dens,
+              temperature=T, material=mat, body=np.where(kind == 1, body, -1).astype(np.int32),
+              wall_velocity=np.zeros((n, 3)), wall_temperature=wall_T)
+    b.parts.append(ch)
+    margin = 0.0 if periodic else 0.05
+    p = default_params(dim, dx, [-margin] * dim, [L + margin] * dim, dt_mode=0, dt_fixed=1e-4,
+                       precision=precision)
+    if periodic:
+        p["periodic"] = [1] * dim + [0] * (3 - dim)
+    return b.finish(p, mats)
+
+
+def strong_scaling_cube(dx=0.2, L=30.0, D=2.5, per_axis=6, rho_s=10.0, rho_f=1.0, c=50.0, nu=1.0,
+                        g=-1.0, precision=64, dt=1e-3):
+    """Sec. 4.6 scene: 6^3 = 216 spheres of diameter D on a regular grid in a cube of edge L,
+    fluid elsewhere, three wall layers; dt = 1e-3 as in the paper."""
+    n = int(round(L / dx))
+    sites = lattice([0.0] * 3, [n] * 3, dx)
+    R = 0.5 * D
+    pitch = L / per_axis
+    owner = np.full(len(sites), -1, dtype=np.int64)
+    # each site belongs to at most one sphere; index the candidate sphere by position
+    idx = np.minimum((sites // pitch).astype(int), per_axis - 1)
+    cc = (idx + 0.5) * pitch
+    inside = np.sum((sites - cc) ** 2, axis=1) <= R * R
+    sid = idx[:, 0] + per_axis * (idx[:, 1] + per_axis * idx[:, 2])
+    owner[inside] = sid[inside]
+    mats = [material(FLUID, rho_f, c=c, eta=rho_f * nu), material(WALL, rho_f),
+            material(RIGID, rho_s)]
+    b = _Builder(3)
+    b.add(sites[owner < 0], 0, rho_f * dx ** 3, rho_f, 300.0)
+    order = np.argsort(owner[owner >= 0], kind="stable")
+    rig = sites[owner >= 0][order]
+    rid = owner[owner >= 0][order]
+    for k in range(per_axis ** 3):
+        b.add_body()
+    b.add(rig, 2, rho_s * dx ** 3, rho_s, 300.0, body=rid.astype(np.int32))
+    b.add(wall_shell(3, [n, n, n], dx, 3), 1, rho_f * dx ** 3, rho_f, 300.0)
+    p = default_params(3, dx, [-3 * dx] * 3, [L + 3 * dx] * 3, gravity=[0.0, 0.0, g],
+                       dt_mode=0, dt_fixed=dt, precision=precision)
+    return b.finish(p, mats)

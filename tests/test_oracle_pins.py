@@ -1,0 +1,502 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints, closed forms, conservation laws of the discrete equations,
+quadrature, brute force on tiny inputs, or special cases with textbook
+solutions.  CPU only.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import oracle as O
+from paper_2103_07925_gb300 import scenes as S
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------- kernel (Sec. 3.1)
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_kernel_normalisation_by_quadrature(dim):
+    """Normalisation property of the kernel remark: integral of W over its support is 1."""
+    h = 0.37
+    area = (lambda r: 2 * math.pi * r) if dim == 2 else (lambda r: 4 * math.pi * r * r)
+    tot = 0.0
+    for a, b in [(0, h), (h, 2 * h), (2 * h, 3 * h)]:  # integrate piecewise between the knots
+        v, _ = integrate.quad(lambda r: O.kernel_w(dim, r, h) * area(r), a, b, epsabs=1e-15, epsrel=1e-13, limit=200)
+        tot += v
+    assert abs(tot - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_kernel_compact_support_positive_monotone_smooth(dim):
+    h = 1.3
+    rc = 3 * h
+    r = np.linspace(0, rc, 3001)
+    w = np.array([O.kernel_w(dim, x, h) for x in r])
+    assert O.kernel_w(dim, rc, h) == 0.0 and O.kernel_w(dim, 1.01 * rc, h) == 0.0
+    assert np.all(w >= 0) and np.all(np.diff(w) <= 0)
+    # the derivative is the derivative of W (central differences), continuous at the knots
+    for x in [0.3 * h, 0.999 * h, h, 1.5 * h, 2 * h, 2.7 * h]:
+        e = 1e-6 * h
+        fd = (O.kernel_w(dim, x + e, h) - O.kernel_w(dim, x - e, h)) / (2 * e)
+        assert abs(O.kernel_dw(dim, x, h) - fd) < 1e-7 * abs(O.kernel_w(dim, 0, h)) / h
+    assert O.kernel_dw(dim, 0.0, h) == 0.0  # smooth maximum at r = 0
+    assert abs(O.kernel_dw(dim, rc, h)) == 0.0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_lattice_partition_of_unity_and_zero_gradient(dim):
+    """Sum_b V_b W_ab on a regular lattice with h = dx is close to 1 and the gradient sum
+    vanishes by symmetry (Sec. 3.1.1, kernel consistency)."""
+    dx = 0.1
+    n = 9
+    g = np.arange(-n, n + 1) * dx
+    pts = np.stack(np.meshgrid(*([g] * dim), indexing="ij"), -1).reshape(-1, dim)
+    r = np.linalg.norm(pts, axis=1)
+    w = np.array([O.kernel_w(dim, x, dx) for x in r])
+    s = dx ** dim * w.sum()
+    assert abs(s - 1.0) < 1e-4
+    dw = np.array([O.kernel_dw(dim, x, dx) for x in r])
+    with np.errstate(invalid="ignore", divide="ignore"):
+        e = np.where(r[:, None] > 0, pts / r[:, None], 0.0)
+    grad = (dw[:, None] * e).sum(0)
+    assert np.all(np.abs(grad) < 1e-9 * np.abs(dw).sum())
+
+
+# ----------------------------------------------------------------------------- neighbours (Sec. 3.2)
+
+def _brute_sets(pos, dim, rc, box_lo=None, box_hi=None, periodic=None):
+    n = len(pos)
+    sets = []
+    for i in range(n):
+        d = pos[i] - pos
+        if periodic is not None:
+            for k in range(dim):
+                if periodic[k]:
+                    L = box_hi[k] - box_lo[k]
+                    d[:, k] = np.where(d[:, k] > 0.5 * L, d[:, k] - L, np.where(d[:, k] < -0.5 * L, d[:, k] + L, d[:, k]))
+        r2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]
+        if dim == 3:
+            r2 = r2 + d[:, 2] * d[:, 2]
+        m = r2 < rc * rc
+        m[i] = False
+        sets.append(np.nonzero(m)[0])
+    return sets
+
+
+@pytest.mark.parametrize("dim,periodic,n", [(2, False, 2600), (3, False, 2500), (3, True, 2500), (2, True, 2100)])
+def test_neighbour_sets_equal_brute_force(dim, periodic, n):
+    sc = S.random_cloud(dim=dim, n=n, L=1.0, dx=0.05 if dim == 3 else 0.03, periodic=periodic, seed=11 + n)
+    o = O.OracleScene(sc)  # n > 2000: the oracle uses its cell list
+    counts, lst = o.neighbors()
+    p = sc["params"]
+    sets = _brute_sets(sc["particles"]["pos"].copy(), dim, 3 * p["h"], p["box_min"], p["box_max"],
+                       p["periodic"] if periodic else None)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for i in range(n):
+        assert np.array_equal(lst[off[i]:off[i + 1]], sets[i]), i
+    ob = O.OracleScene(sc, force_brute=True)
+    c2, l2 = ob.neighbors()
+    assert np.array_equal(counts, c2) and np.array_equal(lst, l2)
+
+
+def test_lattice_neighbour_counts():
+    """Interior lattice site with h = dx, r_c = 3 dx: 24 sites (2D) / 92 (3D) lie in the
+    open disc/ball of radius 3 dx; these counts are fixed by integer geometry."""
+    for dim, expect in [(2, 24), (3, 92)]:
+        g = np.arange(-3, 4)
+        pts = np.stack(np.meshgrid(*([g] * dim), indexing="ij"), -1).reshape(-1, dim)
+        cnt = int(np.sum(np.sum(pts * pts, 1) < 9)) - 1
+        assert cnt == expect
+        # dx = 1/8 keeps every lattice coordinate and squared distance exact in binary
+        sc = S.periodic_box(dim=dim, n=10, dx=0.125, jitter=0.0, vel_amp=0.0)
+        counts, _ = O.OracleScene(sc).neighbors()
+        assert np.all(counts == expect)
+
+
+# ----------------------------------------------------------------------------- density (Eq. densum)
+
+def test_density_summation_on_periodic_lattice():
+    dim = 3
+    sc = S.periodic_box(dim=dim, n=8, dx=0.1, jitter=0.0, vel_amp=0.0)
+    o = O.OracleScene(sc)
+    rho = o.get("rho")
+    # independent brute-force sum with the (pinned) kernel over the lattice images
+    dx = 0.1
+    g = np.arange(-3, 4) * dx
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    r = np.linalg.norm(pts, axis=1)
+    expect = 1.0 * dx ** 3 * sum(O.kernel_w(3, x, dx) for x in r if x < 3 * dx)
+    assert np.allclose(rho, expect, rtol=1e-13, atol=0)
+    assert abs(expect - 1.0) < 1e-4
+
+
+# ----------------------------------------------------------------------------- conservation (Eqs. conservlinmom, couplingforce)
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_linear_momentum_conserved_periodic_box(dim):
+    sc = S.periodic_box(dim=dim, n=10 if dim == 3 else 20, dx=0.1, bodies=2 if dim == 3 else 3,
+                        body_radius=0.16, vel_amp=0.2, jitter=0.1, seed=4)
+    o = O.OracleScene(sc)
+    d0 = o.diagnostics()
+    scale = np.abs(sc["particles"]["mass"][:, None] * sc["particles"]["vel"]).sum()
+    for _ in range(10):
+        o.step(10)
+        d = o.diagnostics()
+        assert np.all(np.abs(d[:3] - d0[:3]) <= 1e-13 * scale), (d[:3], d0[:3])
+    assert d[10] == 100
+
+
+def test_angular_momentum_conserved_inviscid_fluid_cluster():
+    """nu = 0, no walls, no gravity, non-periodic: every pair force is central and the
+    KDK scheme conserves angular momentum of point particles exactly (rounding only)."""
+    sc = S.cluster(dim=3, n=9, dx=0.1, n_bodies=0, vel_amp=0.05)
+    o = O.OracleScene(sc)
+    d0 = o.diagnostics()
+    m = sc["particles"]["mass"]
+    scale = np.sum(m * np.linalg.norm(sc["particles"]["pos"], axis=1) * np.linalg.norm(sc["particles"]["vel"], axis=1))
+    o.step(60)
+    d = o.diagnostics()
+    assert np.linalg.norm(d[3:6] - d0[3:6]) < 1e-13 * scale, (d[3:6], d0[3:6])
+
+
+def test_angular_momentum_with_isotropic_bodies():
+    """Same with two spheres of isotropic inertia: the coupling forces are central too,
+    so angular momentum of fluid plus bodies is kept up to the O(dt^2) time error of the
+    body rotation update."""
+    sc = S.cluster(dim=3, n=9, dx=0.1, n_bodies=2, vel_amp=0.05)
+    o = O.OracleScene(sc)
+    I = o.bodies()["inertia"]
+    for k in range(2):
+        assert np.allclose(I[k], I[k][0, 0] * np.eye(3), rtol=1e-12, atol=1e-16)
+    d0 = o.diagnostics()
+    o.step(60)
+    d = o.diagnostics()
+    Lscale = np.linalg.norm(d0[3:6])
+    err60 = np.linalg.norm(d[3:6] - d0[3:6])
+    assert err60 < 1e-6 * Lscale, (d[3:6], d0[3:6])
+    assert np.all(np.abs(d[:3] - d0[:3]) < 1e-13 * (1 + np.abs(d0[:3]).max()))
+
+
+def test_heat_energy_conserved_adiabatic():
+    """Adiabatic closed system (periodic, no walls): sum m c_p T is constant because the
+    Cleary-Monaghan pair terms are antisymmetric (Eq. heat_equation)."""
+    sc = S.periodic_box(dim=3, n=8, dx=0.1, bodies=1, body_radius=0.25, vel_amp=0.05, kappa=2.0,
+                        cp=1.5, T_amp=30.0)
+    sc["materials"][1]["kappa"] = 7.0
+    sc["materials"][1]["cp"] = 0.6
+    sc["params"]["dt_fixed"] = 1e-4  # below the conduction limit 0.1 rho c_p h^2 / kappa
+    o = O.OracleScene(sc)
+    e0 = o.diagnostics()[7]
+    for _ in range(5):
+        o.step(4)
+        assert abs(o.diagnostics()[7] - e0) < 1e-13 * abs(e0)
+    T = o.get("temp")
+    assert T.std() < sc["particles"]["temperature"].std()
+
+
+# ----------------------------------------------------------------------------- rigid bodies (Sec. 3.4)
+
+def test_disk_mass_and_inertia_converge_to_paper_values():
+    gd = json.load(open(os.path.join(GOLD, "disk_mass_inertia.json")))
+    R = gd["diameter"] / 2
+    errs_m, errs_i = [], []
+    for dx in gd["dx"]:
+        n = int(np.ceil(2 * R / dx)) + 2
+        ax = (np.arange(-n, n) + 0.5) * dx
+        X, Y = np.meshgrid(ax, ax, indexing="ij")
+        P = np.stack([X.ravel(), Y.ravel(), 0 * X.ravel()], 1)
+        P = P[(P[:, 0] ** 2 + P[:, 1] ** 2) <= R * R]
+        m = np.full(len(P), gd["density"] * dx * dx)
+        M, c, I = O.body_mass_chunked(2, dx, P, m, len(P))
+        assert gd["mass_axis_range"][0] < M < gd["mass_axis_range"][1]
+        assert gd["inertia_axis_range"][0] < I[2, 2] < gd["inertia_axis_range"][1]
+        errs_m.append(abs(M / gd["mass_analytic"] - 1))
+        errs_i.append(abs(I[2, 2] / gd["inertia_analytic"] - 1))
+    assert errs_m[-1] < 1e-3 and errs_i[-1] < 1e-3
+    assert errs_m[-1] < errs_m[0] / 50 and errs_i[-1] < errs_i[0] / 50
+
+
+def test_two_level_mass_quantities_equal_direct_sum():
+    """Eqs. procwise_* + global_* (chunks as processors) reproduce the serial result."""
+    rng = np.random.default_rng(0)
+    P = rng.normal(size=(997, 3))
+    m = rng.uniform(0.5, 2.0, size=997)
+    M1, c1, I1 = O.body_mass_chunked(3, 0.1, P, m, 997)
+    for chunk in (1, 7, 64, 500):
+        M2, c2, I2 = O.body_mass_chunked(3, 0.1, P, m, chunk)
+        assert abs(M2 - M1) < 1e-14 * M1
+        assert np.allclose(c2, c1, rtol=0, atol=1e-14 * np.abs(P).max())
+        assert np.allclose(I2, I1, rtol=0, atol=1e-13 * np.abs(I1).max())
+    # inertia of a point cloud = sum m (|d|^2 1 - d d^T) + sum I_r 1 (Huygens-Steiner)
+    d = P - c1
+    ref = np.einsum("i,ij->j", m, d * d).sum() * np.eye(3) - np.einsum("i,ij,ik->jk", m, d, d)
+    Ir = 0.4 * m * ((0.75 / math.pi) ** (1 / 3) * 0.1) ** 2
+    assert np.allclose(I1, ref + Ir.sum() * np.eye(3), rtol=1e-12, atol=0)
+
+
+def test_quaternion_product_composes_rotations():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        a = rng.normal(size=4); a /= np.linalg.norm(a)
+        b = rng.normal(size=4); b /= np.linalg.norm(b)
+        Ra, Rb = O.quat_rot(a), O.quat_rot(b)
+        assert np.allclose(Ra @ Ra.T, np.eye(3), atol=1e-14) and abs(np.linalg.det(Ra) - 1) < 1e-14
+        assert np.allclose(O.quat_rot(O.quat_mul(a, b)), Ra @ Rb, atol=1e-14)
+    # rotation by angle t about z: (cos t/2, 0, 0, sin t/2) maps x to (cos t, sin t, 0)
+    t = 0.7
+    R = O.quat_rot([math.cos(t / 2), 0, 0, math.sin(t / 2)])
+    assert np.allclose(R @ [1, 0, 0], [math.cos(t), math.sin(t), 0], atol=1e-15)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_free_fall_is_exact(dim):
+    """Single body, no fluid, no walls: KDK integrates constant gravity exactly,
+    r_k(t) = r0 + v0 t + g t^2 / 2."""
+    sc = S.free_fall(dim=dim, vel=(0.3, -0.1, 0.2) if dim == 3 else (0.3, -0.1, 0.0))
+    o = O.OracleScene(sc)
+    b0 = o.bodies()
+    g = np.array(sc["params"]["gravity"])
+    v0 = np.array(sc["bodies"]["vel"][0])
+    dt = sc["params"]["dt_fixed"]
+    o.step(200)
+    b = o.bodies()
+    t = 200 * dt
+    expect = b0["com"][0] + v0 * t + 0.5 * g * t * t
+    assert np.allclose(b["com"][0], expect, rtol=0, atol=1e-13 * (1 + np.abs(expect).max()))
+    assert np.allclose(b["vel"][0], v0 + g * t, rtol=0, atol=1e-13)
+
+
+def test_torque_free_sphere_rotates_at_constant_rate():
+    w = np.array([0.3, -1.1, 0.6])
+    sc = S.free_fall(dim=3, g=0.0, omega=tuple(w))
+    o = O.OracleScene(sc)
+    dt = sc["params"]["dt_fixed"]
+    o.step(500)
+    q = o.bodies()["quat"][0]
+    th = np.linalg.norm(w) * 500 * dt
+    ax = w / np.linalg.norm(w)
+    expect = np.concatenate([[math.cos(th / 2)], math.sin(th / 2) * ax])
+    assert np.allclose(q, expect, atol=1e-12)
+    # rigid invariance: pairwise distances inside the body are unchanged
+    x0 = sc["particles"]["pos"]
+    x1 = o.get("pos")
+    d0 = np.linalg.norm(x0[:, None] - x0[None], axis=-1)
+    d1 = np.linalg.norm(x1[:, None] - x1[None], axis=-1)
+    assert np.abs(d1 - d0).max() < 1e-13
+
+
+def test_contact_elastic_head_on_swaps_velocities():
+    """Two equal single-particle bodies, d_c = 0: a linear repulsive spring acting while
+    r < dx returns the velocities exchanged (elastic, equal masses) and lasts half a
+    period pi sqrt(m_eff / k_c) of the spring."""
+    k, speed = 1e3, 0.5
+    sc = S.contact_pair(dim=2, gap=0.001, speed=speed, k_contact=k, d_contact=0.0, dt=2e-5)
+    o = O.OracleScene(sc)
+    m = sc["particles"]["mass"][0]
+    t_contact = math.pi * math.sqrt(0.5 * m / k)
+    steps = int(3 * t_contact / 2e-5) + 200
+    touching = 0
+    fmin = 0.0
+    for _ in range(steps):
+        o.step(1)
+        f = o.get("force")
+        x = o.get("pos")
+        e = (x[0] - x[1]) / np.linalg.norm(x[0] - x[1])
+        fmin = min(fmin, float(f[0] @ e))  # tension cut-off: never attractive
+        touching += np.linalg.norm(x[0] - x[1]) < 0.1
+    v = o.bodies()["vel"]
+    assert fmin >= 0.0
+    assert np.allclose(v[0], [-speed, 0, 0], atol=2e-3 * speed)
+    assert np.allclose(v[1], [speed, 0, 0], atol=2e-3 * speed)
+    assert abs(touching * 2e-5 - t_contact) < 0.02 * t_contact
+
+
+def test_contact_damping_dissipates():
+    sc = S.contact_pair(dim=3, gap=0.001, speed=0.5, k_contact=1e3, d_contact=0.5, dt=2e-5)
+    o = O.OracleScene(sc)
+    ke0 = o.diagnostics()[6]
+    o.step(4000)
+    ke = o.diagnostics()[6]
+    v = o.bodies()["vel"]
+    assert ke < 0.9 * ke0 and v[0][0] < 0 < v[1][0]  # bounced, slower
+
+
+# ----------------------------------------------------------------------------- closed forms of the fluid and heat solvers
+
+def test_hydrostatic_pressure_closed_box():
+    """Closed 2D box filled with fluid at rest under gravity: the static state has
+    dp/dy = -rho0 |g| (EOS, momentum equation and wall extrapolation together; the
+    closed box avoids the free surface, where the plain WCSPH density deficit pulls
+    the surface rows inward)."""
+    dx = 0.02
+    sc = S.hydrostatic_tank2d(dx=dx, width=0.4, depth=0.56, c=10.0, eta=0.2, closed=True)
+    o = O.OracleScene(sc)
+    o.step(2000)
+    x, p, mat, u = o.get("pos"), o.get("pres"), o.get("mat"), o.get("vel")
+    f = mat == 0
+    y, xx = x[f, 1], x[f, 0]
+    sel = (y > 3 * dx) & (y < 0.56 - 3 * dx) & (xx > 3 * dx) & (xx < 0.4 - 3 * dx)
+    A = np.stack([np.ones(sel.sum()), y[sel]], 1)
+    coef = np.linalg.lstsq(A, p[f][sel], rcond=None)[0]
+    rho = o.get("rho")[f][sel].mean()
+    assert abs(coef[1] / (-rho * 1.0) - 1) < 5e-3, coef
+    resid = p[f][sel] - A @ coef
+    assert np.sqrt(np.mean(resid ** 2)) < 1e-2 * np.sqrt(np.mean((p[f][sel] - p[f][sel].mean()) ** 2))
+    assert np.abs(u[f]).max() < 1e-3
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_heat_conduction_sine_decay(dim):
+    """Periodic slab at rest with T = T0 + A sin(k x): the amplitude decays as
+    exp(-kappa k^2 t / (rho c_p)) (1D heat equation, Eq. goveq heat)."""
+    n = (48, 8) if dim == 2 else (48, 8, 8)
+    dx = 1.0 / 48
+    kappa, cp = 1.0, 1.0
+    sc = S.heat_slab(dim=dim, n=n, dx=dx, kappa=kappa, cp=cp)
+    o = O.OracleScene(sc)
+    rho = o.get("rho").mean()
+    x = sc["particles"]["pos"][:, 0]
+    k = 2 * math.pi / 1.0
+    steps = 400
+    o.step(steps)
+    t = steps * sc["params"]["dt_fixed"]
+    T = o.get("temp")
+    A = 2 * np.mean((T - 300.0) * np.sin(k * x))
+    expect = 10.0 * math.exp(-kappa * k * k * t / (rho * cp))
+    assert abs(A / expect - 1) < 1e-2, (A, expect)
+    # particles stay at rest on the periodic lattice
+    assert np.abs(o.get("pos") - sc["particles"]["pos"]).max() < 1e-12
+
+
+def test_linear_temperature_field_is_stationary_in_the_interior():
+    dim = 2
+    sc = S.heat_slab(dim=dim, n=(20, 20), dx=0.05, A=0.0)
+    sc["params"]["periodic"] = [0, 0, 0]
+    sc["params"]["box_min"] = [-1.0, -1.0, 0.0]
+    sc["params"]["box_max"] = [2.0, 2.0, 0.0]
+    x = sc["particles"]["pos"]
+    sc["particles"]["temperature"] = 300.0 + 3.0 * x[:, 0] - 2.0 * x[:, 1]
+    o = O.OracleScene(sc)
+    dT = o.get("dtemp")
+    interior = np.all((x[:, :2] > 3.5 * 0.05) & (x[:, :2] < 1.0 - 3.5 * 0.05), axis=1)
+    assert np.abs(dT[interior]).max() < 1e-9
+
+
+def test_time_step_cfl_condition():
+    sc = S.tank2d_disc()
+    o = O.OracleScene(sc)
+    o.step(1)
+    d = o.diagnostics()
+    # at rest the CFL term 0.25 h / c binds (viscous 0.125 h^2 / nu = 1.95e-3, body force 0.028)
+    assert abs(d[11] - 0.25 * 0.0125 / 10.0) < 1e-18
+
+
+# ----------------------------------------------------------------------------- phase transitions (Sec. 3.6)
+
+def _melt_scene(T_body, T_fluid=1100.0):
+    sc = S.periodic_box(dim=2, n=16, dx=0.1, bodies=1, body_radius=0.35, vel_amp=0.0, kappa=0.0)
+    mats = sc["materials"]
+    mats[0].update(T_transition=1000.0, transitions_to=1)
+    mats[1].update(T_transition=1000.0, transitions_to=0)
+    p = sc["particles"]
+    p["temperature"] = np.where(p["material"] == 1, T_body, T_fluid).astype(float)
+    sc["bodies"]["omega"][:] = [0, 0, 0.5]
+    sc["bodies"]["vel"][:] = [0.1, 0.0, 0.0]
+    return sc
+
+
+def test_melting_relabels_and_retires_body():
+    sc = _melt_scene(T_body=1200.0)
+    o = O.OracleScene(sc)
+    o.step(1)
+    mat = o.get("mat")
+    assert np.all(mat == 0)
+    assert o.bodies()["alive"][0] == 0
+    assert np.all(o.get("body") == -1)
+
+
+def test_partial_melt_keeps_velocity_of_remaining_particles():
+    """After a relabel the remaining particles of the body keep their velocity
+    (u_k = u'_k + w x (r_k - r'_k), reading R10)."""
+    sc = _melt_scene(T_body=900.0)
+    p = sc["particles"]
+    rig = np.nonzero(p["material"] == 1)[0]
+    x = p["pos"][rig]
+    hot = rig[x[:, 0] > np.median(x[:, 0])]
+    p["temperature"][hot] = 1100.0
+    o = O.OracleScene(sc)
+    o.step(1)
+    mat = o.get("mat")
+    stay = rig[mat[rig] == 1]
+    assert len(stay) and np.all(mat[hot] == 0)
+    # reference: the rigid velocity field of the old body evaluated at the positions
+    com_old_sc = O.OracleScene(_melt_scene(T_body=900.0))
+    com_old_sc.step(1)
+    u_ref = com_old_sc.get("vel")
+    u = o.get("vel")
+    assert np.allclose(u[stay], u_ref[stay], rtol=0, atol=1e-14)
+    b = o.bodies()
+    assert b["alive"][0] == 1 and b["mass"][0] < com_old_sc.bodies()["mass"][0]
+
+
+def test_solidification_joins_nearest_body_or_forms_new_ones():
+    sc = _melt_scene(T_body=900.0)
+    p = sc["particles"]
+    x = p["pos"]
+    rig = p["material"] == 1
+    c = x[rig].mean(0)
+    dist = np.linalg.norm(x - c, axis=1)
+    # a ring of fluid touching the body, and a separate cold patch far away
+    ring = (~rig) & (dist < 0.5)
+    far = (~rig) & (np.linalg.norm(x - (c + [0.75, 0.75, 0]), axis=1) < 0.15)
+    p["temperature"][ring | far] = 900.0
+    o = O.OracleScene(sc)
+    o.step(1)
+    mat, body = o.get("mat"), o.get("body")
+    assert np.all(mat[ring] == 1) and np.all(body[ring] == 0)
+    assert np.all(mat[far] == 1)
+    newb = np.unique(body[far])
+    assert len(newb) == 1 and newb[0] == 1
+    b = o.bodies()
+    assert b["alive"][1] == 1 and abs(b["mass"][1] - far.sum() * 0.01) < 1e-15
+
+
+def test_enthalpy_balance_with_source_over_melt_and_solidify():
+    """With latent heat (apparent-capacity extension) and the surface source, sum m H
+    changes by exactly the integrated source power (pair terms cancel)."""
+    sc = S.periodic_box(dim=2, n=16, dx=0.1, bodies=1, body_radius=0.45, vel_amp=0.0, kappa=5.0,
+                        jitter=0.0)
+    sc["particles"]["temperature"] = np.where(sc["particles"]["material"] == 1, 310.0, 400.0)
+    mats = sc["materials"]
+    for m in mats:
+        m.update(T_transition=320.0, latent_heat=20.0, mushy_width=4.0)
+    mats[0]["transitions_to"] = 1
+    mats[1]["transitions_to"] = 0
+    p = sc["params"]
+    p.update(src_power=4000.0, src_radius=0.3, src_origin=[0.8, 0.0, 0.0], src_speed=[0.0, 0.0, 0.0],
+             src_depth=10.0, src_ztop=5.0)
+    o = O.OracleScene(sc)
+    dt = p["dt_fixed"]
+    e0 = o.diagnostics()[7]
+    # expected source power: independent quadrature of the per-particle source terms
+    melted = False
+    for _ in range(40):
+        mass = sc["particles"]["mass"]
+        e_before = o.diagnostics()[7]
+        o.step(1)
+        # the source of step n+1 is evaluated at r^{n+1} with rho^{n+1}
+        x = o.get("pos")
+        q = 4000.0 * np.exp(-2.0 * ((x[:, 0] - 0.8) ** 2) / 0.09)
+        rho1 = o.get("rho")
+        expect = dt * np.sum(mass * q / rho1)
+        assert abs((o.diagnostics()[7] - e_before) - expect) < 1e-10 * abs(e_before)
+        melted |= bool(np.any((o.get("mat") == 0) & (sc["particles"]["material"] == 1)))
+    assert melted
+    assert o.diagnostics()[7] > e0
