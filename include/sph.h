@@ -1,0 +1,240 @@
+/*
+ * libsph -- GB300 (sm_103a) implementation of the per-time-step particle interaction
+ * sweep of the SPH fluid / rigid-body / heat / phase-transition method of
+ * Fuchs, Meier, Wall, Cyron (arXiv:2103.07925).
+ *
+ * C ABI: plain pointers and sizes, no C++ types, no exceptions across the boundary.
+ * Every call returns an sph_status; sph_last_error() gives a thread-local message.
+ *
+ * Ownership: the library copies every input array (the caller keeps its buffers);
+ * output buffers are caller-allocated host memory unless stated otherwise.  One
+ * scene (or batch) must be driven by one host thread at a time.
+ *
+ * Units are the caller's; the method is unit-free.  Positions and vectors always
+ * carry three components, z = 0 in 2D.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* particle kinds: fluid particle i, rigid particle r of a body k, wall boundary particle b
+ * (Sec. 3.1.2 and Sec. 3.3.4) */
+#define SPH_FLUID 0
+#define SPH_RIGID 1
+#define SPH_WALL 2
+
+#define SPH_MAX_MATERIALS 16
+
+typedef enum {
+  SPH_OK = 0,
+  SPH_ERR_INVALID = -1,   /* bad argument or inconsistent input */
+  SPH_ERR_OOM = -2,       /* device or host allocation failed */
+  SPH_ERR_CUDA = -3,      /* a CUDA call failed (message in sph_last_error) */
+  SPH_ERR_NONFINITE = -4, /* a NaN or Inf appeared in the particle state */
+  SPH_ERR_TIMEOUT = -5,   /* a bounded device wait gave up */
+  SPH_ERR_CAPACITY = -6   /* a fixed capacity (bodies, batch slots, memory cap) is exceeded */
+} sph_status;
+
+/* One material (phase).  Fluid phases use rho0, c (artificial speed of sound, Eq. eos),
+ * eta (dynamic viscosity, Eq. momentum); every phase carries cp and kappa (Eq.
+ * heat_equation).  A phase with transitions_to >= 0 turns into that material when its
+ * temperature crosses T_transition (Sec. 3.6): a rigid phase melts above it, a fluid
+ * phase solidifies below it.  latent_heat > 0 switches that pair of phases to the
+ * enthalpy form of the apparent-capacity extension named in the paper's remark on
+ * latent heat, with a mushy interval of width mushy_width around T_transition. */
+typedef struct {
+  int32_t kind;
+  double rho0, c, eta, cp, kappa;
+  double T_transition;
+  int32_t transitions_to;
+  double latent_heat, mushy_width;
+} sph_material;
+
+/* Scene parameters.
+ *  dim              2 or 3
+ *  dx, h            initial particle spacing and smoothing length (the paper uses h = dx)
+ *  kernel_support   kappa of r_c = kappa h (3 for the quintic spline, Sec. 3.1.1)
+ *  box_min/max      cell lattice extent (Sec. 3.2); periodic axes repeat with this period
+ *  gravity          body force per unit mass b (fluid and bodies)
+ *  dt_mode          0: dt_fixed;  1: Eq. timestepcond evaluated every step
+ *  k_contact/d_contact  contact stiffness and damping of Eq. contactforce; <= 0 / < 0
+ *                   select defaults k_c = m_r (0.22 / dt_ref)^2, d_c = 0.2 sqrt(k_c m_r / 2)
+ *                   with dt_ref = 0.25 h / c_max and m_r the smallest rigid particle mass
+ *  precision        64: FP64 everywhere; 32: FP32 pair sums with cell-relative positions,
+ *                   FP64 body sums, orientation and diagnostics
+ *  rebin_interval   steps between cell re-binning (1 = every step, the exact method)
+ *  key_order        0: Morton order of cells;  1: row-major order (x fastest)
+ *  cells_per_group  cells along x handled by one warp (0 = automatic; row-major only)
+ *  body_capacity    maximum number of bodies including those created by solidification
+ *                   (0: initial count + 1024)
+ *  src_*            optional moving Gaussian surface heat source (not in the paper; see
+ *                   the design notes): power density src_power, radius src_radius, centre
+ *                   src_origin + src_speed t, acting within src_depth below src_ztop on
+ *                   phases that take part in a transition. */
+typedef struct {
+  int32_t dim;
+  double dx, h, kernel_support;
+  double box_min[3], box_max[3];
+  int32_t periodic[3];
+  double gravity[3];
+  int32_t dt_mode;
+  double dt_fixed;
+  double k_contact, d_contact;
+  int32_t precision;
+  int32_t rebin_interval;
+  int32_t key_order;
+  int32_t cells_per_group;
+  int32_t body_capacity;
+  int32_t n_materials;
+  const sph_material* materials;
+  double src_power, src_radius, src_speed[3], src_origin[3], src_depth, src_ztop;
+} sph_params;
+
+/* Particles (Sec. 3.1.2: phase, position, velocity, mass, density, temperature, body).
+ * All arrays have n rows; vectors are n*3 doubles, row-major.
+ *  density          fluid: initial value (recomputed by Eq. densum); rigid and wall:
+ *                   the constant density that sets the particle volume V = m / rho
+ *  material         index into sph_params.materials; the material's kind is the kind
+ *  body             body id of rigid particles (0 .. k-1), ignored otherwise
+ *  wall_velocity    prescribed velocity of wall particles (nullable: zero)
+ *  wall_temperature prescribed (Dirichlet) temperature of wall particles, NaN =
+ *                   adiabatic (nullable: all adiabatic) */
+typedef struct {
+  int64_t n;
+  const double *pos, *vel, *mass, *density, *temperature;
+  const int32_t *material, *body;
+  const double *wall_velocity, *wall_temperature;
+} sph_particles_in;
+
+/* Rigid bodies (Sec. 3.4).  Mass, centre of mass and inertia are always derived from
+ * the rigid particles (Eqs. procwise_centerofmass, procwise_inertia); quat (w,x,y,z)
+ * is the initial orientation, vel and omega the initial linear and angular velocity. */
+typedef struct {
+  int32_t k;
+  const double *quat, *vel, *omega;
+} sph_bodies_in;
+
+typedef struct sph_scene sph_scene;
+
+/* Create a scene on the current CUDA device.  Copies the inputs, bins the particles,
+ * derives body mass quantities and evaluates the initial accelerations (one full
+ * evaluation at t = 0).  stream: a cudaStream_t or NULL (the library creates one).
+ * Errors: SPH_ERR_INVALID (bad sizes, particle outside a non-periodic box, fewer than
+ * three cells on a periodic axis, body without particles), SPH_ERR_OOM, SPH_ERR_CUDA. */
+sph_status sph_create_scene(const sph_params* params, const sph_particles_in* particles,
+                            const sph_bodies_in* bodies, void* stream, sph_scene** out);
+
+/* Advance nsteps time steps of the velocity-Verlet scheme of Sec. 3.7 (asynchronous on
+ * the scene's stream except for a final status read).  SPH_ERR_NONFINITE if the state
+ * went non-finite. */
+sph_status sph_step(sph_scene* scene, int32_t nsteps);
+
+/* Same as sph_step without the final status read (no host synchronisation). */
+sph_status sph_step_async(sph_scene* scene, int32_t nsteps);
+
+/* field bits for sph_read_fields / sph_write_fields; dst[b] receives field bit b */
+enum {
+  SPH_F_POS = 0,   /* n*3 double */
+  SPH_F_VEL = 1,   /* n*3 double: fluid u, rigid u_r, wall prescribed velocity */
+  SPH_F_ACC = 2,   /* n*3 double: fluid acceleration a_i */
+  SPH_F_RHO = 3,   /* n double */
+  SPH_F_PRES = 4,  /* n double: fluid EOS pressure, wall/rigid extrapolated pressure */
+  SPH_F_TEMP = 5,  /* n double: temperature (walls: prescribed value or NaN) */
+  SPH_F_DTEMP = 6, /* n double: dT/dt (dH/dt for enthalpy phases) of the last evaluation */
+  SPH_F_MAT = 7,   /* n int32 */
+  SPH_F_BODY = 8,  /* n int32 (-1 for non-rigid) */
+  SPH_F_FORCE = 9, /* n*3 double: f_r of rigid particles (Eq. rigidparticle_force) */
+  SPH_F_VEXT = 10, /* n*3 double: extrapolated velocity of wall and rigid particles */
+  SPH_F_CELL = 11, /* n int32: row-major cell index cx + nx (cy + ny cz) */
+  SPH_F_ENTH = 12, /* n double: specific enthalpy (enthalpy phases) */
+  SPH_F_COUNT = 13
+};
+
+/* Copy fields to host.  original_order = 1 returns rows in input order, 0 in the
+ * library's current (cell-sorted) order.  Synchronises the scene's stream. */
+sph_status sph_read_fields(sph_scene* scene, uint32_t field_mask, void* const* host_dst,
+                           int32_t original_order);
+
+/* Overwrite POS, VEL and TEMP of fluid particles from host arrays in input order
+ * (used for restarts and the host-buffer benchmark); re-bins before the next step. */
+sph_status sph_write_fields(sph_scene* scene, uint32_t field_mask, const void* const* host_src);
+
+/* Body state (k rows; each pointer nullable): com k*3, quat k*4, vel k*3, omega k*3,
+ * mass k, inertia k*9 (world frame), force k*3, torque k*3, alive k. */
+typedef struct {
+  double *com, *quat, *vel, *omega, *mass, *inertia, *force, *torque;
+  int32_t* alive;
+} sph_bodies_out;
+sph_status sph_read_bodies(sph_scene* scene, const sph_bodies_out* out, int32_t* k_out);
+
+/* FP64 diagnostics: [0..2] linear momentum, [3..5] angular momentum, [6] kinetic
+ * energy, [7] thermal energy (sum m c_p T, or m H), [8] fluid+rigid mass, [9] time,
+ * [10] step, [11] last dt, [12] fluid count, [13] rigid count, [14] live bodies,
+ * [15] ordered pairs of the last force/heat sweep. */
+sph_status sph_diagnostics(sph_scene* scene, double out[16]);
+
+/* Neighbour sets N(a) = {b != a : |r_ab| < r_c} of the current positions, by input
+ * index, ascending (test and export entry; FP64 scenes use the FP64 predicate).
+ * counts: n int64; list: cap int32 (may be NULL to query the total). *total = sum. */
+sph_status sph_neighbors(sph_scene* scene, int64_t* counts, int32_t* list, int64_t cap,
+                         int64_t* total);
+
+/* Scene information: [0] n, [1] fluid, [2] rigid, [3] wall, [4] bodies, [5] cells,
+ * [6] cells x, [7] cells y, [8] cells z, [9] steps taken, [10] kernels per step,
+ * [11] device bytes, [12] warp groups, [13] cells per group, [14] key order,
+ * [15] ordered pairs evaluated by the force / heat sweep over all steps taken. */
+sph_status sph_info(sph_scene* scene, int64_t out[16]);
+
+/* Tracing: run reps complete steps with the kernels launched one by one (no graph) and
+ * CUDA events between them; ms_per_stage[SPH_PROFILE_STAGES] receives the mean device
+ * time of each stage.  The scene advances by reps steps. */
+#define SPH_PROFILE_STAGES 18
+sph_status sph_profile(sph_scene* scene, int32_t reps, double* ms_per_stage);
+const char* sph_profile_stage_name(int32_t stage);
+
+void sph_destroy_scene(sph_scene* scene);
+const char* sph_last_error(void);
+
+/* ------------------------------------------------------------------ batches and serving
+ * A batch advances many independent scenes (jobs) together: every stage of a step is one
+ * launch over all resident scenes, driven by a device table of scene offsets, and the
+ * whole step is a captured CUDA graph.  Jobs are admitted while their device footprint
+ * fits under hbm_cap_bytes and a slot is free; finished jobs are reported by poll and
+ * their memory is released when they are read out. */
+typedef struct sph_batch sph_batch;
+typedef struct {
+  const sph_params* params;
+  const sph_particles_in* particles;
+  const sph_bodies_in* bodies;
+  int32_t nsteps_total;
+} sph_job_desc;
+
+sph_status sph_batch_create(int32_t capacity_scenes, size_t hbm_cap_bytes, int32_t precision,
+                            void* stream, sph_batch** out);
+/* footprint estimate of one job in bytes (device memory it would hold) */
+sph_status sph_job_footprint(const sph_job_desc* job, size_t* bytes);
+/* SPH_ERR_CAPACITY when the job does not fit now (no slot or over the memory cap) */
+sph_status sph_batch_admit(sph_batch* batch, const sph_job_desc* job, int64_t* job_id);
+/* advance every resident, unfinished job by up to nsteps (jobs stop at nsteps_total) */
+sph_status sph_batch_step(sph_batch* batch, int32_t nsteps);
+/* ids of jobs that reached nsteps_total since the last poll (n_done <= max_done) */
+sph_status sph_batch_poll(sph_batch* batch, int64_t* done_ids, int32_t max_done, int32_t* n_done);
+sph_status sph_batch_read_fields(sph_batch* batch, int64_t job_id, uint32_t field_mask,
+                                 void* const* host_dst);
+sph_status sph_batch_job_diagnostics(sph_batch* batch, int64_t job_id, double out[16]);
+/* release a job's device memory and slot */
+sph_status sph_batch_release(sph_batch* batch, int64_t job_id);
+/* [0] resident jobs, [1] resident particles, [2] bytes in use, [3] steps taken */
+sph_status sph_batch_info(sph_batch* batch, int64_t out[8]);
+void sph_batch_destroy(sph_batch* batch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

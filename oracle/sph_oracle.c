@@ -1121,11 +1121,16 @@ void orc_get(orc_scene* s, int32_t field, void* out) {
   int32_t* o = (int32_t*)out;
   switch (field) {
     case ORC_F_POS: memcpy(d, s->x, sizeof(double) * 3 * (size_t)n); break;
-    case ORC_F_VEL: memcpy(d, s->u, sizeof(double) * 3 * (size_t)n); break;
+    case ORC_F_VEL: /* walls report their prescribed velocity */
+      for (int64_t i = 0; i < n; i++)
+        for (int q = 0; q < 3; q++) d[3 * i + q] = is_kind(s, i, ORC_WALL) ? s->wu[3 * i + q] : s->u[3 * i + q];
+      break;
     case ORC_F_ACC: memcpy(d, s->a, sizeof(double) * 3 * (size_t)n); break;
     case ORC_F_RHO: memcpy(d, s->rho, sizeof(double) * (size_t)n); break;
     case ORC_F_PRES: memcpy(d, s->p, sizeof(double) * (size_t)n); break;
-    case ORC_F_TEMP: memcpy(d, s->T, sizeof(double) * (size_t)n); break;
+    case ORC_F_TEMP: /* walls report their prescribed temperature (NaN: adiabatic) */
+      for (int64_t i = 0; i < n; i++) d[i] = is_kind(s, i, ORC_WALL) ? s->wT[i] : s->T[i];
+      break;
     case ORC_F_DTEMP: memcpy(d, s->dT, sizeof(double) * (size_t)n); break;
     case ORC_F_MAT: memcpy(o, s->mat, sizeof(int32_t) * (size_t)n); break;
     case ORC_F_BODY: memcpy(o, s->body, sizeof(int32_t) * (size_t)n); break;

@@ -1,0 +1,300 @@
+// Import / export, diagnostics and the neighbour-set export of libsph.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sph_kernels.cuh"
+
+namespace sph {
+
+struct ImportArgs {
+  const double *pos, *vel, *mass, *dens, *temp, *wvel, *wtemp;
+  const int *mat, *body, *slot;
+};
+
+// specific enthalpy of the apparent-capacity extension (H = 0 at T_t - w/2)
+__device__ __forceinline__ double enthalpy_of(const MatD* mats, int mt, double T) {
+  const MatD& M = mats[mt];
+  int so = mt, li = mt;
+  if (M.to >= 0) {
+    so = M.kind == KRIGID ? mt : M.to;
+    li = M.kind == KRIGID ? M.to : mt;
+  }
+  double cs = mats[so].cp, cl = mats[li].cp, w = M.w, Tlo = M.Tt - 0.5 * w;
+  double Hh = (cs + M.L / w) * w;
+  if (T <= Tlo) return cs * (T - Tlo);
+  if (T <= Tlo + w) return (cs + M.L / w) * (T - Tlo);
+  return Hh + cl * (T - Tlo - w);
+}
+
+// input (original order, FP64) -> bank P of the scene, unsorted; the forced rebin that
+// follows orders the particles by cell
+template <class R>
+__global__ void k_import(Scene<R>* const* sc, ImportArgs a) {
+  const Scene<R>& S = **sc;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
+    int mt = a.mat[i];
+    int kind = S.mat[mt].kind;
+    double x[3] = {a.pos[3 * i], a.pos[3 * i + 1], S.dim == 3 ? a.pos[3 * i + 2] : 0.0};
+    for (int k = 0; k < S.dim; k++)
+      if (S.per[k]) {
+        if (x[k] >= S.hi[k]) x[k] -= S.L[k];
+        else if (x[k] < S.lo[k]) x[k] += S.L[k];
+      }
+    int c[3] = {0, 0, 0};
+    for (int k = 0; k < S.dim; k++) {
+      double v = floor(__ddiv_rn(__dsub_rn(x[k], S.lo[k]), S.ell[k]));
+      c[k] = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
+    }
+    int lin = c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]);
+    S.key[i] = cell_key(S, lin);
+    if (sizeof(R) == 8) {
+      S.P.px[i] = (R)x[0]; S.P.py[i] = (R)x[1]; S.P.pz[i] = (R)x[2];
+    } else {
+      S.P.px[i] = (R)(x[0] - (S.lo[0] + c[0] * S.ell[0]));
+      S.P.py[i] = (R)(x[1] - (S.lo[1] + c[1] * S.ell[1]));
+      S.P.pz[i] = S.dim == 3 ? (R)(x[2] - (S.lo[2] + c[2] * S.ell[2])) : R(0);
+    }
+    double v[3] = {0, 0, 0};
+    if (kind == KFLUID) { v[0] = a.vel[3 * i]; v[1] = a.vel[3 * i + 1]; v[2] = a.vel[3 * i + 2]; }
+    else if (kind == KWALL && a.wvel) { v[0] = a.wvel[3 * i]; v[1] = a.wvel[3 * i + 1]; v[2] = a.wvel[3 * i + 2]; }
+    S.P.vx[i] = (R)v[0]; S.P.vy[i] = (R)v[1]; S.P.vz[i] = (R)v[2];
+    S.P.ax[i] = R(0); S.P.ay[i] = R(0); S.P.az[i] = R(0);
+    double T = kind == KWALL ? (a.wtemp ? a.wtemp[i] : (double)NAN) : a.temp[i];
+    S.P.T[i] = (R)T;
+    S.P.H[i] = (kind != KWALL && S.mat[mt].enth) ? (R)enthalpy_of(S.mat, mt, T) : R(0);
+    S.P.m[i] = (R)a.mass[i];
+    S.P.rho[i] = (R)a.dens[i];
+    S.P.mt[i] = mt;
+    S.P.body[i] = kind == KRIGID ? a.body[i] : -1;
+    S.P.slot[i] = a.slot[i];
+    S.P.orig[i] = i;
+    S.where[i] = i;
+    S.prs[i] = R(0);
+    S.dT[i] = R(0);
+    S.vex[i] = R(0); S.vey[i] = R(0); S.vez[i] = R(0);
+    if (a.slot[i] >= 0) S.slot_part[a.slot[i]] = i;
+  }
+}
+
+// overwrite position / velocity / temperature of fluid particles (input order)
+template <class R>
+__global__ void k_import_fluid(Scene<R>* const* sc, const double* pos, const double* vel, const double* temp) {
+  const Scene<R>& S = **sc;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < S.n; o += gridDim.x * blockDim.x) {
+    int i = S.where[o];
+    int mt = S.P.mt[i];
+    if (S.mat[mt].kind != KFLUID) continue;
+    if (pos) {
+      double x[3] = {pos[3 * o], pos[3 * o + 1], S.dim == 3 ? pos[3 * o + 2] : 0.0};
+      for (int k = 0; k < S.dim; k++)
+        if (S.per[k]) {
+          if (x[k] >= S.hi[k]) x[k] -= S.L[k];
+          else if (x[k] < S.lo[k]) x[k] += S.L[k];
+        }
+      if (sizeof(R) == 8) {
+        S.P.px[i] = (R)x[0]; S.P.py[i] = (R)x[1]; S.P.pz[i] = (R)x[2];
+      } else {
+        int c[3] = {0, 0, 0};
+        for (int k = 0; k < S.dim; k++) {
+          double v = floor((x[k] - S.lo[k]) / S.ell[k]);
+          c[k] = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
+        }
+        S.key[i] = cell_key(S, c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]));
+        S.P.px[i] = (R)(x[0] - (S.lo[0] + c[0] * S.ell[0]));
+        S.P.py[i] = (R)(x[1] - (S.lo[1] + c[1] * S.ell[1]));
+        S.P.pz[i] = S.dim == 3 ? (R)(x[2] - (S.lo[2] + c[2] * S.ell[2])) : R(0);
+      }
+    }
+    if (vel) { S.P.vx[i] = (R)vel[3 * o]; S.P.vy[i] = (R)vel[3 * o + 1]; S.P.vz[i] = (R)vel[3 * o + 2]; }
+    if (temp) {
+      S.P.T[i] = (R)temp[o];
+      if (S.mat[mt].enth) S.P.H[i] = (R)enthalpy_of(S.mat, mt, temp[o]);
+    }
+  }
+}
+
+struct ExportArgs {
+  double* f[SPH_F_COUNT];  // double fields (null: not requested)
+  int* fi[SPH_F_COUNT];    // int fields
+  int original;
+};
+
+template <class R>
+__global__ void k_export(Scene<R>* const* sc, ExportArgs a) {
+  const Scene<R>& S = **sc;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
+    int o = a.original ? S.P.orig[i] : i;
+    int mt = S.P.mt[i];
+    int kind = S.mat[mt].kind;
+    if (a.f[SPH_F_POS]) {
+      double x[3];
+      abs_pos<R>(S, i, x);
+      for (int q = 0; q < 3; q++) a.f[SPH_F_POS][3 * o + q] = x[q];
+    }
+    if (a.f[SPH_F_VEL]) {
+      a.f[SPH_F_VEL][3 * o] = S.P.vx[i]; a.f[SPH_F_VEL][3 * o + 1] = S.P.vy[i]; a.f[SPH_F_VEL][3 * o + 2] = S.P.vz[i];
+    }
+    if (a.f[SPH_F_ACC]) {
+      bool fl = kind == KFLUID;
+      a.f[SPH_F_ACC][3 * o] = fl ? (double)S.P.ax[i] : 0.0;
+      a.f[SPH_F_ACC][3 * o + 1] = fl ? (double)S.P.ay[i] : 0.0;
+      a.f[SPH_F_ACC][3 * o + 2] = fl ? (double)S.P.az[i] : 0.0;
+    }
+    if (a.f[SPH_F_RHO]) a.f[SPH_F_RHO][o] = S.P.rho[i];
+    if (a.f[SPH_F_PRES]) a.f[SPH_F_PRES][o] = S.prs[i];
+    if (a.f[SPH_F_TEMP]) a.f[SPH_F_TEMP][o] = S.P.T[i];
+    if (a.f[SPH_F_DTEMP]) a.f[SPH_F_DTEMP][o] = kind == KWALL ? 0.0 : (double)S.dT[i];
+    if (a.fi[SPH_F_MAT]) a.fi[SPH_F_MAT][o] = mt;
+    if (a.fi[SPH_F_BODY]) a.fi[SPH_F_BODY][o] = S.P.body[i];
+    if (a.f[SPH_F_FORCE]) {
+      int sl = S.P.slot[i];
+      bool rg = kind == KRIGID && sl >= 0;
+      for (int q = 0; q < 3; q++) a.f[SPH_F_FORCE][3 * o + q] = rg ? (double)S.fr[3 * sl + q] : 0.0;
+    }
+    if (a.f[SPH_F_VEXT]) {
+      bool b = kind != KFLUID;
+      a.f[SPH_F_VEXT][3 * o] = b ? (double)S.vex[i] : 0.0;
+      a.f[SPH_F_VEXT][3 * o + 1] = b ? (double)S.vey[i] : 0.0;
+      a.f[SPH_F_VEXT][3 * o + 2] = b ? (double)S.vez[i] : 0.0;
+    }
+    if (a.fi[SPH_F_CELL]) a.fi[SPH_F_CELL][o] = key_lin(S, S.key[i]);
+    if (a.f[SPH_F_ENTH]) a.f[SPH_F_ENTH][o] = S.P.H[i];
+  }
+}
+
+// ------------------------------------------------------------------ FP64 diagnostics
+// deterministic two-pass reduction: block partials in a fixed order, then one block
+constexpr int NDIAG = 11;
+template <class R>
+__global__ void __launch_bounds__(256) k_diag_part(Scene<R>* const* sc, double* part) {
+  const Scene<R>& S = **sc;
+  __shared__ double red[NDIAG][256];
+  double v[NDIAG];
+  for (int q = 0; q < NDIAG; q++) v[q] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
+    int mt = S.P.mt[i];
+    const MatD& A = S.mat[mt];
+    if (A.kind == KWALL) continue;
+    double m = (double)S.P.m[i];
+    if (A.kind == KFLUID) {
+      double u[3] = {(double)S.P.vx[i], (double)S.P.vy[i], (double)S.P.vz[i]};
+      double x[3], mu[3] = {m * u[0], m * u[1], m * u[2]}, c[3];
+      abs_pos<R>(S, i, x);
+      cross(x, mu, c);
+      for (int q = 0; q < 3; q++) { v[q] += mu[q]; v[3 + q] += c[q]; }
+      v[6] += 0.5 * m * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      v[9] += 1.0;
+    } else {
+      v[10] += 1.0;
+    }
+    v[7] += A.enth ? m * (double)S.P.H[i] : m * A.cp * (double)S.P.T[i];
+    v[8] += m;
+  }
+  for (int q = 0; q < NDIAG; q++) red[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < NDIAG; q++) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < NDIAG; q++) part[NDIAG * blockIdx.x + q] = red[q][0];
+}
+
+template <class R>
+__global__ void k_diag_fin(Scene<R>* const* sc, const double* part, int nblk, double* out) {
+  const Scene<R>& S = **sc;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double v[NDIAG];
+  for (int q = 0; q < NDIAG; q++) v[q] = 0.0;
+  for (int b = 0; b < nblk; b++)
+    for (int q = 0; q < NDIAG; q++) v[q] += part[NDIAG * b + q];
+  double nb = 0;
+  for (int k = 0; k < *S.K; k++) {
+    if (!S.balive[k]) continue;
+    nb += 1.0;
+    double mk = S.bm[k];
+    const double* u = &S.bu[3 * k];
+    const double* w = &S.bw[3 * k];
+    double mu[3] = {mk * u[0], mk * u[1], mk * u[2]}, c[3], Iw[3];
+    cross(&S.br[3 * k], mu, c);
+    mv(&S.bIw[9 * k], w, Iw);
+    for (int q = 0; q < 3; q++) { v[q] += mu[q]; v[3 + q] += c[q] + Iw[q]; }
+    v[6] += 0.5 * mk * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) + 0.5 * (w[0] * Iw[0] + w[1] * Iw[1] + w[2] * Iw[2]);
+  }
+  for (int q = 0; q < 9; q++) out[q] = v[q];
+  out[9] = S.st[1];
+  out[10] = S.st[2];
+  out[11] = S.st[3];
+  out[12] = v[9];
+  out[13] = v[10];
+  out[14] = nb;
+  out[15] = (double)S.pairs[0];
+}
+
+// ------------------------------------------------------------------ neighbour-set export
+template <class R, int DIM>
+struct NbPol {
+  R *sx, *sy, *sz;
+  int* so;
+  bool active;
+  int idx;
+  R tp[3];
+  int64_t cnt, off;
+  int32_t* list;
+  unsigned long long hits;
+  __device__ void stage(const Scene<R>& S, int j, int lane) {
+    sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
+    so[lane] = S.P.orig[j];
+  }
+  __device__ bool accept(int) const { return true; }
+  __device__ void pair(const Scene<R>&, int k, int, R, R, R, R) {
+    if (list) list[off + cnt] = so[k];
+    cnt++;
+  }
+};
+
+template <class R, int DIM>
+__global__ void __launch_bounds__(128) k_neighbors(Scene<R>* const* sc, int ngroups, int64_t* counts,
+                                                   const int64_t* offs, int32_t* list) {
+  __shared__ R sm[4][3][32];
+  __shared__ int smo[4][32];
+  const Scene<R>& S = **sc;
+  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  NbPol<R, DIM> pol;
+  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2]; pol.so = smo[wib];
+  pol.list = list;
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int g = gw; g < ngroups; g += nw) {
+    Group<R, DIM> G = group_of<R, DIM>(S, g);
+    for (int tb = G.ts; tb < G.te; tb += 32) {
+      int i = tb + lane;
+      bool valid = i < G.te;
+      pol.active = valid;
+      if (!__any_sync(FULL, pol.active)) continue;
+      pol.idx = valid ? i : -1;
+      if (valid) target_pos(S, i, G.cx0, pol.tp);
+      pol.cnt = 0;
+      pol.off = (valid && offs) ? offs[S.P.orig[i]] : 0;
+      pol.hits = 0;
+      traverse<R, DIM>(S, G, pol, lane);
+      if (valid && !offs) counts[S.P.orig[i]] = pol.cnt;
+    }
+  }
+}
+
+static __global__ void k_sort_segments(const int64_t* offs, int n, int32_t* list) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    int64_t a = offs[o], e = offs[o + 1];
+    for (int64_t p = a + 1; p < e; p++) {
+      int32_t v = list[p];
+      int64_t q = p - 1;
+      while (q >= a && list[q] > v) { list[q + 1] = list[q]; q--; }
+      list[q + 1] = v;
+    }
+  }
+}
+
+}  // namespace sph

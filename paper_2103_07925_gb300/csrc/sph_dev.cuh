@@ -1,0 +1,139 @@
+// Device-side data layout of libsph.
+//
+// A scene lives in device memory as a Scene<R> descriptor (R = double for the FP64 path,
+// float for the FP32 path) that holds constants and pointers to structure-of-arrays
+// particle fields.  Particle arrays are kept sorted by cell key (Sec. 3.2: cells of edge
+// >= r_c); each rebin permutes them into the second bank and a one-thread kernel swaps
+// the banks, so a captured CUDA graph can replay every step with fixed arguments.
+//
+// FP64 scenes store absolute positions.  FP32 scenes store positions relative to the
+// origin of the particle's current cell, so that a pair distance is formed from small
+// numbers: d = (o_i - o_j) - (c_j - c_i) * edge.
+//
+// Kernels address many scenes at once (batches): every launch walks a global item space
+// (particles, cells, bodies, warp groups) and finds the scene of an item by binary search
+// in a prefix table.  A single scene is a batch of one.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sph {
+
+constexpr int MAXMAT = 16;
+enum { KFLUID = 0, KRIGID = 1, KWALL = 2 };
+
+struct MatD {  // material constants, FP64
+  int kind, to, enth, src;
+  double rho0, c, eta, cp, kappa, Tt, L, w, p0;
+};
+
+template <class R>
+struct MatR {  // material constants in the working precision (pair sums)
+  int kind, enth;
+  R rho0, c2, eta, cp, kappa, inv_p0;
+};
+
+template <class R>
+struct PBank {  // particle fields (one bank)
+  R *px, *py, *pz;     // position (FP64: absolute; FP32: relative to the cell origin)
+  R *vx, *vy, *vz;     // velocity (fluid u, rigid u_r, wall prescribed velocity)
+  R *ax, *ay, *az;     // fluid acceleration; rigid: kinematic acceleration used by Eq. R4
+  R *rho, *T, *H, *m;  // density, temperature (walls: prescribed or NaN), enthalpy, mass
+  int *mt, *body, *slot, *orig;  // material, body id, rigid slot, input index
+};
+
+template <class R>
+struct Scene {
+  // ---------------------------------------------------------------- constants
+  int dim, n, nmat, key_order, G;
+  int ncell[3], ncells, ngroups, ngx, ncblk;
+  int per[3];
+  double lo[3], hi[3], L[3], ell[3];
+  R ellR[3], LR[3];
+  double g[3];
+  R gR[3];
+  double h, rc, rc2, dx;
+  R rc2R, inv_h, sig_w, sig_dw, w0;  // W = sig_w w(q), dW/dr = sig_dw w'(q)
+  double kc, dc;
+  R kcR, dcR, dxR;
+  double src_Q, src_r, src_v[3], src_x0[3], src_depth, src_ztop;
+  int dt_mode, rebin_interval, has_transition, has_enthalpy, has_source, any_heat;
+  double dt_fixed, dt_cond;  // dt_cond: min of the velocity-independent conditions
+  double cmax;
+  MatD mat[MAXMAT];
+  MatR<R> matR[MAXMAT];
+  // ---------------------------------------------------------------- particles
+  PBank<R> P, Q;       // current and alternate bank
+  R *prs, *dT;         // pressure, rate (not permuted: recomputed every evaluation)
+  R *vex, *vey, *vez;  // extrapolated velocity of wall and rigid particles
+  int* key;            // cell key of each (sorted) particle
+  int* where;          // input index -> current sorted index
+  // rebin scratch
+  int *tkey, *tloc, *bucket, *perm, *tshift;
+  // ---------------------------------------------------------------- cells
+  int *cstart;         // ncells + 1 entries, by key
+  int *ccount;         // ncells, kept at zero between rebins
+  int *cblk;           // block sums of the counting scan
+  const int *lin2key;  // Morton rank of a row-major cell (null for row-major keys)
+  const int *key2lin;
+  // ---------------------------------------------------------------- bodies (FP64)
+  int Kcap, nslot;
+  int* K;              // device: bodies in use (ids 0..K-1)
+  double *bm, *br, *bq, *bu, *bw, *ba, *bal, *bf, *bt, *bIb, *bIbinv, *bIw;
+  int *balive, *bstart, *bend;  // slot ranges of each body
+  double* rb;          // body-frame offset of every slot (3 per slot)
+  int* slot_part;      // slot -> current sorted particle index
+  R* fr;               // force on every slot (3 per slot)
+  // ---------------------------------------------------------------- per-step state
+  double* st;          // [0] dt [1] time [2] step [3] dt of last step
+  unsigned long long* umax;  // bits of max |u| over fluid particles (FP64, non-negative)
+  int* status;         // [0] non-finite flag, [1] relabel count, [2] capacity error
+  int* pfx1;           // prefix tables of this scene alone (6 x 2 ints)
+  Scene<R>** self;     // device array holding the address of this descriptor
+  unsigned long long* pairs;  // [0] force-sweep pairs of the last evaluation
+  double* red;         // scratch for deterministic FP64 reductions
+};
+
+// batch view handed to every kernel
+template <class R>
+struct BatchView {
+  Scene<R>* const* sc;  // device array of pointers to the scene descriptors
+  int nsc;
+  const int* pfx_part;   // nsc+1 prefix of particle counts
+  const int* pfx_cell;   // cells
+  const int* pfx_grp;    // warp groups of the sweeps
+  const int* pfx_body;   // body capacities
+  const int* pfx_cblk;   // scan blocks of 1024 cells
+  const int* pfx_slot;   // rigid slots
+};
+
+__device__ __forceinline__ int find_scene(const int* __restrict__ pfx, int nsc, int g) {
+  int lo = 0, hi = nsc - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(pfx + mid) <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------------------- Morton
+__host__ __device__ inline uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
+  v &= 0x1fffff;
+  v = (v | v << 32) & 0x1f00000000ffffULL;
+  v = (v | v << 16) & 0x1f0000ff0000ffULL;
+  v = (v | v << 8) & 0x100f00f00f00f00fULL;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+  v = (v | v << 2) & 0x1249249249249249ULL;
+  return v;
+}
+__host__ __device__ inline uint64_t spread2(uint64_t v) {  // 32 bits -> every second bit
+  v &= 0xffffffffULL;
+  v = (v | v << 16) & 0x0000ffff0000ffffULL;
+  v = (v | v << 8) & 0x00ff00ff00ff00ffULL;
+  v = (v | v << 4) & 0x0f0f0f0f0f0f0f0fULL;
+  v = (v | v << 2) & 0x3333333333333333ULL;
+  v = (v | v << 1) & 0x5555555555555555ULL;
+  return v;
+}
+
+}  // namespace sph

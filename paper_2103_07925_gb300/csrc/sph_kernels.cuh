@@ -1,0 +1,1193 @@
+// CUDA kernels of the SPH interaction sweep (sm_103a).  Templated on the working
+// precision R (double: FP64 path; float: FP32 path with FP64 bodies) and the dimension.
+//
+// Step order (Sec. 3.7, velocity-Verlet kick-drift-kick):
+//   k_umax, k_dt            time step, Eq. timestepcond (or fixed)
+//   k_body_kick_drift       u_k, w_k half kick; r_k drift; q_k <- q_inc o q_k
+//   k_kick_drift            fluid half kick + drift; rigid particles follow their body
+//   k_bin .. k_flip         cell binning: counting sort by cell key, stable (Sec. 3.2)
+//   k_density               Eq. densum + Eq. eos                       (pair sweep 1)
+//   k_extrap                wall / rigid extrapolation (Adami 2012)     (pair sweep 2)
+//   k_force                 Eq. momentum, couplingforce, contactforce,
+//                           heat_equation                               (pair sweep 3)
+//   k_body_reduce           Eqs. procwise_force / global_force, body accelerations,
+//                           final body kick                             (FP64)
+//   k_final                 T (or H) update, final fluid kick, rigid velocities
+//   k_end_step              time and step counters
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sph_dev.cuh"
+
+namespace sph {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <class R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return 1.0 / sqrt(x); }
+template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+
+// quintic spline (Morris 1997), polynomial part: w(q) and dw/dq, valid for q < 3
+template <class R>
+__device__ __forceinline__ void quintic(R q, R& w, R& dw) {
+  R t3 = R(3) - q;
+  R t2 = fmax(R(2) - q, R(0));
+  R t1 = fmax(R(1) - q, R(0));
+  R a2 = t3 * t3, b2 = t2 * t2, c2 = t1 * t1;
+  R a4 = a2 * a2, b4 = b2 * b2, c4 = c2 * c2;
+  w = a4 * t3 - R(6) * b4 * t2 + R(15) * c4 * t1;
+  dw = R(-5) * a4 + R(30) * b4 - R(75) * c4;
+}
+template <class R>
+__device__ __forceinline__ R quintic_w(R q) {
+  R t3 = R(3) - q;
+  R t2 = fmax(R(2) - q, R(0));
+  R t1 = fmax(R(1) - q, R(0));
+  R a2 = t3 * t3, b2 = t2 * t2, c2 = t1 * t1;
+  return a2 * a2 * t3 - R(6) * b2 * b2 * t2 + R(15) * c2 * c2 * t1;
+}
+template <class R>
+__device__ __forceinline__ R quintic_dw(R q) {
+  R t3 = R(3) - q;
+  R t2 = fmax(R(2) - q, R(0));
+  R t1 = fmax(R(1) - q, R(0));
+  R a2 = t3 * t3, b2 = t2 * t2, c2 = t1 * t1;
+  return R(-5) * a2 * a2 + R(30) * b2 * b2 - R(75) * c2 * c2;
+}
+
+__device__ __forceinline__ void qrot(const double* q, double* Rm) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  Rm[0] = 1.0 - 2.0 * (y * y + z * z); Rm[1] = 2.0 * (x * y - w * z);       Rm[2] = 2.0 * (x * z + w * y);
+  Rm[3] = 2.0 * (x * y + w * z);       Rm[4] = 1.0 - 2.0 * (x * x + z * z); Rm[5] = 2.0 * (y * z - w * x);
+  Rm[6] = 2.0 * (x * z - w * y);       Rm[7] = 2.0 * (y * z + w * x);       Rm[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+__device__ __forceinline__ void mv(const double* M, const double* v, double* o) {
+  o[0] = M[0] * v[0] + M[1] * v[1] + M[2] * v[2];
+  o[1] = M[3] * v[0] + M[4] * v[1] + M[5] * v[2];
+  o[2] = M[6] * v[0] + M[7] * v[1] + M[8] * v[2];
+}
+__device__ __forceinline__ void mtv(const double* M, const double* v, double* o) {
+  o[0] = M[0] * v[0] + M[3] * v[1] + M[6] * v[2];
+  o[1] = M[1] * v[0] + M[4] * v[1] + M[7] * v[2];
+  o[2] = M[2] * v[0] + M[5] * v[1] + M[8] * v[2];
+}
+__device__ __forceinline__ void cross(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// cell key of a row-major cell index
+template <class R>
+__device__ __forceinline__ int cell_key(const Scene<R>& S, int lin) {
+  return S.lin2key ? __ldg(S.lin2key + lin) : lin;
+}
+template <class R>
+__device__ __forceinline__ int key_lin(const Scene<R>& S, int key) {
+  return S.key2lin ? __ldg(S.key2lin + key) : key;
+}
+template <class R>
+__device__ __forceinline__ void lin_xyz(const Scene<R>& S, int lin, int& cx, int& cy, int& cz) {
+  cx = lin % S.ncell[0];
+  int r = lin / S.ncell[0];
+  cy = r % S.ncell[1];
+  cz = r / S.ncell[1];
+}
+
+// absolute FP64 position of particle i (sorted index) from the current bank
+template <class R>
+__device__ __forceinline__ void abs_pos(const Scene<R>& S, int i, double* x);
+template <>
+__device__ __forceinline__ void abs_pos<double>(const Scene<double>& S, int i, double* x) {
+  x[0] = S.P.px[i]; x[1] = S.P.py[i]; x[2] = S.P.pz[i];
+}
+template <>
+__device__ __forceinline__ void abs_pos<float>(const Scene<float>& S, int i, double* x) {
+  int cx, cy, cz;
+  lin_xyz(S, key_lin(S, S.key[i]), cx, cy, cz);
+  x[0] = S.lo[0] + cx * S.ell[0] + (double)S.P.px[i];
+  x[1] = S.lo[1] + cy * S.ell[1] + (double)S.P.py[i];
+  x[2] = S.dim == 3 ? S.lo[2] + cz * S.ell[2] + (double)S.P.pz[i] : 0.0;
+}
+
+// store an absolute FP64 position into particle i's slot of the current bank
+template <class R>
+__device__ __forceinline__ void store_pos(const Scene<R>& S, int i, const double* x);
+template <>
+__device__ __forceinline__ void store_pos<double>(const Scene<double>& S, int i, const double* x) {
+  double y[3] = {x[0], x[1], x[2]};
+  for (int k = 0; k < S.dim; k++)
+    if (S.per[k]) {
+      if (y[k] >= S.hi[k]) y[k] -= S.L[k];
+      else if (y[k] < S.lo[k]) y[k] += S.L[k];
+    }
+  S.P.px[i] = y[0]; S.P.py[i] = y[1]; S.P.pz[i] = y[2];
+}
+template <>
+__device__ __forceinline__ void store_pos<float>(const Scene<float>& S, int i, const double* x) {
+  int c[3];
+  lin_xyz(S, key_lin(S, S.key[i]), c[0], c[1], c[2]);
+  float o[3] = {0.f, 0.f, 0.f};
+  for (int k = 0; k < S.dim; k++) {
+    double v = x[k] - (S.lo[k] + c[k] * S.ell[k]);
+    if (S.per[k]) v -= S.L[k] * nearbyint((v - 0.5 * S.ell[k]) / S.L[k]);
+    o[k] = (float)v;
+  }
+  S.P.px[i] = o[0]; S.P.py[i] = o[1]; S.P.pz[i] = o[2];
+}
+
+// ============================================================================ time step
+template <class R>
+__global__ void k_umax(BatchView<R> B) {
+  int total = __ldg(B.pfx_part + B.nsc);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int s = find_scene(B.pfx_part, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    if (S.dt_mode == 0) continue;
+    int i = g - __ldg(B.pfx_part + s);
+    if (S.matR[S.P.mt[i]].kind != KFLUID) continue;
+    double ux = S.P.vx[i], uy = S.P.vy[i], uz = S.P.vz[i];
+    double u = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz)));
+    // bits of a non-negative double order like unsigned integers, so the maximum is exact
+    if (u > 0.0) atomicMax(S.umax, (unsigned long long)__double_as_longlong(u));
+  }
+}
+
+template <class R>
+__global__ void k_dt(BatchView<R> B) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B.nsc) return;
+  Scene<R>& S = *B.sc[s];
+  double dt = S.dt_fixed;
+  if (S.dt_mode == 1) {
+    double umax = __longlong_as_double((long long)*S.umax);
+    dt = S.dt_cond;
+    if (S.cmax + umax > 0.0) dt = fmin(dt, 0.25 * S.h / (S.cmax + umax));
+    if (!(dt < 1e300)) dt = S.dt_fixed;
+  }
+  *S.umax = 0ull;
+  S.st[0] = dt;
+  S.pairs[0] = 0ull;
+}
+
+// ============================================================================ kick + drift
+template <class R>
+__global__ void k_body_kick_drift(BatchView<R> B) {
+  int total = __ldg(B.pfx_body + B.nsc);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int s = find_scene(B.pfx_body, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    int k = g - __ldg(B.pfx_body + s);
+    if (k >= *S.K || !S.balive[k]) continue;
+    double dt = S.st[0], half = 0.5 * dt, phi[3];
+    for (int q = 0; q < 3; q++) {
+      S.bu[3 * k + q] = S.bu[3 * k + q] + half * S.ba[3 * k + q];
+      S.bw[3 * k + q] = S.bw[3 * k + q] + half * S.bal[3 * k + q];
+      S.br[3 * k + q] = S.br[3 * k + q] + dt * S.bu[3 * k + q];
+      phi[q] = dt * S.bw[3 * k + q];
+    }
+    // transition quaternion of the increment phi = dt w^{n+1/2}; q^{n+1} = q_inc o q^n
+    double ang = sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
+    double a[4] = {1.0, 0.0, 0.0, 0.0};
+    if (ang > 0.0) {
+      double sh = sin(0.5 * ang) / ang;
+      a[0] = cos(0.5 * ang); a[1] = sh * phi[0]; a[2] = sh * phi[1]; a[3] = sh * phi[2];
+    }
+    double* b = &S.bq[4 * k];
+    double w = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    double x = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    double y = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    double z = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    double nq = sqrt(w * w + x * x + y * y + z * z);
+    b[0] = w / nq; b[1] = x / nq; b[2] = y / nq; b[3] = z / nq;
+  }
+}
+
+// fluid: u += dt/2 a, r += dt u;  rigid: r_r = r_k + R r_rk, u_r = u_k + w x R r_rk and the
+// kinematic acceleration a_k + alpha_k x r_rk + w x (w x r_rk) used by the extrapolation
+template <class R>
+__global__ void k_kick_drift(BatchView<R> B) {
+  int total = __ldg(B.pfx_part + B.nsc);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int s = find_scene(B.pfx_part, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    int i = g - __ldg(B.pfx_part + s);
+    int kind = S.matR[S.P.mt[i]].kind;
+    if (kind == KFLUID) {
+      R dt = (R)S.st[0], half = R(0.5) * dt;
+      R ux = S.P.vx[i] + half * S.P.ax[i];
+      R uy = S.P.vy[i] + half * S.P.ay[i];
+      R uz = S.P.vz[i] + half * S.P.az[i];
+      S.P.vx[i] = ux; S.P.vy[i] = uy; S.P.vz[i] = uz;
+      if (sizeof(R) == 8) {
+        double x[3] = {(double)S.P.px[i] + (double)dt * ux, (double)S.P.py[i] + (double)dt * uy,
+                       (double)S.P.pz[i] + (double)dt * uz};
+        store_pos<R>(S, i, x);
+      } else {
+        S.P.px[i] = S.P.px[i] + dt * ux;
+        S.P.py[i] = S.P.py[i] + dt * uy;
+        S.P.pz[i] = S.P.pz[i] + dt * uz;
+      }
+    } else if (kind == KRIGID) {
+      int k = S.P.body[i], sl = S.P.slot[i];
+      double Rm[9], rr[3], t1[3], t2[3], t3[3], x[3];
+      qrot(&S.bq[4 * k], Rm);
+      mv(Rm, &S.rb[3 * sl], rr);
+      const double* w = &S.bw[3 * k];
+      cross(w, rr, t2);
+      for (int q = 0; q < 3; q++) x[q] = S.br[3 * k + q] + rr[q];
+      store_pos<R>(S, i, x);
+      S.P.vx[i] = (R)(S.bu[3 * k] + t2[0]);
+      S.P.vy[i] = (R)(S.bu[3 * k + 1] + t2[1]);
+      S.P.vz[i] = (R)(S.bu[3 * k + 2] + t2[2]);
+      cross(&S.bal[3 * k], rr, t1);
+      cross(w, t2, t3);
+      S.P.ax[i] = (R)(S.ba[3 * k] + t1[0] + t3[0]);
+      S.P.ay[i] = (R)(S.ba[3 * k + 1] + t1[1] + t3[1]);
+      S.P.az[i] = (R)(S.ba[3 * k + 2] + t1[2] + t3[2]);
+    }
+  }
+}
+
+// ============================================================================ binning
+// Counting sort of the particles by cell key (one digit spanning the whole key): count,
+// scan, scatter, then restore input order inside each cell so that the result equals a
+// stable sort.  Skipped (early exit) on steps that are not rebin steps.
+template <class R>
+__device__ __forceinline__ bool rebin_now(const Scene<R>& S) {
+  long long step = (long long)S.st[2];
+  return S.rebin_interval <= 1 || (step % S.rebin_interval) == 0;
+}
+
+template <class R>
+__global__ void k_bin(BatchView<R> B, int force) {
+  int total = __ldg(B.pfx_part + B.nsc);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int s = find_scene(B.pfx_part, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    if (!force && !rebin_now(S)) continue;
+    int i = g - __ldg(B.pfx_part + s);
+    int c[3] = {0, 0, 0};
+    int shift = 0;
+    if (sizeof(R) == 8) {
+      double x[3] = {(double)S.P.px[i], (double)S.P.py[i], (double)S.P.pz[i]};
+      for (int k = 0; k < S.dim; k++) {
+        double v = floor(__ddiv_rn(__dsub_rn(x[k], S.lo[k]), S.ell[k]));
+        int ci = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
+        c[k] = ci;
+      }
+    } else {
+      // cell-relative positions: new cell = old cell + floor(offset / edge)
+      int co[3];
+      lin_xyz(S, key_lin(S, S.key[i]), co[0], co[1], co[2]);
+      R o[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
+      for (int k = 0; k < S.dim; k++) {
+        int d = (int)floorf((float)o[k] / (float)S.ellR[k]);
+        int cu = co[k] + d;
+        int cn;
+        if (S.per[k]) cn = ((cu % S.ncell[k]) + S.ncell[k]) % S.ncell[k];
+        else cn = cu < 0 ? 0 : (cu >= S.ncell[k] ? S.ncell[k] - 1 : cu);
+        c[k] = cn;
+        // offset correction applied by the permutation: o -= (c_new_unwrapped - c_old) * edge
+        int dd = S.per[k] ? d : cn - co[k];
+        dd = dd < -127 ? -127 : (dd > 127 ? 127 : dd);
+        shift |= (dd & 0xff) << (8 * k);
+      }
+    }
+    int lin = c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]);
+    int key = cell_key(S, lin);
+    S.tkey[i] = key;
+    S.tshift[i] = shift;
+    S.tloc[i] = atomicAdd(&S.ccount[key], 1);
+  }
+}
+
+// block sums of cell counts (blocks of 1024 cells, never straddling scenes)
+template <class R>
+__global__ void __launch_bounds__(1024) k_scan_blocks(BatchView<R> B, int force) {
+  int total = __ldg(B.pfx_cblk + B.nsc);
+  __shared__ int red[32];
+  for (int blk = blockIdx.x; blk < total; blk += gridDim.x) {
+    int s = find_scene(B.pfx_cblk, B.nsc, blk);
+    const Scene<R>& S = *B.sc[s];
+    if (!force && !rebin_now(S)) continue;
+    int b = blk - __ldg(B.pfx_cblk + s);
+    int c = b * 1024 + threadIdx.x;
+    int v = c < S.ncells ? S.ccount[c] : 0;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int t = red[threadIdx.x];
+      for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+      if (threadIdx.x == 0) S.cblk[b] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// exclusive scan of the block sums of each scene (one block per scene)
+template <class R>
+__global__ void __launch_bounds__(1024) k_scan_top(BatchView<R> B, int force) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  for (int s = blockIdx.x; s < B.nsc; s += gridDim.x) {
+    const Scene<R>& S = *B.sc[s];
+    if (!force && !rebin_now(S)) continue;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < S.ncblk; base += 1024) {
+      int idx = base + threadIdx.x;
+      int v = idx < S.ncblk ? S.cblk[idx] : 0;
+      int x = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL, x, o);
+        if ((threadIdx.x & 31) >= o) x += y;
+      }
+      if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        int t = wsum[threadIdx.x], u = t;
+        for (int o = 1; o < 32; o <<= 1) {
+          int y = __shfl_up_sync(FULL, u, o);
+          if (threadIdx.x >= o) u += y;
+        }
+        wsum[threadIdx.x] = u - t;
+      }
+      __syncthreads();
+      int excl = carry + wsum[threadIdx.x >> 5] + x - v;
+      if (idx < S.ncblk) S.cblk[idx] = excl;
+      __syncthreads();
+      if (threadIdx.x == 1023) carry = excl + v;
+      __syncthreads();
+    }
+  }
+}
+
+// cell starts: exclusive scan inside each block plus the block offset; resets the counts
+template <class R>
+__global__ void __launch_bounds__(1024) k_scan_cells(BatchView<R> B, int force) {
+  int total = __ldg(B.pfx_cblk + B.nsc);
+  __shared__ int wsum[32];
+  for (int blk = blockIdx.x; blk < total; blk += gridDim.x) {
+    int s = find_scene(B.pfx_cblk, B.nsc, blk);
+    const Scene<R>& S = *B.sc[s];
+    if (!force && !rebin_now(S)) continue;
+    int b = blk - __ldg(B.pfx_cblk + s);
+    int c = b * 1024 + threadIdx.x;
+    int v = c < S.ncells ? S.ccount[c] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(FULL, x, o);
+      if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int t = wsum[threadIdx.x], u = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL, u, o);
+        if (threadIdx.x >= o) u += y;
+      }
+      wsum[threadIdx.x] = u - t;
+    }
+    __syncthreads();
+    if (c < S.ncells) {
+      S.cstart[c] = S.cblk[b] + wsum[threadIdx.x >> 5] + x - v;
+      S.ccount[c] = 0;
+    }
+    if (c == S.ncells - 1) S.cstart[S.ncells] = S.n;
+    __syncthreads();
+  }
+}
+
+template <class R>
+__global__ void k_scatter(BatchView<R> B, int force) {
+  int total = __ldg(B.pfx_part + B.nsc);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int s = find_scene(B.pfx_part, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    if (!force && !rebin_now(S)) continue;
+    int i = g - __ldg(B.pfx_part + s);
+    S.bucket[S.cstart[S.tkey[i]] + S.tloc[i]] = i;
+  }
+}
+
+// inside each cell, order the entries by their previous index (one warp per cell):
+// rank = number of entries with a smaller previous index
+template <class R>
+__global__ void k_rank(BatchView<R> B, int force) {
+  int total = __ldg(B.pfx_cell + B.nsc);
+  int lane = threadIdx.x & 31;
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int g = gw; g < total; g += nw) {
+    int s = find_scene(B.pfx_cell, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    if (!force && !rebin_now(S)) continue;
+    int c = g - __ldg(B.pfx_cell + s);
+    int a = S.cstart[c], e = S.cstart[c + 1];
+    int cnt = e - a;
+    if (cnt == 0) continue;
+    if (cnt < 0 || a < 0 || e > S.n) {  // inconsistent table: flag it, never loop on it
+      S.status[3] = 1;
+      continue;
+    }
+    if (cnt == 1) {
+      if (lane == 0) S.perm[a] = S.bucket[a];
+      continue;
+    }
+    for (int t0 = 0; t0 < cnt; t0 += 32) {
+      int t = t0 + lane;
+      int v = t < cnt ? S.bucket[a + t] : 0x7fffffff;
+      int rank = 0;
+      for (int u0 = 0; u0 < cnt; u0 += 32) {
+        int w = (u0 + lane) < cnt ? S.bucket[a + u0 + lane] : 0x7fffffff;
+        int lim = min(32, cnt - u0);
+        for (int k = 0; k < lim; k++) rank += (__shfl_sync(FULL, w, k) < v);
+      }
+      if (t < cnt) S.perm[a + rank] = v;
+    }
+  }
+}
+
+template <class R>
+__global__ void k_permute(BatchView<R> B, int force) {
+  int total = __ldg(B.pfx_part + B.nsc);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int s = find_scene(B.pfx_part, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    if (!force && !rebin_now(S)) continue;
+    int j = g - __ldg(B.pfx_part + s);
+    int i = S.perm[j];
+    const PBank<R>& P = S.P;
+    const PBank<R>& Q = S.Q;
+    R px = P.px[i], py = P.py[i], pz = P.pz[i];
+    if (sizeof(R) == 4) {
+      int sh = S.tshift[i];
+      int d0 = (int)(signed char)(sh & 0xff), d1 = (int)(signed char)((sh >> 8) & 0xff),
+          d2 = (int)(signed char)((sh >> 16) & 0xff);
+      px = px - (R)d0 * S.ellR[0];
+      py = py - (R)d1 * S.ellR[1];
+      pz = pz - (R)d2 * S.ellR[2];
+    }
+    Q.px[j] = px; Q.py[j] = py; Q.pz[j] = pz;
+    Q.vx[j] = P.vx[i]; Q.vy[j] = P.vy[i]; Q.vz[j] = P.vz[i];
+    Q.ax[j] = P.ax[i]; Q.ay[j] = P.ay[i]; Q.az[j] = P.az[i];
+    Q.rho[j] = P.rho[i]; Q.T[j] = P.T[i]; Q.H[j] = P.H[i]; Q.m[j] = P.m[i];
+    Q.mt[j] = P.mt[i];
+    int b = P.body[i], sl = P.slot[i], o = P.orig[i];
+    Q.body[j] = b; Q.slot[j] = sl; Q.orig[j] = o;
+    S.key[j] = S.tkey[i];
+    S.where[o] = j;
+    if (sl >= 0) S.slot_part[sl] = j;
+  }
+}
+
+template <class R>
+__global__ void k_flip(BatchView<R> B, int force) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B.nsc) return;
+  Scene<R>& S = *B.sc[s];
+  if (!force && !rebin_now(S)) return;
+  PBank<R> t = S.P;
+  S.P = S.Q;
+  S.Q = t;
+}
+
+// ============================================================================ pair sweeps
+// One warp per target group (G consecutive cells along x, or one cell).  For each chunk of
+// <= 32 targets the warp visits the neighbour cells; each chunk of <= 32 candidates is
+// staged in shared memory, every lane tests all candidates against its target (hit mask,
+// r^2 < r_c^2), then processes its own hits.
+
+template <class R, int DIM>
+struct Group {
+  int cx0, cy, cz, ncx, ts, te;
+};
+
+template <class R, int DIM>
+__device__ __forceinline__ Group<R, DIM> group_of(const Scene<R>& S, int grp) {
+  Group<R, DIM> G;
+  if (S.key2lin) {  // Morton keys: one cell per group
+    int lin = __ldg(S.key2lin + grp);
+    lin_xyz(S, lin, G.cx0, G.cy, G.cz);
+    G.ncx = 1;
+    G.ts = max(S.cstart[grp], 0);
+    G.te = min(S.cstart[grp + 1], S.n);
+  } else {
+    int gx = grp % S.ngx, r = grp / S.ngx;
+    G.cy = r % S.ncell[1];
+    G.cz = r / S.ncell[1];
+    G.cx0 = gx * S.G;
+    G.ncx = min(S.G, S.ncell[0] - G.cx0);
+    int lin0 = G.cx0 + S.ncell[0] * (G.cy + S.ncell[1] * G.cz);
+    G.ts = max(S.cstart[lin0], 0);
+    G.te = min(S.cstart[lin0 + G.ncx], S.n);
+  }
+  return G;
+}
+
+// target position in the frame of the group: FP64 absolute; FP32 relative to the origin
+// of the group's first cell
+template <class R>
+__device__ __forceinline__ void target_pos(const Scene<R>& S, int i, int cx0, R* p) {
+  p[0] = S.P.px[i]; p[1] = S.P.py[i]; p[2] = S.P.pz[i];
+  if (sizeof(R) == 4 && S.G > 1 && !S.key2lin) {
+    int lin = S.key[i];
+    int cx = lin % S.ncell[0];
+    p[0] += (R)(cx - cx0) * S.ellR[0];
+  }
+}
+
+// neighbour cell (ox, dy, dz) of the group: key and the shift subtracted from p_i - p_j
+template <class R, int DIM>
+__device__ __forceinline__ bool stencil_cell(const Scene<R>& S, const Group<R, DIM>& G, int ox, int dy,
+                                             int dz, int& key, R* shift) {
+  int c[3] = {G.cx0 + ox, G.cy + dy, G.cz + dz};
+  int off[3] = {ox, dy, dz};
+  for (int k = 0; k < DIM; k++) {
+    shift[k] = R(0);
+    if (c[k] < 0 || c[k] >= S.ncell[k]) {
+      if (!S.per[k]) return false;
+      int w = c[k] < 0 ? 1 : -1;  // image of the cell inside the box
+      c[k] += w * S.ncell[k];
+      if (sizeof(R) == 8) shift[k] = w > 0 ? -S.LR[k] : S.LR[k];
+    }
+    if (sizeof(R) == 4) shift[k] = (R)off[k] * S.ellR[k];
+  }
+  if (DIM == 2) { c[2] = 0; shift[2] = R(0); }
+  int lin = c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]);
+  key = cell_key(S, lin);
+  return true;
+}
+
+template <class R, int DIM>
+__device__ __forceinline__ R dist2(R dx, R dy, R dz) {
+  if (DIM == 2) return dx * dx + dy * dy;
+  return (dx * dx + dy * dy) + dz * dz;
+}
+
+// FP64 path: the squared distance of the predicate is formed without contraction so that
+// neighbour sets match a plain IEEE evaluation bit for bit
+template <int DIM>
+__device__ __forceinline__ double dist2_exact(double dx, double dy, double dz) {
+  double s = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  if (DIM == 3) s = __dadd_rn(s, __dmul_rn(dz, dz));
+  return s;
+}
+
+template <class R, int DIM>
+__device__ __forceinline__ R pair_r2(R dx, R dy, R dz) {
+  if (sizeof(R) == 8) return (R)dist2_exact<DIM>((double)dx, (double)dy, (double)dz);
+  return dist2<R, DIM>(dx, dy, dz);
+}
+
+template <class R>
+__device__ __forceinline__ R dsub(R a, R b) {
+  if (sizeof(R) == 8) return (R)__dsub_rn((double)a, (double)b);
+  return a - b;
+}
+
+// generic traversal.  Pol provides: stage(S, j, lane), active, tp[3], idx,
+// bool accept(k) (candidate filter for the hit mask), pair(S, k, j, dx, dy, dz, r2).
+template <class R, int DIM, class Pol>
+__device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>& G, Pol& pol, int lane) {
+  const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
+  const R rc2 = S.rc2R;
+  for (int dz = zlo; dz <= zhi; dz++)
+    for (int dy = -1; dy <= 1; dy++)
+      for (int ox = -1; ox <= G.ncx; ox++) {
+        int key;
+        R sh[3];
+        if (!stencil_cell<R, DIM>(S, G, ox, dy, dz, key, sh)) continue;
+        int cs = max(S.cstart[key], 0), ce = min(S.cstart[key + 1], S.n);
+        for (int cb = cs; cb < ce; cb += 32) {
+          int cnt = min(32, ce - cb);
+          __syncwarp();
+          if (lane < cnt) pol.stage(S, cb + lane, lane);
+          __syncwarp();
+          unsigned mask = 0u;
+          if (pol.active) {
+            for (int k = 0; k < cnt; k++) {
+              R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sh[0]);
+              R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
+              R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
+              R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
+              if (r2 < rc2 && cb + k != pol.idx && pol.accept(k)) mask |= 1u << k;
+            }
+          }
+          pol.hits += __popc(mask);
+          while (mask) {
+            int k = __ffs(mask) - 1;
+            mask &= mask - 1;
+            R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sh[0]);
+            R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
+            R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
+            R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
+            pol.pair(S, k, cb + k, dx, dy2, dz2, r2);
+          }
+        }
+      }
+}
+
+// ---------------------------------------------------------------- sweep 1: density (Eq. densum, eos)
+template <class R, int DIM>
+struct DensityPol {
+  R *sx, *sy, *sz;
+  bool active;
+  int idx;
+  R tp[3];
+  R acc;
+  unsigned long long hits;
+  __device__ void stage(const Scene<R>& S, int j, int lane) {
+    sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
+  }
+  __device__ bool accept(int) const { return true; }
+  __device__ void pair(const Scene<R>& S, int, int, R, R, R, R r2) {
+    R r = sqrt(r2);
+    acc += quintic_w<R>(r * S.inv_h);
+  }
+};
+
+template <class R, int DIM>
+__global__ void __launch_bounds__(128) k_density(BatchView<R> B) {
+  __shared__ R sm[4][3][32];
+  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  DensityPol<R, DIM> pol;
+  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
+  int total = __ldg(B.pfx_grp + B.nsc);
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int g = gw; g < total; g += nw) {
+    int s = find_scene(B.pfx_grp, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    Group<R, DIM> G = group_of<R, DIM>(S, g - __ldg(B.pfx_grp + s));
+    for (int tb = G.ts; tb < G.te; tb += 32) {
+      int i = tb + lane;
+      bool valid = i < G.te;
+      pol.active = valid && S.matR[S.P.mt[i]].kind == KFLUID;
+      if (!__any_sync(FULL, pol.active)) continue;
+      pol.idx = valid ? i : -1;
+      if (valid) target_pos(S, i, G.cx0, pol.tp);
+      pol.acc = R(0);
+      pol.hits = 0;
+      traverse<R, DIM>(S, G, pol, lane);
+      if (pol.active) {
+        const MatR<R>& A = S.matR[S.P.mt[i]];
+        R rho = S.P.m[i] * (S.w0 + S.sig_w * pol.acc);
+        S.P.rho[i] = rho;
+        S.prs[i] = A.c2 * (rho - A.rho0);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- sweep 2: extrapolation (Adami 2012)
+template <class R, int DIM>
+struct ExtrapPol {
+  R *sx, *sy, *sz, *sp, *sr, *su, *sv, *sw;
+  int* sk;
+  bool active;
+  int idx;
+  R tp[3];
+  R S0, P0, Rv[3], U[3];
+  unsigned long long hits;
+  __device__ void stage(const Scene<R>& S, int j, int lane) {
+    sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
+    int kind = S.matR[S.P.mt[j]].kind;
+    sk[lane] = kind;
+    if (kind == KFLUID) {
+      sp[lane] = S.prs[j]; sr[lane] = S.P.rho[j];
+      su[lane] = S.P.vx[j]; sv[lane] = S.P.vy[j]; sw[lane] = S.P.vz[j];
+    }
+  }
+  __device__ bool accept(int k) const { return sk[k] == KFLUID; }
+  __device__ void pair(const Scene<R>& S, int k, int, R dx, R dy, R dz, R r2) {
+    R r = sqrt(r2);
+    R W = quintic_w<R>(r * S.inv_h);
+    S0 += W;
+    P0 += sp[k] * W;
+    R rw = sr[k] * W;
+    Rv[0] += rw * dx; Rv[1] += rw * dy; Rv[2] += rw * dz;
+    U[0] += su[k] * W; U[1] += sv[k] * W; U[2] += sw[k] * W;
+  }
+};
+
+template <class R, int DIM>
+__global__ void __launch_bounds__(128) k_extrap(BatchView<R> B) {
+  __shared__ R sm[4][8][32];
+  __shared__ int smk[4][32];
+  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  ExtrapPol<R, DIM> pol;
+  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2]; pol.sp = sm[wib][3];
+  pol.sr = sm[wib][4]; pol.su = sm[wib][5]; pol.sv = sm[wib][6]; pol.sw = sm[wib][7];
+  pol.sk = smk[wib];
+  int total = __ldg(B.pfx_grp + B.nsc);
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int g = gw; g < total; g += nw) {
+    int s = find_scene(B.pfx_grp, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    Group<R, DIM> G = group_of<R, DIM>(S, g - __ldg(B.pfx_grp + s));
+    for (int tb = G.ts; tb < G.te; tb += 32) {
+      int i = tb + lane;
+      bool valid = i < G.te;
+      pol.active = valid && S.matR[S.P.mt[i]].kind != KFLUID;
+      if (!__any_sync(FULL, pol.active)) continue;
+      pol.idx = valid ? i : -1;
+      if (valid) target_pos(S, i, G.cx0, pol.tp);
+      pol.S0 = pol.P0 = R(0);
+      for (int q = 0; q < 3; q++) pol.Rv[q] = pol.U[q] = R(0);
+      pol.hits = 0;
+      traverse<R, DIM>(S, G, pol, lane);
+      if (pol.active) {
+        R uw[3] = {S.P.vx[i], S.P.vy[i], S.P.vz[i]};  // prescribed wall / rigid velocity
+        if (pol.S0 > R(0)) {
+          R aw[3] = {R(0), R(0), R(0)};
+          if (S.matR[S.P.mt[i]].kind == KRIGID) { aw[0] = S.P.ax[i]; aw[1] = S.P.ay[i]; aw[2] = S.P.az[i]; }
+          R ga = (S.gR[0] - aw[0]) * pol.Rv[0] + (S.gR[1] - aw[1]) * pol.Rv[1] + (S.gR[2] - aw[2]) * pol.Rv[2];
+          R inv = R(1) / pol.S0;
+          S.prs[i] = (pol.P0 + ga) * inv;
+          S.vex[i] = R(2) * uw[0] - pol.U[0] * inv;
+          S.vey[i] = R(2) * uw[1] - pol.U[1] * inv;
+          S.vez[i] = R(2) * uw[2] - pol.U[2] * inv;
+        } else {
+          S.prs[i] = R(0);
+          S.vex[i] = uw[0]; S.vey[i] = uw[1]; S.vez[i] = uw[2];
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- sweep 3: forces and heat
+template <class R, int DIM>
+struct ForcePol {
+  // staged candidate fields
+  R *sx, *sy, *sz, *su, *sv, *sw, *sex, *sey, *sez, *sr, *sp, *sm, *sT;
+  int *smt, *sb;
+  bool active;
+  int idx;
+  R tp[3];
+  // target fields
+  int tkind, tmat, tbody;
+  R tu[3], tve[3], trho, tp0, tm, tT, tV2, teta, tkap;
+  const MatR<R>* tM;
+  // accumulators
+  R acc[3], heat;
+  unsigned long long hits;
+  __device__ void stage(const Scene<R>& S, int j, int lane) {
+    sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
+    su[lane] = S.P.vx[j]; sv[lane] = S.P.vy[j]; sw[lane] = S.P.vz[j];
+    sex[lane] = S.vex[j]; sey[lane] = S.vey[j]; sez[lane] = S.vez[j];
+    sr[lane] = S.P.rho[j]; sp[lane] = S.prs[j]; sm[lane] = S.P.m[j]; sT[lane] = S.P.T[j];
+    smt[lane] = S.P.mt[j]; sb[lane] = S.P.body[j];
+  }
+  __device__ bool accept(int) const { return true; }
+  __device__ void pair(const Scene<R>& S, int k, int, R dx, R dy, R dz, R r2) {
+    const MatR<R>& Bm = S.matR[smt[k]];
+    int bkind = Bm.kind;
+    R inv_r = rsqrt_<R>(r2);
+    R r = r2 * inv_r;
+    R dW = S.sig_dw * quintic_dw<R>(r * S.inv_h);
+    R ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+    // heat conduction (Cleary & Monaghan), walls Dirichlet or adiabatic
+    if (S.any_heat) {
+      R Tb = sT[k];
+      R kb = bkind == KWALL ? tkap : Bm.kappa;
+      bool on = !(bkind == KWALL && isnan(Tb));
+      if (on) {
+        R ks = tkap + kb;
+        R kab = ks > R(0) ? R(4) * tkap * kb / ks : R(0);
+        R Vb = sm[k] / sr[k];
+        heat += Vb * kab * (tT - Tb) * inv_r * dW;
+      }
+    }
+    if (tkind == KFLUID) {
+      R rhoj, pj, Vj, etaj, uj[3];
+      if (bkind == KFLUID) {
+        rhoj = sr[k]; pj = sp[k]; Vj = sm[k] / rhoj; etaj = Bm.eta;
+        uj[0] = su[k]; uj[1] = sv[k]; uj[2] = sw[k];
+      } else {
+        pj = sp[k];
+        rhoj = tM->rho0 * (pj * tM->inv_p0 + R(1));
+        Vj = sm[k] / sr[k];
+        etaj = teta;
+        uj[0] = sex[k]; uj[1] = sey[k]; uj[2] = sez[k];
+      }
+      R pt = (rhoj * tp0 + trho * pj) / (trho + rhoj);
+      R es = teta + etaj;
+      R et = es > R(0) ? R(2) * teta * etaj / es : R(0);
+      R coef = (tV2 + Vj * Vj) * dW;
+      R vis = et * inv_r;
+      acc[0] += coef * (-pt * ex + vis * (tu[0] - uj[0]));
+      acc[1] += coef * (-pt * ey + vis * (tu[1] - uj[1]));
+      acc[2] += coef * (-pt * ez + vis * (tu[2] - uj[2]));
+    } else {  // rigid target
+      if (bkind == KFLUID) {
+        // -m_j a_jr seen from the fluid particle j (Eq. couplingforce)
+        R rhoj = sr[k], pj = sp[k], Vj = sm[k] / rhoj;
+        R rs = Bm.rho0 * (tp0 * Bm.inv_p0 + R(1));  // inverse EOS of fluid j for p_r
+        R pt = (rs * pj + rhoj * tp0) / (rhoj + rs);
+        R coef = (Vj * Vj + tV2) * dW;
+        R vis = Bm.eta * inv_r;
+        // e_jr = -e, u_jr = u_j - v_r
+        acc[0] -= coef * (pt * ex + vis * (su[k] - tve[0]));
+        acc[1] -= coef * (pt * ey + vis * (sv[k] - tve[1]));
+        acc[2] -= coef * (pt * ez + vis * (sw[k] - tve[2]));
+      } else if (bkind == KWALL || sb[k] != tbody) {
+        if (r < S.dxR) {  // Eq. contactforce with tension cut-off
+          R ev = ex * (tu[0] - su[k]) + ey * (tu[1] - sv[k]) + ez * (tu[2] - sw[k]);
+          R fn = S.kcR * (r - S.dxR) + S.dcR * ev;
+          R mn = fn < R(0) ? fn : R(0);
+          acc[0] -= mn * ex; acc[1] -= mn * ey; acc[2] -= mn * ez;
+        }
+      }
+    }
+  }
+};
+
+template <class R, int DIM>
+__global__ void __launch_bounds__(128) k_force(BatchView<R> B) {
+  __shared__ R sm[4][13][32];
+  __shared__ int smi[4][2][32];
+  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  ForcePol<R, DIM> pol;
+  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
+  pol.su = sm[wib][3]; pol.sv = sm[wib][4]; pol.sw = sm[wib][5];
+  pol.sex = sm[wib][6]; pol.sey = sm[wib][7]; pol.sez = sm[wib][8];
+  pol.sr = sm[wib][9]; pol.sp = sm[wib][10]; pol.sm = sm[wib][11]; pol.sT = sm[wib][12];
+  pol.smt = smi[wib][0]; pol.sb = smi[wib][1];
+  int total = __ldg(B.pfx_grp + B.nsc);
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int g = gw; g < total; g += nw) {
+    int s = find_scene(B.pfx_grp, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    Group<R, DIM> G = group_of<R, DIM>(S, g - __ldg(B.pfx_grp + s));
+    unsigned long long wh = 0;
+    for (int tb = G.ts; tb < G.te; tb += 32) {
+      int i = tb + lane;
+      bool valid = i < G.te;
+      int tm = valid ? S.P.mt[i] : 0;
+      pol.tkind = S.matR[tm].kind;
+      pol.active = valid && pol.tkind != KWALL;
+      if (!__any_sync(FULL, pol.active)) continue;
+      pol.idx = valid ? i : -1;
+      pol.hits = 0;
+      pol.acc[0] = pol.acc[1] = pol.acc[2] = R(0);
+      pol.heat = R(0);
+      if (pol.active) {
+        target_pos(S, i, G.cx0, pol.tp);
+        pol.tmat = tm;
+        pol.tM = &S.matR[tm];
+        pol.tbody = S.P.body[i];
+        pol.tu[0] = S.P.vx[i]; pol.tu[1] = S.P.vy[i]; pol.tu[2] = S.P.vz[i];
+        pol.tve[0] = S.vex[i]; pol.tve[1] = S.vey[i]; pol.tve[2] = S.vez[i];
+        pol.trho = S.P.rho[i];
+        pol.tp0 = S.prs[i];
+        pol.tm = S.P.m[i];
+        pol.tT = S.P.T[i];
+        R V = pol.tm / pol.trho;
+        pol.tV2 = V * V;
+        pol.teta = pol.tM->eta;
+        pol.tkap = pol.tM->kappa;
+      }
+      traverse<R, DIM>(S, G, pol, lane);
+      wh += pol.active ? pol.hits : 0ull;
+      if (pol.active) {
+        if (pol.tkind == KFLUID) {
+          R im = R(1) / pol.tm;
+          S.P.ax[i] = S.gR[0] + pol.acc[0] * im;
+          S.P.ay[i] = S.gR[1] + pol.acc[1] * im;
+          S.P.az[i] = S.gR[2] + pol.acc[2] * im;
+        } else {
+          int sl = S.P.slot[i];
+          S.fr[3 * sl] = pol.acc[0];
+          S.fr[3 * sl + 1] = pol.acc[1];
+          S.fr[3 * sl + 2] = pol.acc[2];
+        }
+        R rate = pol.heat / pol.trho;  // c_p dT/dt = dH/dt
+        if (S.has_source && S.mat[tm].src) {
+          double x[3];
+          abs_pos<R>(S, i, x);
+          double t = S.st[1] + S.st[0];
+          int vz = S.dim - 1;
+          double dd = 0.0;
+          for (int q = 0; q < S.dim; q++)
+            if (q != vz) {
+              double c = x[q] - (S.src_x0[q] + S.src_v[q] * t);
+              dd += c * c;
+            }
+          if (S.src_ztop - x[vz] < S.src_depth)
+            rate += (R)(S.src_Q * exp(-2.0 * dd / (S.src_r * S.src_r))) / pol.trho;
+        }
+        S.dT[i] = pol.tM->enth ? rate : rate / pol.tM->cp;
+      }
+    }
+    for (int o = 16; o; o >>= 1) wh += __shfl_xor_sync(FULL, wh, o);
+    if (lane == 0 && wh) atomicAdd(S.pairs, wh);
+  }
+}
+
+// ============================================================================ bodies (FP64)
+// force and torque of every body (Eq. procwise_force with thread partials as the
+// processors), body accelerations (Eqs. linear/angular momentum), final body kick
+template <class R>
+__global__ void __launch_bounds__(128) k_body_reduce(BatchView<R> B, int kick) {
+  __shared__ double red[6][128];
+  int total = __ldg(B.pfx_body + B.nsc);
+  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+    int s = find_scene(B.pfx_body, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    int k = g - __ldg(B.pfx_body + s);
+    if (k >= *S.K || !S.balive[k]) continue;
+    double Rm[9];
+    qrot(&S.bq[4 * k], Rm);
+    double F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
+    for (int sl = S.bstart[k] + threadIdx.x; sl < S.bend[k]; sl += blockDim.x) {
+      double f[3] = {(double)S.fr[3 * sl], (double)S.fr[3 * sl + 1], (double)S.fr[3 * sl + 2]};
+      double rr[3], c[3];
+      mv(Rm, &S.rb[3 * sl], rr);
+      cross(rr, f, c);
+      for (int q = 0; q < 3; q++) { F[q] += f[q]; Tq[q] += c[q]; }
+    }
+    for (int q = 0; q < 3; q++) { red[q][threadIdx.x] = F[q]; red[3 + q][threadIdx.x] = Tq[q]; }
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+      if (threadIdx.x < w)
+        for (int q = 0; q < 6; q++) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      double f[3], t[3], t1[3], t2[3], al[3];
+      for (int q = 0; q < 3; q++) { f[q] = red[q][0] + S.bm[k] * S.g[q]; t[q] = red[3 + q][0]; }
+      mtv(Rm, t, t1);
+      mv(&S.bIbinv[9 * k], t1, t2);
+      mv(Rm, t2, al);
+      if (S.dim == 2) { al[0] = 0.0; al[1] = 0.0; }
+      double half = 0.5 * S.st[0];
+      for (int q = 0; q < 3; q++) {
+        S.bf[3 * k + q] = f[q];
+        S.bt[3 * k + q] = t[q];
+        S.ba[3 * k + q] = f[q] / S.bm[k];
+        S.bal[3 * k + q] = al[q];
+        if (kick) {
+          S.bu[3 * k + q] = S.bu[3 * k + q] + half * S.ba[3 * k + q];
+          S.bw[3 * k + q] = S.bw[3 * k + q] + half * al[q];
+        }
+      }
+      // world inertia R I_body R^T
+      double T9[9];
+      const double* Ib = &S.bIb[9 * k];
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) T9[3 * a + b] = Rm[3 * a] * Ib[b] + Rm[3 * a + 1] * Ib[3 + b] + Rm[3 * a + 2] * Ib[6 + b];
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+          S.bIw[9 * k + 3 * a + b] = T9[3 * a] * Rm[3 * b] + T9[3 * a + 1] * Rm[3 * b + 1] + T9[3 * a + 2] * Rm[3 * b + 2];
+    }
+    __syncthreads();
+  }
+}
+
+// ============================================================================ final update
+template <class R>
+__global__ void k_final(BatchView<R> B) {
+  int total = __ldg(B.pfx_part + B.nsc);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int s = find_scene(B.pfx_part, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    int i = g - __ldg(B.pfx_part + s);
+    const MatR<R>& A = S.matR[S.P.mt[i]];
+    if (A.kind == KWALL) continue;
+    R dt = (R)S.st[0];
+    if (A.enth) {
+      R Hn = S.P.H[i] + dt * S.dT[i];
+      S.P.H[i] = Hn;
+      const MatD& M = S.mat[S.P.mt[i]];
+      // T(H): apparent-capacity interval of width w below/above T_t
+      int so = S.P.mt[i], li = S.P.mt[i];
+      if (M.to >= 0) {
+        so = M.kind == KRIGID ? S.P.mt[i] : M.to;
+        li = M.kind == KRIGID ? M.to : S.P.mt[i];
+      }
+      double cs = S.mat[so].cp, cl = S.mat[li].cp, w = M.w, Tlo = M.Tt - 0.5 * w;
+      double Hh = (cs + M.L / w) * w, H = (double)Hn, T;
+      if (H <= 0.0) T = Tlo + H / cs;
+      else if (H <= Hh) T = Tlo + H / (cs + M.L / w);
+      else T = Tlo + w + (H - Hh) / cl;
+      S.P.T[i] = (R)T;
+    } else {
+      S.P.T[i] = S.P.T[i] + dt * S.dT[i];
+    }
+    if (A.kind == KFLUID) {
+      R half = R(0.5) * dt;
+      R ux = S.P.vx[i] + half * S.P.ax[i];
+      R uy = S.P.vy[i] + half * S.P.ay[i];
+      R uz = S.P.vz[i] + half * S.P.az[i];
+      S.P.vx[i] = ux; S.P.vy[i] = uy; S.P.vz[i] = uz;
+      if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) S.status[0] = 1;
+    } else {
+      int k = S.P.body[i], sl = S.P.slot[i];
+      double Rm[9], rr[3], c[3];
+      qrot(&S.bq[4 * k], Rm);
+      mv(Rm, &S.rb[3 * sl], rr);
+      cross(&S.bw[3 * k], rr, c);
+      S.P.vx[i] = (R)(S.bu[3 * k] + c[0]);
+      S.P.vy[i] = (R)(S.bu[3 * k + 1] + c[1]);
+      S.P.vz[i] = (R)(S.bu[3 * k + 2] + c[2]);
+    }
+  }
+}
+
+template <class R>
+__global__ void k_end_step(BatchView<R> B) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B.nsc) return;
+  Scene<R>& S = *B.sc[s];
+  S.st[1] += S.st[0];
+  S.st[2] += 1.0;
+  S.st[3] = S.st[0];
+  S.pairs[1] += S.pairs[0];  // cumulative ordered pairs of the force / heat sweep
+}
+
+// ============================================================================ body set-up (FP64)
+// Mass, centre of mass and inertia of every body from its rigid particles: each thread
+// sums a chunk (processor-wise Eqs. procwise_centerofmass / procwise_inertia) and the
+// chunks are combined by Eqs. global_centerofmass / global_inertia (Huygens-Steiner).
+// Then the body-frame inertia R^T I R, its inverse, and the body-frame offsets of the
+// particles r_rk = R^T (x_r - r_k).
+template <class R>
+__global__ void __launch_bounds__(128) k_body_mass(BatchView<R> B, const int* __restrict__ only) {
+  __shared__ double pm[128], pr[3][128], pI[9][128];
+  __shared__ double com[3];
+  int total = __ldg(B.pfx_body + B.nsc);
+  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+    int s = find_scene(B.pfx_body, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    int k = g - __ldg(B.pfx_body + s);
+    if (k >= *S.K) continue;
+    if (only && !only[g]) continue;
+    int a = S.bstart[k], e = S.bend[k];
+    if (e <= a) {
+      if (threadIdx.x == 0) S.balive[k] = 0;
+      continue;
+    }
+    // reference particle for minimum-image unwrapping on periodic axes
+    double x0[3];
+    abs_pos<R>(S, S.slot_part[a], x0);
+    double Ir_c = S.dim == 2 ? 0.5 * S.dx * S.dx / M_PI : 0.4 * cbrt(0.75 / M_PI) * cbrt(0.75 / M_PI) * S.dx * S.dx;
+    double m = 0, c[3] = {0, 0, 0};
+    // chunk of this thread: contiguous slots
+    int n = e - a, per = (n + blockDim.x - 1) / blockDim.x;
+    int s0 = a + threadIdx.x * per, s1 = min(e, s0 + per);
+    for (int sl = s0; sl < s1; sl++) {
+      double x[3];
+      abs_pos<R>(S, S.slot_part[sl], x);
+      for (int q = 0; q < S.dim; q++)
+        if (S.per[q]) {
+          double d = x[q] - x0[q];
+          if (d > 0.5 * S.L[q]) x[q] -= S.L[q]; else if (d < -0.5 * S.L[q]) x[q] += S.L[q];
+        }
+      double mr = (double)S.P.m[S.slot_part[sl]];
+      m += mr;
+      for (int q = 0; q < 3; q++) c[q] += mr * x[q];
+    }
+    double I[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (m > 0)
+      for (int q = 0; q < 3; q++) c[q] /= m;
+    for (int sl = s0; sl < s1; sl++) {
+      double x[3];
+      abs_pos<R>(S, S.slot_part[sl], x);
+      for (int q = 0; q < S.dim; q++)
+        if (S.per[q]) {
+          double d = x[q] - x0[q];
+          if (d > 0.5 * S.L[q]) x[q] -= S.L[q]; else if (d < -0.5 * S.L[q]) x[q] += S.L[q];
+        }
+      double mr = (double)S.P.m[S.slot_part[sl]];
+      double d[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
+      double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      for (int p = 0; p < 3; p++)
+        for (int q = 0; q < 3; q++) I[3 * p + q] += Ir_c * mr * (p == q) + ((p == q) * d2 - d[p] * d[q]) * mr;
+    }
+    pm[threadIdx.x] = m;
+    for (int q = 0; q < 3; q++) pr[q][threadIdx.x] = c[q];
+    for (int q = 0; q < 9; q++) pI[q][threadIdx.x] = I[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double M = 0, C[3] = {0, 0, 0};
+      for (int t = 0; t < blockDim.x; t++) {
+        M += pm[t];
+        for (int q = 0; q < 3; q++) C[q] += pm[t] * pr[q][t];
+      }
+      for (int q = 0; q < 3; q++) C[q] /= M;
+      double IG[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int t = 0; t < blockDim.x; t++) {
+        if (pm[t] == 0.0) continue;
+        double d[3] = {C[0] - pr[0][t], C[1] - pr[1][t], C[2] - pr[2][t]};
+        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        for (int p = 0; p < 3; p++)
+          for (int q = 0; q < 3; q++) IG[3 * p + q] += pI[3 * p + q][t] + ((p == q) * d2 - d[p] * d[q]) * pm[t];
+      }
+      S.bm[k] = M;
+      for (int q = 0; q < 3; q++) { S.br[3 * k + q] = C[q]; com[q] = C[q]; }
+      double Rm[9], T9[9], Ib[9];
+      qrot(&S.bq[4 * k], Rm);
+      for (int q = 0; q < 9; q++) S.bIw[9 * k + q] = IG[q];
+      // I_body = R^T I R
+      for (int p = 0; p < 3; p++)
+        for (int q = 0; q < 3; q++) T9[3 * p + q] = Rm[p] * IG[q] + Rm[3 + p] * IG[3 + q] + Rm[6 + p] * IG[6 + q];
+      for (int p = 0; p < 3; p++)
+        for (int q = 0; q < 3; q++) Ib[3 * p + q] = T9[3 * p] * Rm[q] + T9[3 * p + 1] * Rm[3 + q] + T9[3 * p + 2] * Rm[6 + q];
+      for (int q = 0; q < 9; q++) S.bIb[9 * k + q] = Ib[q];
+      double c00 = Ib[4] * Ib[8] - Ib[5] * Ib[7], c01 = Ib[5] * Ib[6] - Ib[3] * Ib[8], c02 = Ib[3] * Ib[7] - Ib[4] * Ib[6];
+      double det = Ib[0] * c00 + Ib[1] * c01 + Ib[2] * c02, id = 1.0 / det;
+      double* Bi = &S.bIbinv[9 * k];
+      Bi[0] = c00 * id; Bi[1] = (Ib[2] * Ib[7] - Ib[1] * Ib[8]) * id; Bi[2] = (Ib[1] * Ib[5] - Ib[2] * Ib[4]) * id;
+      Bi[3] = c01 * id; Bi[4] = (Ib[0] * Ib[8] - Ib[2] * Ib[6]) * id; Bi[5] = (Ib[2] * Ib[3] - Ib[0] * Ib[5]) * id;
+      Bi[6] = c02 * id; Bi[7] = (Ib[1] * Ib[6] - Ib[0] * Ib[7]) * id; Bi[8] = (Ib[0] * Ib[4] - Ib[1] * Ib[3]) * id;
+      S.balive[k] = 1;
+    }
+    __syncthreads();
+    double Rm[9];
+    qrot(&S.bq[4 * k], Rm);
+    for (int sl = a + threadIdx.x; sl < e; sl += blockDim.x) {
+      double x[3], d[3];
+      abs_pos<R>(S, S.slot_part[sl], x);
+      for (int q = 0; q < 3; q++) {
+        d[q] = x[q] - com[q];
+        if (q < S.dim && S.per[q]) {
+          if (d[q] > 0.5 * S.L[q]) d[q] -= S.L[q]; else if (d[q] < -0.5 * S.L[q]) d[q] += S.L[q];
+        }
+      }
+      mtv(Rm, d, &S.rb[3 * sl]);
+    }
+    __syncthreads();
+  }
+}
+
+// rigid particle velocities from their bodies (after creation or a relabel)
+template <class R>
+__global__ void k_rigid_vel(BatchView<R> B) {
+  int total = __ldg(B.pfx_part + B.nsc);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int s = find_scene(B.pfx_part, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    int i = g - __ldg(B.pfx_part + s);
+    if (S.matR[S.P.mt[i]].kind != KRIGID) continue;
+    int k = S.P.body[i], sl = S.P.slot[i];
+    double Rm[9], rr[3], c[3], t1[3], t3[3];
+    qrot(&S.bq[4 * k], Rm);
+    mv(Rm, &S.rb[3 * sl], rr);
+    cross(&S.bw[3 * k], rr, c);
+    S.P.vx[i] = (R)(S.bu[3 * k] + c[0]);
+    S.P.vy[i] = (R)(S.bu[3 * k + 1] + c[1]);
+    S.P.vz[i] = (R)(S.bu[3 * k + 2] + c[2]);
+    cross(&S.bal[3 * k], rr, t1);
+    cross(&S.bw[3 * k], c, t3);
+    S.P.ax[i] = (R)(S.ba[3 * k] + t1[0] + t3[0]);
+    S.P.ay[i] = (R)(S.ba[3 * k + 1] + t1[1] + t3[1]);
+    S.P.az[i] = (R)(S.ba[3 * k + 2] + t1[2] + t3[2]);
+  }
+}
+
+}  // namespace sph

@@ -1,0 +1,173 @@
+"""GPU (CUDA, through the C ABI) against the FP64 oracle.
+
+Bit-exact: cell binning, neighbour sets, materials, bodies of particles.
+FP64 path: every per-step field within 1e-12 of the oracle relative to max(|y|, RMS(y)).
+FP32 path: per-step fields within 1e-5 (relative to the field RMS) from a shared state.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleScene
+from paper_2103_07925_gb300 import scenes as S
+from tests.parity import compare_bodies, compare_fields, rel_err, state_scene
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def _gpu(sc, **kw):
+    from paper_2103_07925_gb300.sph import Scene
+    return Scene(sc, **kw)
+
+
+def small_scenes():
+    return {
+        "tank2d_quarter": S.tank2d_disc(dx=0.025),
+        "tank2d_full": S.tank2d_disc(),
+        "tank3d_small": S.tank3d_spheres(dx=0.04, n_spheres=6, r_range=(0.08, 0.12)),
+        "periodic3d_heat": S.periodic_box(dim=3, n=12, dx=0.1, bodies=2, body_radius=0.25, vel_amp=0.2,
+                                          jitter=0.1, kappa=1.0, T_amp=20.0),
+        "periodic2d": S.periodic_box(dim=2, n=24, dx=0.1, bodies=3, body_radius=0.22, vel_amp=0.2, jitter=0.1),
+        "cloud3d": S.random_cloud(dim=3, n=1500, L=1.0, dx=0.06, seed=5),
+        "cloud2d_periodic": S.random_cloud(dim=2, n=1800, L=1.0, dx=0.03, seed=6, periodic=True),
+    }
+
+
+SCENES = small_scenes()
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+@pytest.mark.parametrize("key_order", [0, 1])
+def test_binning_and_neighbours_bit_exact(name, key_order):
+    sc = SCENES[name]
+    g = _gpu(sc, precision=64, key_order=key_order)
+    o = OracleScene(sc)
+    assert np.array_equal(g.read("cell"), o.get("cell"))
+    gc, gl = g.neighbors()
+    oc, ol = o.neighbors()
+    assert np.array_equal(gc, oc)
+    assert np.array_equal(gl, ol)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_fp64_initial_evaluation(name):
+    sc = SCENES[name]
+    g = _gpu(sc, precision=64)
+    o = OracleScene(sc)
+    errs = compare_fields(g, o)
+    assert max(errs.values()) < TOL64, errs
+    be = compare_bodies(g, o)
+    assert not be or max(be.values()) < TOL64, be
+    d_g, d_o = g.diagnostics(), o.diagnostics()
+    assert d_g[15] == d_o[15]  # ordered pairs of the force / heat sweep
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_fp64_steps_from_shared_state(name):
+    sc = SCENES[name]
+    o = OracleScene(sc)
+    for k in range(3):
+        st = state_scene(sc, o) if k else sc
+        g = _gpu(st, precision=64)
+        o2 = OracleScene(st)
+        g.step(1)
+        o2.step(1)
+        errs = compare_fields(g, o2)
+        assert max(errs.values()) < TOL64, (k, errs)
+        be = compare_bodies(g, o2)
+        assert not be or max(be.values()) < TOL64, (k, be)
+        o.step(2)
+
+
+@pytest.mark.parametrize("key_order", [0, 1])
+def test_fp64_multi_step_trajectory_close(key_order):
+    """20 consecutive steps on both sides: fields stay within a loose band (rounding
+    differences grow through the dynamics, so this is a consistency check)."""
+    sc = S.tank2d_disc(dx=0.025)
+    g = _gpu(sc, precision=64, key_order=key_order)
+    o = OracleScene(sc)
+    g.step(20)
+    o.step(20)
+    errs = compare_fields(g, o, fields=["pos", "vel", "rho"])
+    assert max(errs.values()) < 1e-8, errs
+
+
+@pytest.mark.parametrize("name", ["tank2d_full", "tank3d_small", "periodic3d_heat"])
+def test_fp32_fields_from_shared_state(name):
+    sc = SCENES[name]
+    g = _gpu(sc, precision=32)
+    o = OracleScene(sc)
+    g.step(1)
+    o.step(1)
+    kinds = np.array([m["kind"] for m in sc["materials"]])[sc["particles"]["material"]]
+    out = {}
+    for f in ("pos", "vel", "rho", "pres", "temp", "acc"):
+        a, b = g.read(f), o.get(f)
+        # relative to the field's RMS (FP32 sums of ~100 terms)
+        m = kinds != S.WALL
+        bb = b[m]
+        s = np.sqrt(np.mean(bb * bb)) if bb.size else 1.0
+        out[f] = float(np.max(np.abs(a[m] - bb)) / max(s, 1e-300))
+    assert out["pos"] < 1e-6 and out["vel"] < 1e-5 and out["rho"] < 1e-5 and out["temp"] < 1e-6, out
+    assert out["acc"] < 1e-3, out  # acceleration: sum of large cancelling pressure terms
+
+
+def test_fp32_rigid_trajectory_100_steps():
+    sc = S.tank2d_disc()
+    g = _gpu(sc, precision=32)
+    o = OracleScene(sc)
+    g.step(100)
+    o.step(100)
+    bg, bo = g.bodies(), o.bodies()
+    disp_o = bo["com"][0] - sc["particles"]["pos"][sc["particles"]["body"] == 0].mean(0)
+    err = np.linalg.norm(bg["com"][0] - bo["com"][0]) / max(np.linalg.norm(disp_o), 1e-12)
+    assert err < 1e-3, err
+
+
+def test_determinism_bitwise():
+    sc = S.tank3d_spheres(dx=0.04, n_spheres=6, r_range=(0.08, 0.12))
+    a = _gpu(sc, precision=32)
+    b = _gpu(sc, precision=32)
+    a.step(5)
+    b.step(5)
+    for f in ("pos", "vel", "rho", "pres"):
+        assert np.array_equal(a.read(f), b.read(f)), f
+
+
+def test_linear_momentum_gpu_periodic():
+    sc = S.periodic_box(dim=3, n=10, dx=0.1, bodies=2, body_radius=0.16, vel_amp=0.2, jitter=0.1, seed=4)
+    g = _gpu(sc, precision=64)
+    d0 = g.diagnostics()
+    scale = np.abs(sc["particles"]["mass"][:, None] * sc["particles"]["vel"]).sum()
+    g.step(100)
+    d = g.diagnostics()
+    assert np.all(np.abs(d[:3] - d0[:3]) <= 1e-13 * scale)
+    g32 = _gpu(sc, precision=32)
+    g32.step(100)
+    d32 = g32.diagnostics()
+    assert np.all(np.abs(d32[:3] - d0[:3]) <= 1e-5 * scale)
+
+
+def test_free_fall_gpu_exact():
+    sc = S.free_fall(dim=3, vel=(0.3, -0.1, 0.2))
+    g = _gpu(sc, precision=64)
+    b0 = g.bodies()
+    g.step(200)
+    b = g.bodies()
+    t = 200 * sc["params"]["dt_fixed"]
+    gv = np.array(sc["params"]["gravity"])
+    expect = b0["com"][0] + np.array([0.3, -0.1, 0.2]) * t + 0.5 * gv * t * t
+    assert np.allclose(b["com"][0], expect, rtol=0, atol=1e-13 * (1 + np.abs(expect).max()))
+
+
+def test_errors_are_reported():
+    from paper_2103_07925_gb300.sph import SphError
+    sc = S.tank2d_disc(dx=0.05)
+    sc["particles"]["pos"][0, 0] = 5.0  # outside the non-periodic box
+    with pytest.raises(SphError) as e:
+        _gpu(sc, precision=64)
+    assert e.value.status == -1
+    sc = S.tank2d_disc(dx=0.05)
+    with pytest.raises(SphError):
+        _gpu(sc, precision=16)

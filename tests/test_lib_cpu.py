@@ -1,0 +1,37 @@
+"""The CUDA library builds for sm_103a, loads without a GPU, and exports every symbol
+that include/sph.h declares (no compute call: there is no device here)."""
+import ctypes
+import os
+import re
+
+from paper_2103_07925_gb300 import build as B
+from paper_2103_07925_gb300 import sph
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    txt = open(os.path.join(ROOT, "include", "sph.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sph_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_builds_and_exports_header_symbols():
+    path = B.build()
+    lib = ctypes.CDLL(path)
+    names = declared()
+    assert len(names) >= 20
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert sorted(sph.EXPORTS) == names
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    monkeypatch.setattr(sph, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(sph, "_lib", None)
+    try:
+        sph.lib()
+    except sph.SphError as e:
+        assert "not built" in str(e)
+    else:
+        raise AssertionError("expected SphError")
