@@ -246,7 +246,7 @@ def main():
                       "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
            "steps_per_s": steps_per_s * world,
            "pairs_per_step": pairs_per_step,
-           "gpu_launches": args.steps * info["kernels_per_step"],
+           "gpu_launches": args.steps * g.info()["kernels_per_step"],
            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                         "frac": achieved_tf / peak_tf, "traffic": None, "kernel": "k_force",
                         "peak_source": "FP32 FMA lanes x SMs x 2 x max SM clock (%s clocks)" % peak_src,

@@ -140,18 +140,35 @@ __device__ __forceinline__ void store_pos<float>(const Scene<float>& S, int i, c
 
 // ============================================================================ time step
 template <class R>
-__global__ void k_umax(BatchView<R> B) {
+__global__ void __launch_bounds__(256) k_umax(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-    int s = find_scene(B.pfx_part, B.nsc, g);
+  for (int g0 = blockIdx.x * blockDim.x; g0 < total; g0 += gridDim.x * blockDim.x) {
+    int g = g0 + threadIdx.x;
+    // the block's first item decides the scene slice handled in this round
+    int s = find_scene(B.pfx_part, B.nsc, min(g, total - 1));
     const Scene<R>& S = *B.sc[s];
-    if (S.dt_mode == 0) continue;
-    int i = g - __ldg(B.pfx_part + s);
-    if (S.matR[S.P.mt[i]].kind != KFLUID) continue;
-    double ux = S.P.vx[i], uy = S.P.vy[i], uz = S.P.vz[i];
-    double u = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz)));
-    // bits of a non-negative double order like unsigned integers, so the maximum is exact
-    if (u > 0.0) atomicMax(S.umax, (unsigned long long)__double_as_longlong(u));
+    double u = 0.0;
+    if (g < total && S.dt_mode == 1) {
+      int i = g - __ldg(B.pfx_part + s);
+      if (S.matR[S.P.mt[i]].kind == KFLUID) {
+        double ux = S.P.vx[i], uy = S.P.vy[i], uz = S.P.vz[i];
+        u = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz)));
+      }
+    }
+    // warp maximum for each scene present in the warp, one atomic per scene (max is exact)
+    unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    unsigned pending = FULL;
+    while (pending) {
+      int leader = __ffs(pending) - 1;
+      int cs = __shfl_sync(FULL, s, leader);
+      unsigned long long v = s == cs ? b : 0ull;
+      for (int o = 16; o; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(FULL, v, o);
+        v = w > v ? w : v;
+      }
+      if ((int)(threadIdx.x & 31) == leader && v > 0ull) atomicMax(S.umax, v);
+      pending &= ~__ballot_sync(FULL, s == cs);
+    }
   }
 }
 
@@ -1151,13 +1168,15 @@ __global__ void __launch_bounds__(128) k_body_mass(BatchView<R> B, const int* __
     double Rm[9];
     qrot(&S.bq[4 * k], Rm);
     for (int sl = a + threadIdx.x; sl < e; sl += blockDim.x) {
+      // same unwrapping as for the mass quantities: image nearest to the reference particle
       double x[3], d[3];
       abs_pos<R>(S, S.slot_part[sl], x);
       for (int q = 0; q < 3; q++) {
-        d[q] = x[q] - com[q];
         if (q < S.dim && S.per[q]) {
-          if (d[q] > 0.5 * S.L[q]) d[q] -= S.L[q]; else if (d[q] < -0.5 * S.L[q]) d[q] += S.L[q];
+          double dd = x[q] - x0[q];
+          if (dd > 0.5 * S.L[q]) x[q] -= S.L[q]; else if (dd < -0.5 * S.L[q]) x[q] += S.L[q];
         }
+        d[q] = x[q] - com[q];
       }
       mtv(Rm, d, &S.rb[3 * sl]);
     }
