@@ -239,6 +239,7 @@ template <class R, int DIM>
 struct NbPol {
   R *sx, *sy, *sz;
   int* so;
+  int cox, cdy, cdz;
   bool active;
   int idx;
   R tp[3];

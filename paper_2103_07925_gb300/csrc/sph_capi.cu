@@ -126,7 +126,7 @@ sph_status sph_profile(sph_scene* s, int32_t reps, double* ms_per_stage) {
 const char* sph_profile_stage_name(int32_t i) {
   static const char* const names[] = {"umax", "dt", "body_kick_drift", "kick_drift", "bin", "scan_blocks",
                                       "scan_top", "scan_cells", "scatter", "rank", "permute", "flip",
-                                      "density", "extrap", "force", "body_reduce", "final", "end_step"};
+                                      "search_density", "extrap", "force", "body_reduce", "final", "end_step"};
   if (i < 0 || i >= SPH_PROFILE_STAGES) return "";
   return names[i];
 }

@@ -66,6 +66,10 @@ struct Scene {
   PBank<R> P, Q;       // current and alternate bank
   R *prs, *dT;         // pressure, rate (not permuted: recomputed every evaluation)
   R *vex, *vey, *vez;  // extrapolated velocity of wall and rigid particles
+  R* vol;              // particle volume m / rho of the current evaluation
+  int* nbl;            // neighbour lists: entry k of particle i at nbl[k * n + i] = j << 5 | cell code
+  int* nbc;            // neighbour count of each particle (may exceed maxnb: then cells are scanned)
+  int maxnb;           // list capacity per particle
   int* key;            // cell key of each (sorted) particle
   int* where;          // input index -> current sorted index
   // rebin scratch

@@ -188,7 +188,7 @@ class Engine {
     SPH_CU(cudaMemsetAsync(d_pfx, 0, sizeof(int) * 7 * (cap + 1), stream));
     int b1 = 0, b2 = 0;
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_kick_drift<R>, 256, 0));
-    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_force<R, DIM>, 128, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_search<R, DIM>, 128, 0));
     grid_part = sms * std::max(1, b1);
     grid_warp = sms * std::max(1, b2);
     grid_blk = sms * 8;
@@ -286,7 +286,8 @@ class Engine {
   }
 
   static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid) {
-    size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 5 * sizeof(R) + 7 * sizeof(int) + 8 * sizeof(double);
+    size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 6 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
+                 (DIM == 3 ? 128 : 48) * sizeof(int);
     size_t cells = (size_t)(ncells + 1) * 4 * sizeof(int) + (size_t)(ncells / 1024 + 2) * sizeof(int);
     size_t bodies = (size_t)kcap * (60 * sizeof(double) + 3 * sizeof(int));
     size_t slots = (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R) + sizeof(int));
@@ -446,8 +447,11 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     int** ifs[] = {&B->mt, &B->body, &B->slot, &B->orig};
     for (int** f : ifs) SPH_TRY(A(f, (size_t)n));
   }
-  R** rx[] = {&S.prs, &S.dT, &S.vex, &S.vey, &S.vez};
+  R** rx[] = {&S.prs, &S.dT, &S.vex, &S.vey, &S.vez, &S.vol};
   for (R** f : rx) SPH_TRY(A(f, (size_t)n));
+  S.maxnb = DIM == 3 ? 128 : 48;
+  SPH_TRY(A(&S.nbl, (size_t)S.maxnb * n));
+  SPH_TRY(A(&S.nbc, (size_t)n));
   int** ix[] = {&S.key, &S.where, &S.tkey, &S.tloc, &S.bucket, &S.perm, &S.tshift};
   for (int** f : ix) SPH_TRY(A(f, (size_t)n));
   SPH_TRY(A(&S.cstart, (size_t)S.ncells + 1));
@@ -586,9 +590,9 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   if (meta[idx].K0 > 0) k_body_mass<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, nullptr);
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B);
   int gw = grid_for((int64_t)S.ngroups * 32, 128, grid_warp);
-  k_density<R, DIM><<<gw, 128, 0, stream>>>(B);
-  k_extrap<R, DIM><<<gw, 128, 0, stream>>>(B);
-  k_force<R, DIM><<<gw, 128, 0, stream>>>(B);
+  k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
+  k_extrap<R, DIM><<<gp, 256, 0, stream>>>(B);
+  k_force<R, DIM><<<gp, 256, 0, stream>>>(B);
   if (meta[idx].K0 > 0) k_body_reduce<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B);
   SPH_CU(cudaGetLastError());
@@ -609,7 +613,7 @@ sph_status Engine<R, DIM>::remove_scene(int idx) {
 // stage names of a step, in launch order (sph_profile reports one time per stage)
 static const char* const kStageNames[] = {"umax", "dt", "body_kick_drift", "kick_drift", "bin", "scan_blocks",
                                           "scan_top", "scan_cells", "scatter", "rank", "permute", "flip",
-                                          "density", "extrap", "force", "body_reduce", "final", "end_step"};
+                                          "search_density", "extrap", "force", "body_reduce", "final", "end_step"};
 constexpr int kStages = 18;
 
 // Launch one step.  With ev != nullptr an event is recorded before the first stage and
@@ -660,11 +664,11 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_flip<R><<<gs, 128, 0, stream>>>(B, 0);
   rec();
-  k_density<R, DIM><<<gw, 128, 0, stream>>>(B);
+  k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   rec();
-  k_extrap<R, DIM><<<gw, 128, 0, stream>>>(B);
+  k_extrap<R, DIM><<<gp, 256, 0, stream>>>(B);
   rec();
-  k_force<R, DIM><<<gw, 128, 0, stream>>>(B);
+  k_force<R, DIM><<<gp, 256, 0, stream>>>(B);
   rec();
   if (any_body) { k_body_reduce<R><<<gb, 128, 0, stream>>>(B, 1); kcount++; }
   rec();

@@ -619,6 +619,9 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
         int key;
         R sh[3];
         if (!stencil_cell<R, DIM>(S, G, ox, dy, dz, key, sh)) continue;
+        pol.cox = ox;
+        pol.cdy = dy;
+        pol.cdz = dz;
         int cs = max(S.cstart[key], 0), ce = min(S.cstart[key + 1], S.n);
         for (int cb = cs; cb < ce; cb += 32) {
           int cnt = min(32, ce - cb);
@@ -649,302 +652,11 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
       }
 }
 
-// ---------------------------------------------------------------- sweep 1: density (Eq. densum, eos)
-template <class R, int DIM>
-struct DensityPol {
-  R *sx, *sy, *sz;
-  bool active;
-  int idx;
-  R tp[3];
-  R acc;
-  unsigned long long hits;
-  __device__ void stage(const Scene<R>& S, int j, int lane) {
-    sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
-  }
-  __device__ bool accept(int) const { return true; }
-  __device__ void pair(const Scene<R>& S, int, int, R, R, R, R r2) {
-    R r = sqrt(r2);
-    acc += quintic_w<R>(r * S.inv_h);
-  }
-};
+}  // namespace sph
 
-template <class R, int DIM>
-__global__ void __launch_bounds__(128) k_density(BatchView<R> B) {
-  __shared__ R sm[4][3][32];
-  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  DensityPol<R, DIM> pol;
-  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
-  int total = __ldg(B.pfx_grp + B.nsc);
-  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  for (int g = gw; g < total; g += nw) {
-    int s = find_scene(B.pfx_grp, B.nsc, g);
-    const Scene<R>& S = *B.sc[s];
-    Group<R, DIM> G = group_of<R, DIM>(S, g - __ldg(B.pfx_grp + s));
-    for (int tb = G.ts; tb < G.te; tb += 32) {
-      int i = tb + lane;
-      bool valid = i < G.te;
-      pol.active = valid && S.matR[S.P.mt[i]].kind == KFLUID;
-      if (!__any_sync(FULL, pol.active)) continue;
-      pol.idx = valid ? i : -1;
-      if (valid) target_pos(S, i, G.cx0, pol.tp);
-      pol.acc = R(0);
-      pol.hits = 0;
-      traverse<R, DIM>(S, G, pol, lane);
-      if (pol.active) {
-        const MatR<R>& A = S.matR[S.P.mt[i]];
-        R rho = S.P.m[i] * (S.w0 + S.sig_w * pol.acc);
-        S.P.rho[i] = rho;
-        S.prs[i] = A.c2 * (rho - A.rho0);
-      }
-    }
-  }
-}
+#include "sph_sweeps.cuh"
 
-// ---------------------------------------------------------------- sweep 2: extrapolation (Adami 2012)
-template <class R, int DIM>
-struct ExtrapPol {
-  R *sx, *sy, *sz, *sp, *sr, *su, *sv, *sw;
-  int* sk;
-  bool active;
-  int idx;
-  R tp[3];
-  R S0, P0, Rv[3], U[3];
-  unsigned long long hits;
-  __device__ void stage(const Scene<R>& S, int j, int lane) {
-    sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
-    int kind = S.matR[S.P.mt[j]].kind;
-    sk[lane] = kind;
-    if (kind == KFLUID) {
-      sp[lane] = S.prs[j]; sr[lane] = S.P.rho[j];
-      su[lane] = S.P.vx[j]; sv[lane] = S.P.vy[j]; sw[lane] = S.P.vz[j];
-    }
-  }
-  __device__ bool accept(int k) const { return sk[k] == KFLUID; }
-  __device__ void pair(const Scene<R>& S, int k, int, R dx, R dy, R dz, R r2) {
-    R r = sqrt(r2);
-    R W = quintic_w<R>(r * S.inv_h);
-    S0 += W;
-    P0 += sp[k] * W;
-    R rw = sr[k] * W;
-    Rv[0] += rw * dx; Rv[1] += rw * dy; Rv[2] += rw * dz;
-    U[0] += su[k] * W; U[1] += sv[k] * W; U[2] += sw[k] * W;
-  }
-};
-
-template <class R, int DIM>
-__global__ void __launch_bounds__(128) k_extrap(BatchView<R> B) {
-  __shared__ R sm[4][8][32];
-  __shared__ int smk[4][32];
-  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  ExtrapPol<R, DIM> pol;
-  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2]; pol.sp = sm[wib][3];
-  pol.sr = sm[wib][4]; pol.su = sm[wib][5]; pol.sv = sm[wib][6]; pol.sw = sm[wib][7];
-  pol.sk = smk[wib];
-  int total = __ldg(B.pfx_grp + B.nsc);
-  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  for (int g = gw; g < total; g += nw) {
-    int s = find_scene(B.pfx_grp, B.nsc, g);
-    const Scene<R>& S = *B.sc[s];
-    Group<R, DIM> G = group_of<R, DIM>(S, g - __ldg(B.pfx_grp + s));
-    for (int tb = G.ts; tb < G.te; tb += 32) {
-      int i = tb + lane;
-      bool valid = i < G.te;
-      pol.active = valid && S.matR[S.P.mt[i]].kind != KFLUID;
-      if (!__any_sync(FULL, pol.active)) continue;
-      pol.idx = valid ? i : -1;
-      if (valid) target_pos(S, i, G.cx0, pol.tp);
-      pol.S0 = pol.P0 = R(0);
-      for (int q = 0; q < 3; q++) pol.Rv[q] = pol.U[q] = R(0);
-      pol.hits = 0;
-      traverse<R, DIM>(S, G, pol, lane);
-      if (pol.active) {
-        R uw[3] = {S.P.vx[i], S.P.vy[i], S.P.vz[i]};  // prescribed wall / rigid velocity
-        if (pol.S0 > R(0)) {
-          R aw[3] = {R(0), R(0), R(0)};
-          if (S.matR[S.P.mt[i]].kind == KRIGID) { aw[0] = S.P.ax[i]; aw[1] = S.P.ay[i]; aw[2] = S.P.az[i]; }
-          R ga = (S.gR[0] - aw[0]) * pol.Rv[0] + (S.gR[1] - aw[1]) * pol.Rv[1] + (S.gR[2] - aw[2]) * pol.Rv[2];
-          R inv = R(1) / pol.S0;
-          S.prs[i] = (pol.P0 + ga) * inv;
-          S.vex[i] = R(2) * uw[0] - pol.U[0] * inv;
-          S.vey[i] = R(2) * uw[1] - pol.U[1] * inv;
-          S.vez[i] = R(2) * uw[2] - pol.U[2] * inv;
-        } else {
-          S.prs[i] = R(0);
-          S.vex[i] = uw[0]; S.vey[i] = uw[1]; S.vez[i] = uw[2];
-        }
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------- sweep 3: forces and heat
-template <class R, int DIM>
-struct ForcePol {
-  // staged candidate fields
-  R *sx, *sy, *sz, *su, *sv, *sw, *sex, *sey, *sez, *sr, *sp, *sm, *sT;
-  int *smt, *sb;
-  bool active;
-  int idx;
-  R tp[3];
-  // target fields
-  int tkind, tmat, tbody;
-  R tu[3], tve[3], trho, tp0, tm, tT, tV2, teta, tkap;
-  const MatR<R>* tM;
-  // accumulators
-  R acc[3], heat;
-  unsigned long long hits;
-  __device__ void stage(const Scene<R>& S, int j, int lane) {
-    sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
-    su[lane] = S.P.vx[j]; sv[lane] = S.P.vy[j]; sw[lane] = S.P.vz[j];
-    sex[lane] = S.vex[j]; sey[lane] = S.vey[j]; sez[lane] = S.vez[j];
-    sr[lane] = S.P.rho[j]; sp[lane] = S.prs[j]; sm[lane] = S.P.m[j]; sT[lane] = S.P.T[j];
-    smt[lane] = S.P.mt[j]; sb[lane] = S.P.body[j];
-  }
-  __device__ bool accept(int) const { return true; }
-  __device__ void pair(const Scene<R>& S, int k, int, R dx, R dy, R dz, R r2) {
-    const MatR<R>& Bm = S.matR[smt[k]];
-    int bkind = Bm.kind;
-    R inv_r = rsqrt_<R>(r2);
-    R r = r2 * inv_r;
-    R dW = S.sig_dw * quintic_dw<R>(r * S.inv_h);
-    R ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
-    // heat conduction (Cleary & Monaghan), walls Dirichlet or adiabatic
-    if (S.any_heat) {
-      R Tb = sT[k];
-      R kb = bkind == KWALL ? tkap : Bm.kappa;
-      bool on = !(bkind == KWALL && isnan(Tb));
-      if (on) {
-        R ks = tkap + kb;
-        R kab = ks > R(0) ? R(4) * tkap * kb / ks : R(0);
-        R Vb = sm[k] / sr[k];
-        heat += Vb * kab * (tT - Tb) * inv_r * dW;
-      }
-    }
-    if (tkind == KFLUID) {
-      R rhoj, pj, Vj, etaj, uj[3];
-      if (bkind == KFLUID) {
-        rhoj = sr[k]; pj = sp[k]; Vj = sm[k] / rhoj; etaj = Bm.eta;
-        uj[0] = su[k]; uj[1] = sv[k]; uj[2] = sw[k];
-      } else {
-        pj = sp[k];
-        rhoj = tM->rho0 * (pj * tM->inv_p0 + R(1));
-        Vj = sm[k] / sr[k];
-        etaj = teta;
-        uj[0] = sex[k]; uj[1] = sey[k]; uj[2] = sez[k];
-      }
-      R pt = (rhoj * tp0 + trho * pj) / (trho + rhoj);
-      R es = teta + etaj;
-      R et = es > R(0) ? R(2) * teta * etaj / es : R(0);
-      R coef = (tV2 + Vj * Vj) * dW;
-      R vis = et * inv_r;
-      acc[0] += coef * (-pt * ex + vis * (tu[0] - uj[0]));
-      acc[1] += coef * (-pt * ey + vis * (tu[1] - uj[1]));
-      acc[2] += coef * (-pt * ez + vis * (tu[2] - uj[2]));
-    } else {  // rigid target
-      if (bkind == KFLUID) {
-        // -m_j a_jr seen from the fluid particle j (Eq. couplingforce)
-        R rhoj = sr[k], pj = sp[k], Vj = sm[k] / rhoj;
-        R rs = Bm.rho0 * (tp0 * Bm.inv_p0 + R(1));  // inverse EOS of fluid j for p_r
-        R pt = (rs * pj + rhoj * tp0) / (rhoj + rs);
-        R coef = (Vj * Vj + tV2) * dW;
-        R vis = Bm.eta * inv_r;
-        // e_jr = -e, u_jr = u_j - v_r
-        acc[0] -= coef * (pt * ex + vis * (su[k] - tve[0]));
-        acc[1] -= coef * (pt * ey + vis * (sv[k] - tve[1]));
-        acc[2] -= coef * (pt * ez + vis * (sw[k] - tve[2]));
-      } else if (bkind == KWALL || sb[k] != tbody) {
-        if (r < S.dxR) {  // Eq. contactforce with tension cut-off
-          R ev = ex * (tu[0] - su[k]) + ey * (tu[1] - sv[k]) + ez * (tu[2] - sw[k]);
-          R fn = S.kcR * (r - S.dxR) + S.dcR * ev;
-          R mn = fn < R(0) ? fn : R(0);
-          acc[0] -= mn * ex; acc[1] -= mn * ey; acc[2] -= mn * ez;
-        }
-      }
-    }
-  }
-};
-
-template <class R, int DIM>
-__global__ void __launch_bounds__(128) k_force(BatchView<R> B) {
-  __shared__ R sm[4][13][32];
-  __shared__ int smi[4][2][32];
-  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  ForcePol<R, DIM> pol;
-  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
-  pol.su = sm[wib][3]; pol.sv = sm[wib][4]; pol.sw = sm[wib][5];
-  pol.sex = sm[wib][6]; pol.sey = sm[wib][7]; pol.sez = sm[wib][8];
-  pol.sr = sm[wib][9]; pol.sp = sm[wib][10]; pol.sm = sm[wib][11]; pol.sT = sm[wib][12];
-  pol.smt = smi[wib][0]; pol.sb = smi[wib][1];
-  int total = __ldg(B.pfx_grp + B.nsc);
-  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  for (int g = gw; g < total; g += nw) {
-    int s = find_scene(B.pfx_grp, B.nsc, g);
-    const Scene<R>& S = *B.sc[s];
-    Group<R, DIM> G = group_of<R, DIM>(S, g - __ldg(B.pfx_grp + s));
-    unsigned long long wh = 0;
-    for (int tb = G.ts; tb < G.te; tb += 32) {
-      int i = tb + lane;
-      bool valid = i < G.te;
-      int tm = valid ? S.P.mt[i] : 0;
-      pol.tkind = S.matR[tm].kind;
-      pol.active = valid && pol.tkind != KWALL;
-      if (!__any_sync(FULL, pol.active)) continue;
-      pol.idx = valid ? i : -1;
-      pol.hits = 0;
-      pol.acc[0] = pol.acc[1] = pol.acc[2] = R(0);
-      pol.heat = R(0);
-      if (pol.active) {
-        target_pos(S, i, G.cx0, pol.tp);
-        pol.tmat = tm;
-        pol.tM = &S.matR[tm];
-        pol.tbody = S.P.body[i];
-        pol.tu[0] = S.P.vx[i]; pol.tu[1] = S.P.vy[i]; pol.tu[2] = S.P.vz[i];
-        pol.tve[0] = S.vex[i]; pol.tve[1] = S.vey[i]; pol.tve[2] = S.vez[i];
-        pol.trho = S.P.rho[i];
-        pol.tp0 = S.prs[i];
-        pol.tm = S.P.m[i];
-        pol.tT = S.P.T[i];
-        R V = pol.tm / pol.trho;
-        pol.tV2 = V * V;
-        pol.teta = pol.tM->eta;
-        pol.tkap = pol.tM->kappa;
-      }
-      traverse<R, DIM>(S, G, pol, lane);
-      wh += pol.active ? pol.hits : 0ull;
-      if (pol.active) {
-        if (pol.tkind == KFLUID) {
-          R im = R(1) / pol.tm;
-          S.P.ax[i] = S.gR[0] + pol.acc[0] * im;
-          S.P.ay[i] = S.gR[1] + pol.acc[1] * im;
-          S.P.az[i] = S.gR[2] + pol.acc[2] * im;
-        } else {
-          int sl = S.P.slot[i];
-          S.fr[3 * sl] = pol.acc[0];
-          S.fr[3 * sl + 1] = pol.acc[1];
-          S.fr[3 * sl + 2] = pol.acc[2];
-        }
-        R rate = pol.heat / pol.trho;  // c_p dT/dt = dH/dt
-        if (S.has_source && S.mat[tm].src) {
-          double x[3];
-          abs_pos<R>(S, i, x);
-          double t = S.st[1] + S.st[0];
-          int vz = S.dim - 1;
-          double dd = 0.0;
-          for (int q = 0; q < S.dim; q++)
-            if (q != vz) {
-              double c = x[q] - (S.src_x0[q] + S.src_v[q] * t);
-              dd += c * c;
-            }
-          if (S.src_ztop - x[vz] < S.src_depth)
-            rate += (R)(S.src_Q * exp(-2.0 * dd / (S.src_r * S.src_r))) / pol.trho;
-        }
-        S.dT[i] = pol.tM->enth ? rate : rate / pol.tM->cp;
-      }
-    }
-    for (int o = 16; o; o >>= 1) wh += __shfl_xor_sync(FULL, wh, o);
-    if (lane == 0 && wh) atomicAdd(S.pairs, wh);
-  }
-}
+namespace sph {
 
 // ============================================================================ bodies (FP64)
 // force and torque of every body (Eq. procwise_force with thread partials as the

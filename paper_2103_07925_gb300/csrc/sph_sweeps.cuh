@@ -1,0 +1,353 @@
+// The three pair sweeps of a step.
+//
+//  k_search   one warp per target group: cell-list candidate tests (staged in shared
+//             memory), the neighbour list of every particle (index and cell-offset code
+//             per entry, layout list[k * n + i] so that a warp of consecutive targets
+//             reads one line per k), and the density summation + EOS of fluid targets
+//             (Eq. densum, Eq. eos).
+//  k_extrap   one thread per wall / rigid target over its list: extrapolation of pressure
+//             and velocity from the fluid (Adami et al. 2012, cited in Sec. 3.3.4).
+//  k_force    one thread per fluid / rigid target over its list: Eq. momentum,
+//             Eq. couplingforce, Eq. contactforce, Eq. heat_equation.
+// A target whose neighbour count exceeds the list capacity scans its 3^d cells directly
+// (same predicate and order, so the result does not depend on the path taken).
+#pragma once
+#include "sph_kernels.cuh"
+
+namespace sph {
+
+template <class R> __device__ __forceinline__ R qdiv(R a, R b);
+template <> __device__ __forceinline__ double qdiv<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
+
+// warp-aggregated add to a per-scene counter (one atomic per scene present in the warp)
+__device__ __forceinline__ void warp_add(int s, unsigned long long v, unsigned long long* ptr) {
+  unsigned pending = FULL;
+  while (pending) {
+    int leader = __ffs(pending) - 1;
+    int cs = __shfl_sync(FULL, s, leader);
+    unsigned long long x = s == cs ? v : 0ull;
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    if ((int)(threadIdx.x & 31) == leader && x) atomicAdd(ptr, x);
+    pending &= ~__ballot_sync(FULL, s == cs);
+  }
+}
+
+// ---------------------------------------------------------------- search + density
+template <class R, int DIM>
+struct SearchPol {
+  R *sx, *sy, *sz;
+  bool active, fluid;
+  int idx, tx, n, maxnb, cnt;
+  int cox, cdy, cdz;
+  int* list;
+  R tp[3];
+  R acc;
+  unsigned long long hits;
+  __device__ void stage(const Scene<R>& S, int j, int lane) {
+    sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
+  }
+  __device__ bool accept(int) const { return true; }
+  __device__ void pair(const Scene<R>& S, int, int j, R, R, R, R r2) {
+    int code = (cox - tx + 1) + 3 * (cdy + 1) + 9 * (cdz + 1);
+    if (cnt < maxnb) list[(size_t)cnt * n + idx] = (j << 5) | code;
+    cnt++;
+    if (fluid) acc += quintic_w<R>(sqrt(r2) * S.inv_h);
+  }
+};
+
+template <class R, int DIM>
+__global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
+  __shared__ R sm[4][3][32];
+  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  SearchPol<R, DIM> pol;
+  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
+  int total = __ldg(B.pfx_grp + B.nsc);
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int g = gw; g < total; g += nw) {
+    int s = find_scene(B.pfx_grp, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    Group<R, DIM> G = group_of<R, DIM>(S, g - __ldg(B.pfx_grp + s));
+    pol.list = S.nbl;
+    pol.n = S.n;
+    pol.maxnb = S.maxnb;
+    for (int tb = G.ts; tb < G.te; tb += 32) {
+      int i = tb + lane;
+      bool valid = i < G.te;
+      pol.active = valid;
+      if (!__any_sync(FULL, valid)) continue;
+      pol.idx = valid ? i : -1;
+      pol.fluid = valid && S.matR[S.P.mt[i]].kind == KFLUID;
+      pol.tx = 0;
+      if (valid) {
+        target_pos(S, i, G.cx0, pol.tp);
+        if (G.ncx > 1) pol.tx = key_lin(S, S.key[i]) % S.ncell[0] - G.cx0;
+      }
+      pol.acc = R(0);
+      pol.cnt = 0;
+      pol.hits = 0;
+      traverse<R, DIM>(S, G, pol, lane);
+      if (valid) {
+        S.nbc[i] = pol.cnt;
+        R rho = S.P.rho[i];
+        if (pol.fluid) {
+          const MatR<R>& A = S.matR[S.P.mt[i]];
+          rho = S.P.m[i] * (S.w0 + S.sig_w * pol.acc);
+          S.P.rho[i] = rho;
+          S.prs[i] = A.c2 * (rho - A.rho0);
+        }
+        S.vol[i] = qdiv<R>(S.P.m[i], rho);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- pair geometry from a list entry
+// d = r_i - r_j: FP64 absolute positions with the minimum image on periodic axes (the same
+// arithmetic as the cell traversal); FP32 cell-relative offsets minus the cell offset
+template <class R, int DIM>
+__device__ __forceinline__ void list_delta(const Scene<R>& S, const R* ti, int j, int code, R* d) {
+  if (sizeof(R) == 8) {
+    d[0] = dsub(ti[0], S.P.px[j]);
+    d[1] = dsub(ti[1], S.P.py[j]);
+    d[2] = DIM == 3 ? dsub(ti[2], S.P.pz[j]) : R(0);
+    for (int k = 0; k < DIM; k++)
+      if (S.per[k]) {
+        R h = R(0.5) * S.LR[k];
+        if (d[k] > h) d[k] = dsub(d[k], S.LR[k]);
+        else if (d[k] < -h) d[k] = dsub(d[k], -S.LR[k]);
+      }
+  } else {
+    int ox = code % 3 - 1, oy = (code / 3) % 3 - 1, oz = code / 9 - 1;
+    d[0] = (ti[0] - S.P.px[j]) - (R)ox * S.ellR[0];
+    d[1] = (ti[1] - S.P.py[j]) - (R)oy * S.ellR[1];
+    d[2] = DIM == 3 ? (ti[2] - S.P.pz[j]) - (R)oz * S.ellR[2] : R(0);
+  }
+}
+
+// scan of the 3^d cells around target i (targets whose list overflowed); calls
+// f(j, code) for every candidate j != i in the traversal order of k_search
+template <class R, int DIM, class F>
+__device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
+  int cx, cy, cz;
+  lin_xyz(S, key_lin(S, S.key[i]), cx, cy, cz);
+  const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
+  for (int dz = zlo; dz <= zhi; dz++)
+    for (int dy = -1; dy <= 1; dy++)
+      for (int dx = -1; dx <= 1; dx++) {
+        int c[3] = {cx + dx, cy + dy, cz + dz};
+        bool skip = false;
+        for (int k = 0; k < DIM; k++)
+          if (c[k] < 0 || c[k] >= S.ncell[k]) {
+            if (!S.per[k]) skip = true;
+            else c[k] = c[k] < 0 ? c[k] + S.ncell[k] : c[k] - S.ncell[k];
+          }
+        if (skip) continue;
+        if (DIM == 2) c[2] = 0;
+        int key = cell_key(S, c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]));
+        int a = max(S.cstart[key], 0), e = min(S.cstart[key + 1], S.n);
+        int code = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+        for (int j = a; j < e; j++)
+          if (j != i) f(j, code);
+      }
+}
+
+// ---------------------------------------------------------------- extrapolation (walls, rigid)
+template <class R, int DIM>
+__global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
+  int total = __ldg(B.pfx_part + B.nsc);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int s = find_scene(B.pfx_part, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    int i = g - __ldg(B.pfx_part + s);
+    int kind = S.matR[S.P.mt[i]].kind;
+    if (kind == KFLUID) continue;
+    R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
+    R S0 = R(0), P0 = R(0), Rv[3] = {R(0), R(0), R(0)}, U[3] = {R(0), R(0), R(0)};
+    auto visit = [&](int j, int code) {
+      if (S.matR[S.P.mt[j]].kind != KFLUID) return;
+      R d[3];
+      list_delta<R, DIM>(S, ti, j, code, d);
+      R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+      if (!(r2 < S.rc2R)) return;
+      R W = quintic_w<R>(sqrt(r2) * S.inv_h);
+      S0 += W;
+      P0 += S.prs[j] * W;
+      R rw = S.P.rho[j] * W;
+      Rv[0] += rw * d[0]; Rv[1] += rw * d[1]; Rv[2] += rw * d[2];
+      U[0] += S.P.vx[j] * W; U[1] += S.P.vy[j] * W; U[2] += S.P.vz[j] * W;
+    };
+    int cnt = S.nbc[i];
+    if (cnt <= S.maxnb) {
+      const int* L = S.nbl + i;
+      for (int k = 0; k < cnt; k++) {
+        int e = __ldg(L + (size_t)k * S.n);
+        visit(e >> 5, e & 31);
+      }
+    } else {
+      scan_cells<R, DIM>(S, i, visit);
+    }
+    R uw[3] = {S.P.vx[i], S.P.vy[i], S.P.vz[i]};  // prescribed wall / rigid velocity
+    if (S0 > R(0)) {
+      R aw[3] = {R(0), R(0), R(0)};
+      if (kind == KRIGID) { aw[0] = S.P.ax[i]; aw[1] = S.P.ay[i]; aw[2] = S.P.az[i]; }
+      R ga = (S.gR[0] - aw[0]) * Rv[0] + (S.gR[1] - aw[1]) * Rv[1] + (S.gR[2] - aw[2]) * Rv[2];
+      R inv = R(1) / S0;
+      S.prs[i] = (P0 + ga) * inv;
+      S.vex[i] = R(2) * uw[0] - U[0] * inv;
+      S.vey[i] = R(2) * uw[1] - U[1] * inv;
+      S.vez[i] = R(2) * uw[2] - U[2] * inv;
+    } else {
+      S.prs[i] = R(0);
+      S.vex[i] = uw[0]; S.vey[i] = uw[1]; S.vez[i] = uw[2];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- forces and heat
+template <class R>
+struct Target {
+  int kind, body;
+  const MatR<R>* M;
+  R rho, p, V2, eta, kap, T;
+  R u[3], ve[3];
+};
+
+template <class R, int DIM>
+__device__ __forceinline__ void force_pair(const Scene<R>& S, const Target<R>& t, int j, const R* d, R r2,
+                                           R* acc, R& heat) {
+  const MatR<R>& Bm = S.matR[S.P.mt[j]];
+  int bk = Bm.kind;
+  R inv_r = rsqrt_<R>(r2);
+  R r = r2 * inv_r;
+  R dW = S.sig_dw * quintic_dw<R>(r * S.inv_h);
+  R ex = d[0] * inv_r, ey = d[1] * inv_r, ez = d[2] * inv_r;
+  R Vj = S.vol[j];
+  // heat conduction (Cleary & Monaghan), walls Dirichlet (kappa_b = kappa_a) or adiabatic
+  if (S.any_heat) {
+    R Tb = S.P.T[j];
+    if (!(bk == KWALL && isnan(Tb))) {
+      R kb = bk == KWALL ? t.kap : Bm.kappa;
+      R ks = t.kap + kb;
+      R kab = ks > R(0) ? qdiv<R>(R(4) * t.kap * kb, ks) : R(0);
+      heat += Vj * kab * (t.T - Tb) * inv_r * dW;
+    }
+  }
+  if (t.kind == KFLUID) {
+    R rhoj, pj, etaj, uj[3];
+    pj = S.prs[j];
+    if (bk == KFLUID) {
+      rhoj = S.P.rho[j];
+      etaj = Bm.eta;
+      uj[0] = S.P.vx[j]; uj[1] = S.P.vy[j]; uj[2] = S.P.vz[j];
+    } else {  // wall / rigid: inverse EOS of fluid i for the extrapolated pressure
+      rhoj = t.M->rho0 * (pj * t.M->inv_p0 + R(1));
+      etaj = t.eta;
+      uj[0] = S.vex[j]; uj[1] = S.vey[j]; uj[2] = S.vez[j];
+    }
+    R pt = qdiv<R>(rhoj * t.p + t.rho * pj, t.rho + rhoj);
+    R es = t.eta + etaj;
+    R et = es > R(0) ? qdiv<R>(R(2) * t.eta * etaj, es) : R(0);
+    R coef = (t.V2 + Vj * Vj) * dW;
+    R vis = et * inv_r;
+    acc[0] += coef * (-pt * ex + vis * (t.u[0] - uj[0]));
+    acc[1] += coef * (-pt * ey + vis * (t.u[1] - uj[1]));
+    acc[2] += coef * (-pt * ez + vis * (t.u[2] - uj[2]));
+  } else if (bk == KFLUID) {  // rigid target: -m_j a_jr seen from fluid particle j
+    R rhoj = S.P.rho[j], pj = S.prs[j];
+    R rs = Bm.rho0 * (t.p * Bm.inv_p0 + R(1));
+    R pt = qdiv<R>(rs * pj + rhoj * t.p, rhoj + rs);
+    R coef = (Vj * Vj + t.V2) * dW;
+    R vis = Bm.eta * inv_r;
+    acc[0] -= coef * (pt * ex + vis * (S.P.vx[j] - t.ve[0]));
+    acc[1] -= coef * (pt * ey + vis * (S.P.vy[j] - t.ve[1]));
+    acc[2] -= coef * (pt * ez + vis * (S.P.vz[j] - t.ve[2]));
+  } else if (bk == KWALL || S.P.body[j] != t.body) {
+    if (r < S.dxR) {  // Eq. contactforce with tension cut-off
+      R ev = ex * (t.u[0] - S.P.vx[j]) + ey * (t.u[1] - S.P.vy[j]) + ez * (t.u[2] - S.P.vz[j]);
+      R fn = S.kcR * (r - S.dxR) + S.dcR * ev;
+      R mn = fn < R(0) ? fn : R(0);
+      acc[0] -= mn * ex; acc[1] -= mn * ey; acc[2] -= mn * ez;
+    }
+  }
+}
+
+template <class R, int DIM>
+__global__ void __launch_bounds__(256) k_force(BatchView<R> B) {
+  int total = __ldg(B.pfx_part + B.nsc);
+  int nthr = gridDim.x * blockDim.x;
+  // uniform trip count so that the warp-wide pair counter sees every lane
+  for (int g0 = blockIdx.x * blockDim.x; g0 < total; g0 += nthr) {
+    int g = g0 + threadIdx.x;
+    int s = find_scene(B.pfx_part, B.nsc, min(g, total - 1));
+    const Scene<R>& S = *B.sc[s];
+    unsigned long long npairs = 0;
+    int i = g - __ldg(B.pfx_part + s);
+    int tm = g < total ? S.P.mt[i] : 0;
+    int kind = S.matR[tm].kind;
+    if (g < total && kind != KWALL) {
+      Target<R> t;
+      t.kind = kind;
+      t.body = S.P.body[i];
+      t.M = &S.matR[tm];
+      t.rho = S.P.rho[i];
+      t.p = S.prs[i];
+      R V = S.vol[i];
+      t.V2 = V * V;
+      t.eta = t.M->eta;
+      t.kap = t.M->kappa;
+      t.T = S.P.T[i];
+      t.u[0] = S.P.vx[i]; t.u[1] = S.P.vy[i]; t.u[2] = S.P.vz[i];
+      t.ve[0] = S.vex[i]; t.ve[1] = S.vey[i]; t.ve[2] = S.vez[i];
+      R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
+      R acc[3] = {R(0), R(0), R(0)}, heat = R(0);
+      auto visit = [&](int j, int code) {
+        R d[3];
+        list_delta<R, DIM>(S, ti, j, code, d);
+        R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+        if (r2 < S.rc2R) force_pair<R, DIM>(S, t, j, d, r2, acc, heat);
+      };
+      int cnt = S.nbc[i];
+      npairs = (unsigned long long)cnt;
+      if (cnt <= S.maxnb) {
+        const int* L = S.nbl + i;
+        for (int k = 0; k < cnt; k++) {
+          int e = __ldg(L + (size_t)k * S.n);
+          visit(e >> 5, e & 31);
+        }
+      } else {
+        scan_cells<R, DIM>(S, i, visit);
+      }
+      if (kind == KFLUID) {
+        R im = R(1) / S.P.m[i];
+        S.P.ax[i] = S.gR[0] + acc[0] * im;
+        S.P.ay[i] = S.gR[1] + acc[1] * im;
+        S.P.az[i] = S.gR[2] + acc[2] * im;
+      } else {
+        int sl = S.P.slot[i];
+        S.fr[3 * sl] = acc[0];
+        S.fr[3 * sl + 1] = acc[1];
+        S.fr[3 * sl + 2] = acc[2];
+      }
+      R rate = heat / t.rho;  // c_p dT/dt = dH/dt
+      if (S.has_source && S.mat[tm].src) {
+        double x[3];
+        abs_pos<R>(S, i, x);
+        double tt = S.st[1] + S.st[0];
+        int vz = S.dim - 1;
+        double dd = 0.0;
+        for (int q = 0; q < S.dim; q++)
+          if (q != vz) {
+            double c = x[q] - (S.src_x0[q] + S.src_v[q] * tt);
+            dd += c * c;
+          }
+        if (S.src_ztop - x[vz] < S.src_depth)
+          rate += (R)(S.src_Q * exp(-2.0 * dd / (S.src_r * S.src_r))) / t.rho;
+      }
+      S.dT[i] = t.M->enth ? rate : rate / t.M->cp;
+    }
+    warp_add(s, npairs, S.pairs);
+  }
+}
+
+}  // namespace sph
