@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--key-order", type=int, default=0)
     ap.add_argument("--dx", type=float, default=0.01)
+    ap.add_argument("--skin", type=float, default=0.3, help="Verlet skin in units of h")
     return ap.parse_args()
 
 
@@ -200,7 +201,8 @@ def main():
     hbm, smmax, peak_src = peaks()
     sc = workload(args.dx)
     stream = torch.cuda.Stream()
-    g = Scene(sc, precision=args.precision, stream=stream.cuda_stream, key_order=args.key_order)
+    skin = args.skin * sc["params"]["h"]
+    g = Scene(sc, precision=args.precision, stream=stream.cuda_stream, key_order=args.key_order, skin=skin)
     info = g.info()
     g.step(args.warmup)
     clocks = Clocks(local)
@@ -242,10 +244,12 @@ def main():
                       "wall": info["n_wall"], "bodies": info["n_bodies"], "cells": info["n_cells"],
                       "precision": "FP32 pair sums, FP64 bodies" if args.precision == 32 else "FP64",
                       "key_order": "morton" if args.key_order == 0 else "row-major",
+                      "skin_h": args.skin,
                       "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (info["bytes"] / 1e6),
                       "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
            "steps_per_s": steps_per_s * world,
            "pairs_per_step": pairs_per_step,
+           "list_rebuilds": g.info()["rebuilds"],
            "gpu_launches": args.steps * g.info()["kernels_per_step"],
            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                         "frac": achieved_tf / peak_tf, "traffic": None, "kernel": "k_force",
@@ -256,7 +260,7 @@ def main():
     # plain FP64 path on the same workload
     if not args.no_fp64 and args.precision == 32:
         s64 = torch.cuda.Stream()
-        g64 = Scene(sc, precision=64, stream=s64.cuda_stream, key_order=args.key_order)
+        g64 = Scene(sc, precision=64, stream=s64.cuda_stream, key_order=args.key_order, skin=skin)
         g64.step(2)
         k64 = max(5, min(args.steps // 10, 30))
         q0 = g64.info()["pairs_total"]

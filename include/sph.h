@@ -68,7 +68,13 @@ typedef struct {
  *                   with dt_ref = 0.25 h / c_max and m_r the smallest rigid particle mass
  *  precision        64: FP64 everywhere; 32: FP32 pair sums with cell-relative positions,
  *                   FP64 body sums, orientation and diagnostics
- *  rebin_interval   steps between cell re-binning (1 = every step, the exact method)
+ *  skin             Verlet skin (Sec. 3.2 combines Verlet and cell lists): neighbour lists
+ *                   hold pairs closer than r_c + skin and are rebuilt (with the cell
+ *                   binning) when some particle has moved more than skin / 2 since the last
+ *                   rebuild, so every evaluation still sees exactly the pairs closer than
+ *                   r_c.  0: rebuild every step.  Cells have edge >= r_c + skin.
+ *  rebin_interval   with skin > 0: also rebuild at least every rebin_interval steps (0: no
+ *                   forced rebuild)
  *  key_order        0: Morton order of cells;  1: row-major order (x fastest)
  *  cells_per_group  cells along x handled by one warp (0 = automatic; row-major only)
  *  body_capacity    maximum number of bodies including those created by solidification
@@ -87,6 +93,7 @@ typedef struct {
   double dt_fixed;
   double k_contact, d_contact;
   int32_t precision;
+  double skin;
   int32_t rebin_interval;
   int32_t key_order;
   int32_t cells_per_group;
@@ -188,13 +195,14 @@ sph_status sph_neighbors(sph_scene* scene, int64_t* counts, int32_t* list, int64
 /* Scene information: [0] n, [1] fluid, [2] rigid, [3] wall, [4] bodies, [5] cells,
  * [6] cells x, [7] cells y, [8] cells z, [9] steps taken, [10] kernels per step,
  * [11] device bytes, [12] warp groups, [13] cells per group, [14] key order,
- * [15] ordered pairs evaluated by the force / heat sweep over all steps taken. */
-sph_status sph_info(sph_scene* scene, int64_t out[16]);
+ * [15] ordered pairs evaluated by the force / heat sweep over all steps taken,
+ * [16] neighbour-list rebuilds so far, [17] list capacity per particle.  out[] has 32 rows. */
+sph_status sph_info(sph_scene* scene, int64_t out[32]);
 
 /* Tracing: run reps complete steps with the kernels launched one by one (no graph) and
  * CUDA events between them; ms_per_stage[SPH_PROFILE_STAGES] receives the mean device
  * time of each stage.  The scene advances by reps steps. */
-#define SPH_PROFILE_STAGES 18
+#define SPH_PROFILE_STAGES 20
 sph_status sph_profile(sph_scene* scene, int32_t reps, double* ms_per_stage);
 const char* sph_profile_stage_name(int32_t stage);
 

@@ -38,7 +38,7 @@ class _Params(C.Structure):
                 ("materials", _Mat * ORC_MAXMAT), ("body_capacity", C.c_int32),
                 ("src_power", C.c_double), ("src_radius", C.c_double), ("src_speed", C.c_double * 3),
                 ("src_origin", C.c_double * 3), ("src_depth", C.c_double), ("src_ztop", C.c_double),
-                ("force_brute", C.c_int32)]
+                ("skin", C.c_double), ("force_brute", C.c_int32)]
 
 
 def lib():
@@ -114,6 +114,7 @@ def _params(scene, force_brute=False):
     P.src_radius = p["src_radius"]
     P.src_depth = p["src_depth"]
     P.src_ztop = p.get("src_ztop", 0.0)
+    P.skin = p.get("skin", 0.0)
     P.force_brute = 1 if force_brute else 0
     return P
 

@@ -14,7 +14,7 @@
  *      (terms dropped when negative), q = r/h, s_2 = 7/(478 pi h^2), s_3 = 1/(120 pi h^3),
  *      support r_c = 3h (Remark on the applied kernel, Sec. 3.1.1).
  *  R2  neighbour set N(a) = { b != a : r_ab^2 < r_c^2 }, r^2 = (dx*dx + dy*dy) + dz*dz,
- *      minimum image on periodic axes.  Cells: n_d = max(1, floor(L_d / r_c)),
+ *      minimum image on periodic axes.  Cells: n_d = max(1, floor(L_d / (r_c + skin))),
  *      edge L_d / n_d, c_d = clamp(floor((x_d - lo_d) / edge_d), 0, n_d - 1).
  *  R3  density summation (Eq. densum) over fluid targets, self term W(0) included,
  *      neighbours of every kind contribute; rigid and wall particles keep the density
@@ -963,7 +963,7 @@ orc_scene* orc_create(const orc_params* P, int64_t n, const double* pos, const d
   for (int d = 0; d < 3; d++) {
     if (d < P->dim) {
       double L = P->box_max[d] - P->box_min[d];
-      int32_t nc = (int32_t)floor(L / s->rc);
+      int32_t nc = (int32_t)floor(L / (s->rc + (P->skin > 0.0 ? P->skin : 0.0)));
       if (nc < 1) nc = 1;
       s->ncell[d] = nc;
       s->ell[d] = L / nc;

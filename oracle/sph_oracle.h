@@ -47,6 +47,7 @@ typedef struct {
   orc_material materials[ORC_MAXMAT];
   int32_t body_capacity;
   double src_power, src_radius, src_speed[3], src_origin[3], src_depth, src_ztop;
+  double skin;         /* cells of the neighbour search have edge >= r_c + skin */
   int32_t force_brute; /* 1: brute-force O(N^2) neighbour search */
 } orc_params;
 

@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(128) k_neighbors(Scene<R>* const* sc, int ngro
       pol.cnt = 0;
       pol.off = (valid && offs) ? offs[S.P.orig[i]] : 0;
       pol.hits = 0;
-      traverse<R, DIM>(S, G, pol, lane);
+      traverse<R, DIM>(S, G, pol, lane, S.rc2R);
       if (valid && !offs) counts[S.P.orig[i]] = pol.cnt;
     }
   }

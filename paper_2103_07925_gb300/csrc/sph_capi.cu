@@ -113,7 +113,7 @@ sph_status sph_neighbors(sph_scene* s, int64_t* counts, int32_t* list, int64_t c
   return s->e->neighbors(0, counts, list, cap, total);
 }
 
-sph_status sph_info(sph_scene* s, int64_t out[16]) {
+sph_status sph_info(sph_scene* s, int64_t out[32]) {
   if (!s || !out) { set_error("null argument"); return SPH_ERR_INVALID; }
   return s->e->info(0, out);
 }
@@ -124,9 +124,10 @@ sph_status sph_profile(sph_scene* s, int32_t reps, double* ms_per_stage) {
 }
 
 const char* sph_profile_stage_name(int32_t i) {
-  static const char* const names[] = {"umax", "dt", "body_kick_drift", "kick_drift", "bin", "scan_blocks",
-                                      "scan_top", "scan_cells", "scatter", "rank", "permute", "flip",
-                                      "search_density", "extrap", "force", "body_reduce", "final", "end_step"};
+  static const char* const names[] = {"umax", "dt", "body_kick_drift", "kick_drift", "decide", "bin",
+                                      "scan_blocks", "scan_top", "scan_cells", "scatter", "rank", "permute",
+                                      "flip", "search_density", "density", "extrap", "force", "body_reduce",
+                                      "final", "end_step"};
   if (i < 0 || i >= SPH_PROFILE_STAGES) return "";
   return names[i];
 }

@@ -52,8 +52,9 @@ struct Scene {
   R ellR[3], LR[3];
   double g[3];
   R gR[3];
-  double h, rc, rc2, dx;
-  R rc2R, inv_h, sig_w, sig_dw, w0;  // W = sig_w w(q), dW/dr = sig_dw w'(q)
+  double h, rc, rc2, dx, skin;
+  R rc2R, rl2R, inv_h, sig_w, sig_dw, w0;  // W = sig_w w(q), dW/dr = sig_dw w'(q); rl: list radius
+  R half_skin2;
   double kc, dc;
   R kcR, dcR, dxR;
   double src_Q, src_r, src_v[3], src_x0[3], src_depth, src_ztop;
@@ -69,6 +70,8 @@ struct Scene {
   R* vol;              // particle volume m / rho of the current evaluation
   int* nbl;            // neighbour lists: entry k of particle i at nbl[k * n + i] = j << 5 | cell code
   int* nbc;            // neighbour count of each particle (may exceed maxnb: then cells are scanned)
+  R *xr, *yr, *zr;     // positions at the last list rebuild (same frame as the bank)
+  unsigned long long* disp;  // bits of the largest squared displacement since the rebuild
   int maxnb;           // list capacity per particle
   int* key;            // cell key of each (sorted) particle
   int* where;          // input index -> current sorted index
@@ -91,7 +94,8 @@ struct Scene {
   // ---------------------------------------------------------------- per-step state
   double* st;          // [0] dt [1] time [2] step [3] dt of last step
   unsigned long long* umax;  // bits of max |u| over fluid particles (FP64, non-negative)
-  int* status;         // [0] non-finite flag, [1] relabel count, [2] capacity error
+  int* status;         // [0] non-finite flag [1] relabel count [2] capacity error [3] table error
+                       // [4] rebuild in this step [5] steps since rebuild [6] rebuild count
   int* pfx1;           // prefix tables of this scene alone (6 x 2 ints)
   Scene<R>** self;     // device array holding the address of this descriptor
   unsigned long long* pairs;  // [0] force-sweep pairs of the last evaluation

@@ -71,9 +71,9 @@ inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
     if (d < p->dim) {
       double L = p->box_max[d] - p->box_min[d];
       if (!(L > 0)) { set_error("box_max must exceed box_min"); return SPH_ERR_INVALID; }
-      int nc = (int)std::floor(L / S.rc);
+      int nc = (int)std::floor(L / (S.rc + (p->skin > 0.0 ? p->skin : 0.0)));
       if (nc < 1) nc = 1;
-      if (S.per[d] && nc < 3) { set_error("periodic axis %d needs at least 3 cells of edge >= r_c", d); return SPH_ERR_INVALID; }
+      if (S.per[d] && nc < 3) { set_error("periodic axis %d needs at least 3 cells of edge >= r_c + skin", d); return SPH_ERR_INVALID; }
       if (nc > (1 << 20)) { set_error("too many cells on axis %d", d); return SPH_ERR_INVALID; }
       S.ncell[d] = nc;
       S.L[d] = L;
@@ -88,7 +88,10 @@ inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
     if ((double)S.ncells * S.ncell[d] > 2.0e9) { set_error("cell lattice too large"); return SPH_ERR_INVALID; }
     S.ncells *= S.ncell[d];
   }
+  S.skin = p->skin > 0.0 ? p->skin : 0.0;
   S.rc2R = (R)S.rc2;
+  S.rl2R = (R)((S.rc + S.skin) * (S.rc + S.skin));
+  S.half_skin2 = (R)(0.25 * S.skin * S.skin);
   S.inv_h = (R)(1.0 / S.h);
   double sig = p->dim == 2 ? 7.0 / (478.0 * M_PI * S.h * S.h) : 1.0 / (120.0 * M_PI * S.h * S.h * S.h);
   S.sig_w = (R)sig;
@@ -286,8 +289,8 @@ class Engine {
   }
 
   static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid) {
-    size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 6 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
-                 (DIM == 3 ? 128 : 48) * sizeof(int);
+    size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 9 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
+                 (DIM == 3 ? 192 : 64) * sizeof(int);
     size_t cells = (size_t)(ncells + 1) * 4 * sizeof(int) + (size_t)(ncells / 1024 + 2) * sizeof(int);
     size_t bodies = (size_t)kcap * (60 * sizeof(double) + 3 * sizeof(int));
     size_t slots = (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R) + sizeof(int));
@@ -336,6 +339,14 @@ class Engine {
 namespace sph {
 
 // ------------------------------------------------------------------------------ helpers
+// list capacity: 1.3 x the lattice sites inside the list radius, rounded up to 32
+inline int list_capacity(int dim, double radius_in_dx) {
+  double ball = dim == 3 ? 4.0 / 3.0 * M_PI * radius_in_dx * radius_in_dx * radius_in_dx
+                         : M_PI * radius_in_dx * radius_in_dx;
+  int c = (int)std::ceil(1.3 * ball / 32.0) * 32;
+  return c < 32 ? 32 : c;
+}
+
 inline int grid_for(int64_t items, int per_block, int max_grid) {
   int64_t b = (items + per_block - 1) / per_block;
   if (b < 1) b = 1;
@@ -449,9 +460,14 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   }
   R** rx[] = {&S.prs, &S.dT, &S.vex, &S.vey, &S.vez, &S.vol};
   for (R** f : rx) SPH_TRY(A(f, (size_t)n));
-  S.maxnb = DIM == 3 ? 128 : 48;
+  S.maxnb = list_capacity(DIM, (S.rc + S.skin) / S.dx);
   SPH_TRY(A(&S.nbl, (size_t)S.maxnb * n));
   SPH_TRY(A(&S.nbc, (size_t)n));
+  SPH_TRY(A(&S.xr, (size_t)n));
+  SPH_TRY(A(&S.yr, (size_t)n));
+  SPH_TRY(A(&S.zr, (size_t)n));
+  SPH_TRY(A(&S.disp, 1));
+  SPH_CU(cudaMemsetAsync(S.disp, 0, sizeof(unsigned long long), stream));
   int** ix[] = {&S.key, &S.where, &S.tkey, &S.tloc, &S.bucket, &S.perm, &S.tshift};
   for (int** f : ix) SPH_TRY(A(f, (size_t)n));
   SPH_TRY(A(&S.cstart, (size_t)S.ncells + 1));
@@ -492,7 +508,10 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   SPH_CU(cudaMemsetAsync(S.ccount, 0, sizeof(int) * S.ncells, stream));
   SPH_CU(cudaMemsetAsync(S.st, 0, sizeof(double) * 8, stream));
   SPH_CU(cudaMemsetAsync(S.umax, 0, sizeof(unsigned long long), stream));
-  SPH_CU(cudaMemsetAsync(S.status, 0, sizeof(int) * 8, stream));
+  {
+    int st0[8] = {0, 0, 0, 0, 1, 0, 0, 0};  // [4]: the creation step builds the lists
+    SPH_CU(cudaMemcpyAsync(S.status, st0, sizeof(st0), cudaMemcpyHostToDevice, stream));
+  }
   SPH_CU(cudaMemsetAsync(S.pairs, 0, sizeof(unsigned long long) * 2, stream));
   for (int q = 0; q < 12; q++) SPH_CU(cudaMemsetAsync(*bd[q], 0, sizeof(double) * bdn[q] * kc, stream));
   SPH_CU(cudaMemsetAsync(S.balive, 0, sizeof(int) * kc, stream));
@@ -611,10 +630,11 @@ sph_status Engine<R, DIM>::remove_scene(int idx) {
 }
 
 // stage names of a step, in launch order (sph_profile reports one time per stage)
-static const char* const kStageNames[] = {"umax", "dt", "body_kick_drift", "kick_drift", "bin", "scan_blocks",
-                                          "scan_top", "scan_cells", "scatter", "rank", "permute", "flip",
-                                          "search_density", "extrap", "force", "body_reduce", "final", "end_step"};
-constexpr int kStages = 18;
+static const char* const kStageNames[] = {"umax", "dt", "body_kick_drift", "kick_drift", "decide", "bin",
+                                          "scan_blocks", "scan_top", "scan_cells", "scatter", "rank", "permute",
+                                          "flip", "search_density", "density", "extrap", "force", "body_reduce",
+                                          "final", "end_step"};
+constexpr int kStages = 20;
 
 // Launch one step.  With ev != nullptr an event is recorded before the first stage and
 // after every stage (stages that do not apply record an empty interval).
@@ -648,6 +668,8 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_kick_drift<R><<<gp, 256, 0, stream>>>(B);
   rec();
+  k_decide<R><<<gs, 128, 0, stream>>>(B);
+  rec();
   k_bin<R><<<gp, 256, 0, stream>>>(B, 0);
   rec();
   k_scan_blocks<R><<<gcb, 1024, 0, stream>>>(B, 0);
@@ -666,6 +688,8 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   rec();
+  k_density<R, DIM><<<gp, 256, 0, stream>>>(B);
+  rec();
   k_extrap<R, DIM><<<gp, 256, 0, stream>>>(B);
   rec();
   k_force<R, DIM><<<gp, 256, 0, stream>>>(B);
@@ -676,7 +700,7 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_end_step<R><<<gs, 128, 0, stream>>>(B);
   rec();
-  kcount += 15;
+  kcount += 17;
   kernels_per_step = kcount;
   SPH_CU(cudaGetLastError());
   return SPH_OK;

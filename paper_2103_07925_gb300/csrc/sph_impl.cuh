@@ -27,18 +27,22 @@ struct EngineImpl final : EngineIface {
   sph_status info(int idx, int64_t* out) override {
     const Scene<R>& S = e.hs[idx];
     const HostScene& M = e.meta[idx];
-    for (int q = 0; q < 16; q++) out[q] = 0;
+    for (int q = 0; q < 32; q++) out[q] = 0;
     out[0] = S.n; out[1] = M.nfluid; out[2] = M.nrigid; out[3] = M.nwall; out[4] = M.K0;
     out[5] = S.ncells; out[6] = S.ncell[0]; out[7] = S.ncell[1]; out[8] = S.ncell[2];
     out[9] = M.steps_done; out[10] = e.kernels_per_step; out[11] = (int64_t)M.bytes;
     out[12] = S.ngroups; out[13] = S.G; out[14] = S.key_order;
     unsigned long long pc[2] = {0, 0};
+    int st[8] = {0};
     if (cudaMemcpyAsync(pc, S.pairs, sizeof(pc), cudaMemcpyDeviceToHost, e.stream) != cudaSuccess ||
+        cudaMemcpyAsync(st, S.status, sizeof(st), cudaMemcpyDeviceToHost, e.stream) != cudaSuccess ||
         cudaStreamSynchronize(e.stream) != cudaSuccess) {
-      set_error("cannot read the pair counters");
+      set_error("cannot read the scene counters");
       return SPH_ERR_CUDA;
     }
     out[15] = (int64_t)pc[1];
+    out[16] = st[6];
+    out[17] = S.maxnb;
     return SPH_OK;
   }
   sph_status profile(int32_t reps, double* ms) override { return e.profile(reps, ms); }

@@ -225,13 +225,25 @@ __global__ void k_body_kick_drift(BatchView<R> B) {
 // fluid: u += dt/2 a, r += dt u;  rigid: r_r = r_k + R r_rk, u_r = u_k + w x R r_rk and the
 // kinematic acceleration a_k + alpha_k x r_rk + w x (w x r_rk) used by the extrapolation
 template <class R>
-__global__ void k_kick_drift(BatchView<R> B) {
+__device__ __forceinline__ unsigned long long disp_bits(R d2);
+template <>
+__device__ __forceinline__ unsigned long long disp_bits<double>(double d2) {
+  return (unsigned long long)__double_as_longlong(d2);
+}
+template <>
+__device__ __forceinline__ unsigned long long disp_bits<float>(float d2) {
+  return (unsigned long long)(unsigned)__float_as_int(d2);
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_kick_drift(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-    int s = find_scene(B.pfx_part, B.nsc, g);
+  for (int g0 = blockIdx.x * blockDim.x; g0 < total; g0 += gridDim.x * blockDim.x) {
+    int g = g0 + threadIdx.x;
+    int s = find_scene(B.pfx_part, B.nsc, min(g, total - 1));
     const Scene<R>& S = *B.sc[s];
     int i = g - __ldg(B.pfx_part + s);
-    int kind = S.matR[S.P.mt[i]].kind;
+    int kind = g < total ? S.matR[S.P.mt[i]].kind : KWALL;
     if (kind == KFLUID) {
       R dt = (R)S.st[0], half = R(0.5) * dt;
       R ux = S.P.vx[i] + half * S.P.ax[i];
@@ -265,6 +277,30 @@ __global__ void k_kick_drift(BatchView<R> B) {
       S.P.ay[i] = (R)(S.ba[3 * k + 1] + t1[1] + t3[1]);
       S.P.az[i] = (R)(S.ba[3 * k + 2] + t1[2] + t3[2]);
     }
+    // displacement since the last list rebuild (skin criterion)
+    R d2 = R(0);
+    if (kind != KWALL && S.skin > 0.0) {
+      R d[3] = {S.P.px[i] - S.xr[i], S.P.py[i] - S.yr[i], S.P.pz[i] - S.zr[i]};
+      for (int k = 0; k < S.dim; k++)
+        if (sizeof(R) == 8 && S.per[k]) {
+          if (d[k] > R(0.5) * S.LR[k]) d[k] -= S.LR[k];
+          else if (d[k] < R(-0.5) * S.LR[k]) d[k] += S.LR[k];
+        }
+      d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    }
+    unsigned long long b = disp_bits<R>(d2);
+    unsigned pending = FULL;
+    while (pending) {
+      int leader = __ffs(pending) - 1;
+      int cs = __shfl_sync(FULL, s, leader);
+      unsigned long long v = s == cs ? b : 0ull;
+      for (int o = 16; o; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(FULL, v, o);
+        v = w > v ? w : v;
+      }
+      if ((int)(threadIdx.x & 31) == leader && v > 0ull) atomicMax(S.disp, v);
+      pending &= ~__ballot_sync(FULL, s == cs);
+    }
   }
 }
 
@@ -274,8 +310,23 @@ __global__ void k_kick_drift(BatchView<R> B) {
 // stable sort.  Skipped (early exit) on steps that are not rebin steps.
 template <class R>
 __device__ __forceinline__ bool rebin_now(const Scene<R>& S) {
-  long long step = (long long)S.st[2];
-  return S.rebin_interval <= 1 || (step % S.rebin_interval) == 0;
+  return S.status[4] != 0;
+}
+
+// rebuild decision of this step (after the drift): every step without a skin, otherwise
+// when a particle moved more than skin / 2 since the last rebuild (or the forced interval)
+template <class R>
+__global__ void k_decide(BatchView<R> B) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B.nsc) return;
+  Scene<R>& S = *B.sc[s];
+  R d2 = sizeof(R) == 8 ? (R)__longlong_as_double((long long)*S.disp) : (R)__int_as_float((int)*S.disp);
+  int since = S.status[5] + 1;
+  bool rb = S.skin <= 0.0 || d2 > S.half_skin2 || (S.rebin_interval > 1 && since >= S.rebin_interval);
+  S.status[4] = rb ? 1 : 0;
+  S.status[5] = rb ? 0 : since;
+  if (rb) S.status[6] += 1;
+  *S.disp = 0ull;
 }
 
 template <class R>
@@ -490,6 +541,7 @@ __global__ void k_permute(BatchView<R> B, int force) {
       pz = pz - (R)d2 * S.ellR[2];
     }
     Q.px[j] = px; Q.py[j] = py; Q.pz[j] = pz;
+    S.xr[j] = px; S.yr[j] = py; S.zr[j] = pz;
     Q.vx[j] = P.vx[i]; Q.vy[j] = P.vy[i]; Q.vz[j] = P.vz[i];
     Q.ax[j] = P.ax[i]; Q.ay[j] = P.ay[i]; Q.az[j] = P.az[i];
     Q.rho[j] = P.rho[i]; Q.T[j] = P.T[i]; Q.H[j] = P.H[i]; Q.m[j] = P.m[i];
@@ -610,9 +662,8 @@ __device__ __forceinline__ R dsub(R a, R b) {
 // generic traversal.  Pol provides: stage(S, j, lane), active, tp[3], idx,
 // bool accept(k) (candidate filter for the hit mask), pair(S, k, j, dx, dy, dz, r2).
 template <class R, int DIM, class Pol>
-__device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>& G, Pol& pol, int lane) {
+__device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>& G, Pol& pol, int lane, R rc2) {
   const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
-  const R rc2 = S.rc2R;
   for (int dz = zlo; dz <= zhi; dz++)
     for (int dy = -1; dy <= 1; dy++)
       for (int ox = -1; ox <= G.ncx; ox++) {

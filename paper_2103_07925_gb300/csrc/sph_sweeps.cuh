@@ -52,7 +52,7 @@ struct SearchPol {
     int code = (cox - tx + 1) + 3 * (cdy + 1) + 9 * (cdz + 1);
     if (cnt < maxnb) list[(size_t)cnt * n + idx] = (j << 5) | code;
     cnt++;
-    if (fluid) acc += quintic_w<R>(sqrt(r2) * S.inv_h);
+    if (fluid && r2 < S.rc2R) acc += quintic_w<R>(sqrt(r2) * S.inv_h);
   }
 };
 
@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
   for (int g = gw; g < total; g += nw) {
     int s = find_scene(B.pfx_grp, B.nsc, g);
     const Scene<R>& S = *B.sc[s];
+    if (!rebin_now(S)) continue;  // lists of the last rebuild still hold (skin)
     Group<R, DIM> G = group_of<R, DIM>(S, g - __ldg(B.pfx_grp + s));
     pol.list = S.nbl;
     pol.n = S.n;
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
       pol.acc = R(0);
       pol.cnt = 0;
       pol.hits = 0;
-      traverse<R, DIM>(S, G, pol, lane);
+      traverse<R, DIM>(S, G, pol, lane, S.rl2R);
       if (valid) {
         S.nbc[i] = pol.cnt;
         R rho = S.P.rho[i];
@@ -150,6 +151,45 @@ __device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
         for (int j = a; j < e; j++)
           if (j != i) f(j, code);
       }
+}
+
+// ---------------------------------------------------------------- density on steps without rebuild
+// Eq. densum + Eq. eos over the list (same pairs in the same order as the search sweep)
+template <class R, int DIM>
+__global__ void __launch_bounds__(256) k_density(BatchView<R> B) {
+  int total = __ldg(B.pfx_part + B.nsc);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int s = find_scene(B.pfx_part, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    if (rebin_now(S)) continue;  // the search sweep computed it
+    int i = g - __ldg(B.pfx_part + s);
+    const MatR<R>& A = S.matR[S.P.mt[i]];
+    R rho = S.P.rho[i];
+    if (A.kind == KFLUID) {
+      R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
+      R acc = R(0);
+      auto visit = [&](int j, int code) {
+        R d[3];
+        list_delta<R, DIM>(S, ti, j, code, d);
+        R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+        if (r2 < S.rc2R) acc += quintic_w<R>(sqrt(r2) * S.inv_h);
+      };
+      int cnt = S.nbc[i];
+      if (cnt <= S.maxnb) {
+        const int* L = S.nbl + i;
+        for (int k = 0; k < cnt; k++) {
+          int e = __ldg(L + (size_t)k * S.n);
+          visit(e >> 5, e & 31);
+        }
+      } else {
+        scan_cells<R, DIM>(S, i, visit);
+      }
+      rho = S.P.m[i] * (S.w0 + S.sig_w * acc);
+      S.P.rho[i] = rho;
+      S.prs[i] = A.c2 * (rho - A.rho0);
+    }
+    S.vol[i] = qdiv<R>(S.P.m[i], rho);
+  }
 }
 
 // ---------------------------------------------------------------- extrapolation (walls, rigid)
@@ -305,10 +345,12 @@ __global__ void __launch_bounds__(256) k_force(BatchView<R> B) {
         R d[3];
         list_delta<R, DIM>(S, ti, j, code, d);
         R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
-        if (r2 < S.rc2R) force_pair<R, DIM>(S, t, j, d, r2, acc, heat);
+        if (r2 < S.rc2R) {
+          force_pair<R, DIM>(S, t, j, d, r2, acc, heat);
+          npairs++;
+        }
       };
       int cnt = S.nbc[i];
-      npairs = (unsigned long long)cnt;
       if (cnt <= S.maxnb) {
         const int* L = S.nbl + i;
         for (int k = 0; k < cnt; k++) {

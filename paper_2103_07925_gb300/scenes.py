@@ -43,7 +43,7 @@ def default_params(dim, dx, box_min, box_max, **kw):
              box_max=[float(v) for v in box_max] + [0.0] * (3 - len(box_max)),
              periodic=[0, 0, 0], gravity=[0.0, 0.0, 0.0],
              dt_mode=0, dt_fixed=1e-4, k_contact=0.0, d_contact=-1.0,
-             precision=64, rebin_interval=1, key_order=0, cells_per_group=0,
+             precision=64, skin=0.0, rebin_interval=1, key_order=0, cells_per_group=0,
              body_capacity=0,
              src_power=0.0, src_radius=0.05, src_speed=[0.0, 0.0, 0.0],
              src_origin=[0.0, 0.0, 0.0], src_depth=0.0, src_ztop=0.0)

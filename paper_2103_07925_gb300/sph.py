@@ -28,7 +28,7 @@ EXPORTS = ["sph_create_scene", "sph_step", "sph_step_async", "sph_read_fields", 
            "sph_batch_step", "sph_batch_poll", "sph_batch_read_fields", "sph_batch_job_diagnostics",
            "sph_batch_release", "sph_batch_info", "sph_batch_destroy", "sph_profile",
            "sph_profile_stage_name"]
-PROFILE_STAGES = 18
+PROFILE_STAGES = 20
 
 
 class SphError(RuntimeError):
@@ -48,7 +48,7 @@ class Params(C.Structure):
                 ("box_min", C.c_double * 3), ("box_max", C.c_double * 3), ("periodic", C.c_int32 * 3),
                 ("gravity", C.c_double * 3), ("dt_mode", C.c_int32), ("dt_fixed", C.c_double),
                 ("k_contact", C.c_double), ("d_contact", C.c_double), ("precision", C.c_int32),
-                ("rebin_interval", C.c_int32), ("key_order", C.c_int32), ("cells_per_group", C.c_int32),
+                ("skin", C.c_double), ("rebin_interval", C.c_int32), ("key_order", C.c_int32), ("cells_per_group", C.c_int32),
                 ("body_capacity", C.c_int32), ("n_materials", C.c_int32),
                 ("materials", C.POINTER(Material)), ("src_power", C.c_double), ("src_radius", C.c_double),
                 ("src_speed", C.c_double * 3), ("src_origin", C.c_double * 3), ("src_depth", C.c_double),
@@ -149,7 +149,7 @@ class _Inputs:
                 setattr(self.mats[q], k, m[k])
         P = Params()
         for k in ("dim", "dx", "h", "kernel_support", "dt_mode", "dt_fixed", "k_contact", "d_contact",
-                  "precision", "rebin_interval", "key_order", "cells_per_group", "body_capacity",
+                  "precision", "skin", "rebin_interval", "key_order", "cells_per_group", "body_capacity",
                   "src_power", "src_radius", "src_depth", "src_ztop"):
             setattr(P, k, p[k])
         for d in range(3):
@@ -265,10 +265,11 @@ class Scene:
         return counts, lst[:tot.value]
 
     def info(self):
-        out = np.zeros(16, dtype=np.int64)
+        out = np.zeros(32, dtype=np.int64)
         _check(lib().sph_info(self.h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         keys = ["n", "n_fluid", "n_rigid", "n_wall", "n_bodies", "n_cells", "cells_x", "cells_y", "cells_z",
-                "steps", "kernels_per_step", "bytes", "groups", "cells_per_group", "key_order", "pairs_total"]
+                "steps", "kernels_per_step", "bytes", "groups", "cells_per_group", "key_order", "pairs_total",
+                "rebuilds", "list_capacity"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
 
     def profile(self, reps=3):
