@@ -67,11 +67,6 @@ __global__ void k_import(Scene<R>* const* sc, ImportArgs a) {
     S.P.m[i] = (R)a.mass[i];
     S.P.rho[i] = (R)a.dens[i];
     S.P.mt[i] = mt;
-    {
-      V4<R> q4;
-      q4.x = S.P.px[i]; q4.y = S.P.py[i]; q4.z = S.P.pz[i]; q4.w = (R)mt;
-      S.pos4[i] = q4;
-    }
     S.P.body[i] = kind == KRIGID ? a.body[i] : -1;
     S.P.slot[i] = a.slot[i];
     S.P.orig[i] = i;
@@ -111,9 +106,6 @@ __global__ void k_import_fluid(Scene<R>* const* sc, const double* pos, const dou
         S.P.py[i] = (R)(x[1] - (S.lo[1] + c[1] * S.ell[1]));
         S.P.pz[i] = S.dim == 3 ? (R)(x[2] - (S.lo[2] + c[2] * S.ell[2])) : R(0);
       }
-      V4<R> q4;
-      q4.x = S.P.px[i]; q4.y = S.P.py[i]; q4.z = S.P.pz[i]; q4.w = (R)mt;
-      S.pos4[i] = q4;
     }
     if (vel) { S.P.vx[i] = (R)vel[3 * o]; S.P.vy[i] = (R)vel[3 * o + 1]; S.P.vz[i] = (R)vel[3 * o + 2]; }
     if (temp) {

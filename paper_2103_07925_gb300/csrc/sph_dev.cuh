@@ -33,12 +33,6 @@ struct MatR {  // material constants in the working precision (pair sums)
   R rho0, c2, eta, cp, kappa, inv_p0;
 };
 
-// four values loaded as one aligned vector (16 bytes for FP32)
-template <class R>
-struct alignas(4 * sizeof(R)) V4 {
-  R x, y, z, w;
-};
-
 template <class R>
 struct PBank {  // particle fields (one bank)
   R *px, *py, *pz;     // position (FP64: absolute; FP32: relative to the cell origin)
@@ -73,13 +67,12 @@ struct Scene {
   PBank<R> P, Q;       // current and alternate bank
   R *prs, *dT;         // pressure, rate (not permuted: recomputed every evaluation)
   R *vex, *vey, *vez;  // extrapolated velocity of wall and rigid particles
-  V4<R>* pos4;         // (position, material) of every particle, refreshed after each drift
-  V4<R>* rec1;         // (V = m / rho, p, rho, T) of the current evaluation
-  V4<R>* rec2;         // (velocity seen by fluid neighbours: u or extrapolated v_w, body id)
-  unsigned* nbm;       // hit masks: chunk c of the candidate stream of particle i at nbm[c * n + i]
+  R* vol;              // particle volume m / rho of the current evaluation
+  int* nbl;            // neighbour lists: entry k of particle i at nbl[k * n + i] = j << 5 | cell code
+  int* nbc;            // neighbour count of each particle (may exceed maxnb: then cells are scanned)
   R *xr, *yr, *zr;     // positions at the last list rebuild (same frame as the bank)
   unsigned long long* disp;  // bits of the largest squared displacement since the rebuild
-  int maxch;           // stored chunks per particle (longer streams recompute their masks)
+  int maxnb;           // list capacity per particle
   int* key;            // cell key of each (sorted) particle
   int* where;          // input index -> current sorted index
   // rebin scratch

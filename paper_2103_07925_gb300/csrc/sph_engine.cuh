@@ -189,11 +189,9 @@ class Engine {
     SPH_CU(cudaMalloc(&d_pfx, sizeof(int) * 7 * (cap + 1)));
     h_pfx.assign(7 * (cap + 1), 0);
     SPH_CU(cudaMemsetAsync(d_pfx, 0, sizeof(int) * 7 * (cap + 1), stream));
-    int b1 = 0, b2 = 0, b3 = 0;
+    int b1 = 0, b2 = 0;
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_kick_drift<R>, 256, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_search<R, DIM>, 128, 0));
-    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, k_force<R, DIM>, 128, 0));
-    b2 = std::min(b2, b3);
     grid_part = sms * std::max(1, b1);
     grid_warp = sms * std::max(1, b2);
     grid_blk = sms * 8;
@@ -291,8 +289,8 @@ class Engine {
   }
 
   static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid) {
-    size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 20 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
-                 (DIM == 3 ? 48 : 16) * sizeof(unsigned);
+    size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 9 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
+                 (DIM == 3 ? 192 : 64) * sizeof(int);
     size_t cells = (size_t)(ncells + 1) * 4 * sizeof(int) + (size_t)(ncells / 1024 + 2) * sizeof(int);
     size_t bodies = (size_t)kcap * (60 * sizeof(double) + 3 * sizeof(int));
     size_t slots = (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R) + sizeof(int));
@@ -341,13 +339,12 @@ class Engine {
 namespace sph {
 
 // ------------------------------------------------------------------------------ helpers
-// stored mask chunks per particle: 1.4 x the lattice sites of a group's stencil cells
-// (streams of denser groups recompute the chunks beyond this on the fly)
-inline int mask_chunks(int dim, int G, const double* ell, double dx) {
-  double sites = (G + 2) * 3.0 * (ell[0] / dx) * (ell[1] / dx);
-  if (dim == 3) sites *= 3.0 * (ell[2] / dx);
-  int c = (int)std::ceil(1.4 * sites / 32.0) + 1;
-  return c < 2 ? 2 : c;
+// list capacity: 1.3 x the lattice sites inside the list radius, rounded up to 32
+inline int list_capacity(int dim, double radius_in_dx) {
+  double ball = dim == 3 ? 4.0 / 3.0 * M_PI * radius_in_dx * radius_in_dx * radius_in_dx
+                         : M_PI * radius_in_dx * radius_in_dx;
+  int c = (int)std::ceil(1.3 * ball / 32.0) * 32;
+  return c < 32 ? 32 : c;
 }
 
 inline int grid_for(int64_t items, int per_block, int max_grid) {
@@ -450,11 +447,6 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   S.key_order = morton ? 0 : 1;
   S.G = 1;
   if (!morton) S.G = p->cells_per_group > 0 ? p->cells_per_group : (DIM == 2 ? 3 : 1);
-  // the stencil of a group, (G + 2) x 3^(d-1) cells, is handled by the lanes of one warp
-  if ((S.G + 2) * (DIM == 3 ? 9 : 3) > 32) {
-    set_error("cells_per_group too large: at most 1 in 3D and 8 in 2D");
-    return SPH_ERR_INVALID;
-  }
   S.ngx = (S.ncell[0] + S.G - 1) / S.G;
   S.ngroups = morton ? S.ncells : S.ngx * S.ncell[1] * S.ncell[2];
   S.ncblk = (S.ncells + 1023) / 1024;
@@ -466,13 +458,11 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     int** ifs[] = {&B->mt, &B->body, &B->slot, &B->orig};
     for (int** f : ifs) SPH_TRY(A(f, (size_t)n));
   }
-  R** rx[] = {&S.prs, &S.dT, &S.vex, &S.vey, &S.vez};
+  R** rx[] = {&S.prs, &S.dT, &S.vex, &S.vey, &S.vez, &S.vol};
   for (R** f : rx) SPH_TRY(A(f, (size_t)n));
-  SPH_TRY(A(&S.pos4, (size_t)n));
-  SPH_TRY(A(&S.rec1, (size_t)n));
-  SPH_TRY(A(&S.rec2, (size_t)n));
-  S.maxch = mask_chunks(DIM, S.G, S.ell, S.dx);
-  SPH_TRY(A(&S.nbm, (size_t)S.maxch * n));
+  S.maxnb = list_capacity(DIM, (S.rc + S.skin) / S.dx);
+  SPH_TRY(A(&S.nbl, (size_t)S.maxnb * n));
+  SPH_TRY(A(&S.nbc, (size_t)n));
   SPH_TRY(A(&S.xr, (size_t)n));
   SPH_TRY(A(&S.yr, (size_t)n));
   SPH_TRY(A(&S.zr, (size_t)n));
@@ -620,8 +610,8 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B);
   int gw = grid_for((int64_t)S.ngroups * 32, 128, grid_warp);
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
-  k_extrap<R, DIM><<<gw, 128, 0, stream>>>(B);
-  k_force<R, DIM><<<gw, 128, 0, stream>>>(B);
+  k_extrap<R, DIM><<<gp, 256, 0, stream>>>(B);
+  k_force<R, DIM><<<gp, 256, 0, stream>>>(B);
   if (meta[idx].K0 > 0) k_body_reduce<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B);
   SPH_CU(cudaGetLastError());
@@ -698,11 +688,11 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   rec();
-  k_density<R, DIM><<<gw, 128, 0, stream>>>(B);
+  k_density<R, DIM><<<gp, 256, 0, stream>>>(B);
   rec();
-  k_extrap<R, DIM><<<gw, 128, 0, stream>>>(B);
+  k_extrap<R, DIM><<<gp, 256, 0, stream>>>(B);
   rec();
-  k_force<R, DIM><<<gw, 128, 0, stream>>>(B);
+  k_force<R, DIM><<<gp, 256, 0, stream>>>(B);
   rec();
   if (any_body) { k_body_reduce<R><<<gb, 128, 0, stream>>>(B, 1); kcount++; }
   rec();

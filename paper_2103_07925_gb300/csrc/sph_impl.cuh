@@ -42,7 +42,7 @@ struct EngineImpl final : EngineIface {
     }
     out[15] = (int64_t)pc[1];
     out[16] = st[6];
-    out[17] = S.maxch;
+    out[17] = S.maxnb;
     return SPH_OK;
   }
   sph_status profile(int32_t reps, double* ms) override { return e.profile(reps, ms); }

@@ -277,11 +277,6 @@ __global__ void __launch_bounds__(256) k_kick_drift(BatchView<R> B) {
       S.P.ay[i] = (R)(S.ba[3 * k + 1] + t1[1] + t3[1]);
       S.P.az[i] = (R)(S.ba[3 * k + 2] + t1[2] + t3[2]);
     }
-    if (kind != KWALL) {
-      V4<R> q4;
-      q4.x = S.P.px[i]; q4.y = S.P.py[i]; q4.z = S.P.pz[i]; q4.w = (R)S.P.mt[i];
-      S.pos4[i] = q4;
-    }
     // displacement since the last list rebuild (skin criterion)
     R d2 = R(0);
     if (kind != KWALL && S.skin > 0.0) {
@@ -547,11 +542,6 @@ __global__ void k_permute(BatchView<R> B, int force) {
     }
     Q.px[j] = px; Q.py[j] = py; Q.pz[j] = pz;
     S.xr[j] = px; S.yr[j] = py; S.zr[j] = pz;
-    {
-      V4<R> q4;
-      q4.x = px; q4.y = py; q4.z = pz; q4.w = (R)P.mt[i];
-      S.pos4[j] = q4;
-    }
     Q.vx[j] = P.vx[i]; Q.vy[j] = P.vy[i]; Q.vz[j] = P.vz[i];
     Q.ax[j] = P.ax[i]; Q.ay[j] = P.ay[i]; Q.az[j] = P.az[i];
     Q.rho[j] = P.rho[i]; Q.T[j] = P.T[i]; Q.H[j] = P.H[i]; Q.m[j] = P.m[i];
