@@ -209,6 +209,33 @@ const char* sph_profile_stage_name(int32_t stage);
 void sph_destroy_scene(sph_scene* scene);
 const char* sph_last_error(void);
 
+/* ------------------------------------------------------------------ allocation-free density
+ * For callers that cannot allocate device memory: code running under a memory manager
+ * that owns every device allocation, inside a region where allocation is not allowed, or
+ * next to a framework that has taken the device memory.  (The paper has no counterpart;
+ * this is a service of the library, not a step of the method.)
+ *
+ * Computes rho_i = m_i (W(0) + sum_j W_ij) over all j != i with |r_ij| < kernel_support h
+ * (quintic spline, the density summation of the scene path) for n particles held in the
+ * caller's device memory.  pos: device, n*3 doubles (z ignored in 2D); mass: device, n
+ * doubles; rho: device output, n doubles; box_min/box_max: HOST arrays of 3 doubles that
+ * contain every particle (non-periodic; particles outside are clamped to the edge cells).
+ * The work is enqueued on stream (NULL: the default stream) and not synchronised.
+ *
+ * No device memory is allocated: the cell-list scratch is a fixed static device array of
+ * this library (about 5 MB, held by every GPU that loads the library until exit).  Limits:
+ * n <= SPH_STATIC_MAX_PARTICLES and at most SPH_STATIC_MAX_CELLS cells of edge >= r_c in
+ * the box; larger inputs return SPH_ERR_CAPACITY without running.  The first call on a
+ * device looks up the array's device address (once per device, with that device current),
+ * so make that first call before any stream capture.  Every call uses the same array and
+ * leaves its contents behind (the counters are cleared at the start of each call): calls
+ * that overlap on the GPU, on different streams or threads, race and must be serialised. */
+#define SPH_STATIC_MAX_PARTICLES (1 << 18)
+#define SPH_STATIC_MAX_CELLS (1 << 18)
+sph_status sph_density_static(int32_t dim, int64_t n, const double* pos, const double* mass, double h,
+                              double kernel_support, const double* box_min, const double* box_max,
+                              double* rho, void* stream);
+
 /* ------------------------------------------------------------------ batches and serving
  * A batch advances many independent scenes (jobs) together: every stage of a step is one
  * launch over all resident scenes, driven by a device table of scene offsets, and the

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsph.so")
-UNITS = ["sph_capi.cu", "sph_f64.cu", "sph_f32.cu"]
+UNITS = ["sph_capi.cu", "sph_f64.cu", "sph_f32.cu", "sph_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler",
          "-fPIC,-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]

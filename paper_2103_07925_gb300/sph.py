@@ -27,7 +27,7 @@ EXPORTS = ["sph_create_scene", "sph_step", "sph_step_async", "sph_read_fields", 
            "sph_last_error", "sph_batch_create", "sph_job_footprint", "sph_batch_admit",
            "sph_batch_step", "sph_batch_poll", "sph_batch_read_fields", "sph_batch_job_diagnostics",
            "sph_batch_release", "sph_batch_info", "sph_batch_destroy", "sph_profile",
-           "sph_profile_stage_name"]
+           "sph_profile_stage_name", "sph_density_static"]
 PROFILE_STAGES = 20
 
 
@@ -115,6 +115,9 @@ def lib():
         L.sph_destroy_scene.restype = None
         L.sph_batch_destroy.argtypes = [vp]
         L.sph_batch_destroy.restype = None
+        L.sph_density_static.argtypes = [i32, i64, vp, vp, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double), vp, vp]
+        L.sph_density_static.restype = C.c_int
         L.sph_profile_stage_name.restype = C.c_char_p
         L.sph_profile_stage_name.argtypes = [i32]
         L.sph_last_error.restype = C.c_char_p
@@ -366,3 +369,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def density_static(dim, n, pos_ptr, mass_ptr, h, kernel_support, box_min, box_max, rho_ptr, stream=None):
+    """Density summation into caller-owned device buffers without any device allocation
+    (device addresses as integers; see sph_density_static in include/sph.h)."""
+    lo = (C.c_double * 3)(*[float(v) for v in box_min])
+    hi = (C.c_double * 3)(*[float(v) for v in box_max])
+    _check(lib().sph_density_static(dim, n, C.c_void_p(pos_ptr), C.c_void_p(mass_ptr), h, kernel_support, lo, hi,
+                                    C.c_void_p(rho_ptr), C.c_void_p(stream) if stream else None))
