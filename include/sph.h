@@ -196,7 +196,8 @@ sph_status sph_neighbors(sph_scene* scene, int64_t* counts, int32_t* list, int64
  * [6] cells x, [7] cells y, [8] cells z, [9] steps taken, [10] kernels per step,
  * [11] device bytes, [12] warp groups, [13] cells per group, [14] key order,
  * [15] ordered pairs evaluated by the force / heat sweep over all steps taken,
- * [16] neighbour-list rebuilds so far, [17] list capacity per particle.  out[] has 32 rows. */
+ * [16] neighbour-list rebuilds so far, [17] list capacity per particle, [18] particles that
+ * changed phase so far.  out[] has 32 rows. */
 sph_status sph_info(sph_scene* scene, int64_t out[32]);
 
 /* Tracing: run reps complete steps with the kernels launched one by one (no graph) and

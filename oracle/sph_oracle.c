@@ -1134,8 +1134,14 @@ void orc_get(orc_scene* s, int32_t field, void* out) {
     case ORC_F_DTEMP: memcpy(d, s->dT, sizeof(double) * (size_t)n); break;
     case ORC_F_MAT: memcpy(o, s->mat, sizeof(int32_t) * (size_t)n); break;
     case ORC_F_BODY: memcpy(o, s->body, sizeof(int32_t) * (size_t)n); break;
-    case ORC_F_FORCE: memcpy(d, s->f, sizeof(double) * 3 * (size_t)n); break;
-    case ORC_F_VEXT: memcpy(d, s->vext, sizeof(double) * 3 * (size_t)n); break;
+    case ORC_F_FORCE: /* f_r of particles that are rigid now */
+      for (int64_t i = 0; i < n; i++)
+        for (int q = 0; q < 3; q++) d[3 * i + q] = is_kind(s, i, ORC_RIGID) ? s->f[3 * i + q] : 0.0;
+      break;
+    case ORC_F_VEXT: /* extrapolated velocity of particles that are wall or rigid now */
+      for (int64_t i = 0; i < n; i++)
+        for (int q = 0; q < 3; q++) d[3 * i + q] = is_kind(s, i, ORC_FLUID) ? 0.0 : s->vext[3 * i + q];
+      break;
     case ORC_F_ENTH: memcpy(d, s->H, sizeof(double) * (size_t)n); break;
     case ORC_F_CELL:
       for (int64_t i = 0; i < n; i++) {

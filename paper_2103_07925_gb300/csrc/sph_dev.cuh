@@ -88,6 +88,11 @@ struct Scene {
   int* K;              // device: bodies in use (ids 0..K-1)
   double *bm, *br, *bq, *bu, *bw, *ba, *bal, *bf, *bt, *bIb, *bIbinv, *bIw;
   int *balive, *bstart, *bend;  // slot ranges of each body
+  int *bchg, *bcur;    // relabel: 1 changed body, 2 new body; slot cursor
+  double* bold;        // relabel: centre of mass before the change (3 per body)
+  double* rb2;         // relabel: body-frame offsets in the new slot order
+  R* fr2;              // relabel: slot forces in the new slot order
+  int* aux;            // relabel: smallest input index of each new-body component (per root)
   double* rb;          // body-frame offset of every slot (3 per slot)
   int* slot_part;      // slot -> current sorted particle index
   R* fr;               // force on every slot (3 per slot)
@@ -96,6 +101,8 @@ struct Scene {
   unsigned long long* umax;  // bits of max |u| over fluid particles (FP64, non-negative)
   int* status;         // [0] non-finite flag [1] relabel count [2] capacity error [3] table error
                        // [4] rebuild in this step [5] steps since rebuild [6] rebuild count
+                       // [7] solidifiers without a rigid neighbour [8] new bodies this step
+                       // [9] relabelled particles so far
   int* pfx1;           // prefix tables of this scene alone (6 x 2 ints)
   Scene<R>** self;     // device array holding the address of this descriptor
   unsigned long long* pairs;  // [0] force-sweep pairs of the last evaluation

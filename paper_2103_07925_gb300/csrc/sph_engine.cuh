@@ -288,13 +288,15 @@ class Engine {
     return SPH_OK;
   }
 
-  static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid) {
+  static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans) {
     size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 9 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
                  (DIM == 3 ? 192 : 64) * sizeof(int);
     size_t cells = (size_t)(ncells + 1) * 4 * sizeof(int) + (size_t)(ncells / 1024 + 2) * sizeof(int);
     size_t bodies = (size_t)kcap * (60 * sizeof(double) + 3 * sizeof(int));
     size_t slots = (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R) + sizeof(int));
-    return per * (size_t)n + cells + bodies + slots + 4096;
+    // relabel scratch: offsets and forces in the new slot order, one root mark per particle
+    size_t relabel = trans ? (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R)) + (size_t)n * sizeof(int) : 0;
+    return per * (size_t)n + cells + bodies + slots + relabel + 4096;
   }
 
   // ---------------------------------------------------------------------------- create
@@ -489,6 +491,15 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   size_t bdn[] = {1, 3, 4, 3, 3, 3, 3, 3, 3, 9, 9, 9};
   for (int q = 0; q < 12; q++) SPH_TRY(A(bd[q], bdn[q] * (size_t)kc));
   SPH_TRY(A(&S.balive, (size_t)kc));
+  SPH_TRY(A(&S.bchg, (size_t)kc));
+  SPH_TRY(A(&S.bcur, (size_t)kc));
+  SPH_TRY(A(&S.bold, 3 * (size_t)kc));
+  SPH_CU(cudaMemsetAsync(S.bchg, 0, sizeof(int) * kc, stream));
+  if (S.has_transition) {
+    SPH_TRY(A(&S.rb2, 3 * (size_t)S.nslot));
+    SPH_TRY(A(&S.fr2, 3 * (size_t)S.nslot));
+    SPH_TRY(A(&S.aux, (size_t)n));
+  }
   SPH_TRY(A(&S.bstart, (size_t)kc));
   SPH_TRY(A(&S.bend, (size_t)kc));
   SPH_TRY(A(&S.K, 1));
@@ -497,7 +508,7 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   SPH_TRY(A(&S.fr, 3 * (size_t)S.nslot));
   SPH_TRY(A(&S.st, 8));
   SPH_TRY(A(&S.umax, 1));
-  SPH_TRY(A(&S.status, 8));
+  SPH_TRY(A(&S.status, 16));
   SPH_TRY(A(&S.pfx1, 12));
   SPH_TRY(A(&S.self, 1));
   SPH_TRY(A(&S.pairs, 2));
@@ -509,7 +520,7 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   SPH_CU(cudaMemsetAsync(S.st, 0, sizeof(double) * 8, stream));
   SPH_CU(cudaMemsetAsync(S.umax, 0, sizeof(unsigned long long), stream));
   {
-    int st0[8] = {0, 0, 0, 0, 1, 0, 0, 0};  // [4]: the creation step builds the lists
+    int st0[16] = {0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // [4]: the creation step builds the lists
     SPH_CU(cudaMemcpyAsync(S.status, st0, sizeof(st0), cudaMemcpyHostToDevice, stream));
   }
   SPH_CU(cudaMemsetAsync(S.pairs, 0, sizeof(unsigned long long) * 2, stream));
@@ -606,14 +617,14 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   k_rank<R><<<grid_for((int64_t)S.ncells * 32, 256, grid_part), 256, 0, stream>>>(B, 1);
   k_permute<R><<<gp, 256, 0, stream>>>(B, 1);
   k_flip<R><<<1, 32, 0, stream>>>(B, 1);
-  if (meta[idx].K0 > 0) k_body_mass<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, nullptr);
-  k_rigid_vel<R><<<gp, 256, 0, stream>>>(B);
+  if (meta[idx].K0 > 0) k_body_mass<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
+  k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
   int gw = grid_for((int64_t)S.ngroups * 32, 128, grid_warp);
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   k_extrap<R, DIM><<<gp, 256, 0, stream>>>(B);
   k_force<R, DIM><<<gp, 256, 0, stream>>>(B);
   if (meta[idx].K0 > 0) k_body_reduce<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
-  k_rigid_vel<R><<<gp, 256, 0, stream>>>(B);
+  k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
   SPH_CU(cudaGetLastError());
   SPH_CU(cudaStreamSynchronize(stream));
   return SPH_OK;
@@ -646,9 +657,11 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   int64_t np = h_pfx[ns], nc = h_pfx[(cap + 1) + ns], ng = h_pfx[2 * (cap + 1) + ns];
   int64_t nb = h_pfx[3 * (cap + 1) + ns], ncb = h_pfx[4 * (cap + 1) + ns];
   bool any_dt = false, any_body = false;
+  bool any_transition = false;
   for (int a : act) {
     any_dt |= hs[a].dt_mode == 1;
     any_body |= meta[a].K0 > 0 || hs[a].has_transition != 0;
+    any_transition |= hs[a].has_transition != 0;
   }
   int gp = grid_for(np, 256, grid_part);
   int gs = grid_for(ns, 128, 1 << 20);
@@ -698,6 +711,29 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_final<R><<<gp, 256, 0, stream>>>(B);
   rec();
+  if (any_transition) {
+    // phase transitions at the end of the step (Sec. 3.6); every kernel exits at once
+    // when no particle of its scene changed phase
+    int gsb = std::min(ns, grid_blk);
+    int gsl = grid_for(h_pfx[5 * (cap + 1) + ns], 256, grid_part);
+    k_rl_flag<R><<<gp, 256, 0, stream>>>(B);
+    k_rl_join<R, DIM><<<gp, 256, 0, stream>>>(B);
+    k_rl_hook<R, DIM><<<gp, 256, 0, stream>>>(B);
+    k_rl_root<R><<<gp, 256, 0, stream>>>(B);
+    k_rl_number<R><<<gsb, 256, 0, stream>>>(B);
+    k_rl_apply<R><<<gp, 256, 0, stream>>>(B);
+    k_rl_slots_clear<R><<<gsb, 256, 0, stream>>>(B);
+    k_rl_slots_count<R><<<gp, 256, 0, stream>>>(B);
+    k_rl_slots_scan<R><<<gsb, 1024, 0, stream>>>(B);
+    k_rl_slots_fill<R><<<gp, 256, 0, stream>>>(B);
+    k_rl_slots_order<R><<<grid_for(nb * 32, 128, grid_part), 128, 0, stream>>>(B);
+    k_rl_slots_adopt<R><<<gsl, 256, 0, stream>>>(B);
+    k_rl_bodies_pre<R><<<grid_for(nb, 128, grid_part), 128, 0, stream>>>(B);
+    k_body_mass<R><<<gb, 128, 0, stream>>>(B, 1);
+    k_rl_bodies_post<R><<<gb, 128, 0, stream>>>(B);
+    k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 1);
+    kcount += 16;
+  }
   k_end_step<R><<<gs, 128, 0, stream>>>(B);
   rec();
   kcount += 17;
@@ -747,10 +783,14 @@ sph_status Engine<R, DIM>::capture() {
 
 template <class R, int DIM>
 sph_status Engine<R, DIM>::check_status(int idx, bool* nonfinite) {
-  int st[8];
+  int st[16];
   SPH_CU(cudaMemcpyAsync(st, hs[idx].status, sizeof(st), cudaMemcpyDeviceToHost, stream));
   SPH_CU(cudaStreamSynchronize(stream));
   *nonfinite = st[0] != 0;
+  if (st[2] != 0) {
+    set_error("body capacity exceeded by new bodies from solidification (scene %d)", idx);
+    return SPH_ERR_CAPACITY;
+  }
   return SPH_OK;
 }
 

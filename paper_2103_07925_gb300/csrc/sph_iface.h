@@ -34,7 +34,7 @@ struct EngineIface {
   virtual void set_reported(int idx) = 0;
   virtual int64_t job_id(int idx) = 0;
   virtual int64_t steps_taken() = 0;
-  virtual size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid) = 0;
+  virtual size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans) = 0;
 };
 
 EngineIface* make_engine_f64(int dim);

@@ -33,7 +33,7 @@ struct EngineImpl final : EngineIface {
     out[9] = M.steps_done; out[10] = e.kernels_per_step; out[11] = (int64_t)M.bytes;
     out[12] = S.ngroups; out[13] = S.G; out[14] = S.key_order;
     unsigned long long pc[2] = {0, 0};
-    int st[8] = {0};
+    int st[16] = {0};
     if (cudaMemcpyAsync(pc, S.pairs, sizeof(pc), cudaMemcpyDeviceToHost, e.stream) != cudaSuccess ||
         cudaMemcpyAsync(st, S.status, sizeof(st), cudaMemcpyDeviceToHost, e.stream) != cudaSuccess ||
         cudaStreamSynchronize(e.stream) != cudaSuccess) {
@@ -43,6 +43,7 @@ struct EngineImpl final : EngineIface {
     out[15] = (int64_t)pc[1];
     out[16] = st[6];
     out[17] = S.maxnb;
+    out[18] = st[9];
     return SPH_OK;
   }
   sph_status profile(int32_t reps, double* ms) override { return e.profile(reps, ms); }
@@ -65,8 +66,8 @@ struct EngineImpl final : EngineIface {
   void set_reported(int idx) override { e.meta[idx].reported = true; }
   int64_t job_id(int idx) override { return e.meta[idx].job_id; }
   int64_t steps_taken() override { return e.steps_taken; }
-  size_t footprint(int64_t n, int64_t nc, int64_t kc, int64_t nr) override {
-    return Engine<R, DIM>::footprint(n, nc, kc, nr);
+  size_t footprint(int64_t n, int64_t nc, int64_t kc, int64_t nr, bool trans) override {
+    return Engine<R, DIM>::footprint(n, nc, kc, nr, trans);
   }
 };
 

@@ -187,6 +187,9 @@ __global__ void k_dt(BatchView<R> B) {
   *S.umax = 0ull;
   S.st[0] = dt;
   S.pairs[0] = 0ull;
+  S.status[1] = 0;  // relabel counters of this step
+  S.status[7] = 0;
+  S.status[8] = 0;
 }
 
 // ============================================================================ kick + drift
@@ -837,7 +840,7 @@ __global__ void k_end_step(BatchView<R> B) {
 // Then the body-frame inertia R^T I R, its inverse, and the body-frame offsets of the
 // particles r_rk = R^T (x_r - r_k).
 template <class R>
-__global__ void __launch_bounds__(128) k_body_mass(BatchView<R> B, const int* __restrict__ only) {
+__global__ void __launch_bounds__(128) k_body_mass(BatchView<R> B, int changed_only) {
   __shared__ double pm[128], pr[3][128], pI[9][128];
   __shared__ double com[3];
   int total = __ldg(B.pfx_body + B.nsc);
@@ -846,7 +849,7 @@ __global__ void __launch_bounds__(128) k_body_mass(BatchView<R> B, const int* __
     const Scene<R>& S = *B.sc[s];
     int k = g - __ldg(B.pfx_body + s);
     if (k >= *S.K) continue;
-    if (only && !only[g]) continue;
+    if (changed_only && !S.bchg[k]) continue;
     int a = S.bstart[k], e = S.bend[k];
     if (e <= a) {
       if (threadIdx.x == 0) S.balive[k] = 0;
@@ -949,11 +952,12 @@ __global__ void __launch_bounds__(128) k_body_mass(BatchView<R> B, const int* __
 
 // rigid particle velocities from their bodies (after creation or a relabel)
 template <class R>
-__global__ void k_rigid_vel(BatchView<R> B) {
+__global__ void k_rigid_vel(BatchView<R> B, int after_relabel) {
   int total = __ldg(B.pfx_part + B.nsc);
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     int s = find_scene(B.pfx_part, B.nsc, g);
     const Scene<R>& S = *B.sc[s];
+    if (after_relabel && !(S.has_transition && S.status[1] > 0 && S.status[2] == 0)) continue;
     int i = g - __ldg(B.pfx_part + s);
     if (S.matR[S.P.mt[i]].kind != KRIGID) continue;
     int k = S.P.body[i], sl = S.P.slot[i];
@@ -973,3 +977,5 @@ __global__ void k_rigid_vel(BatchView<R> B) {
 }
 
 }  // namespace sph
+
+#include "sph_relabel.cuh"

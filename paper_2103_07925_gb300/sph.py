@@ -272,7 +272,7 @@ class Scene:
         _check(lib().sph_info(self.h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         keys = ["n", "n_fluid", "n_rigid", "n_wall", "n_bodies", "n_cells", "cells_x", "cells_y", "cells_z",
                 "steps", "kernels_per_step", "bytes", "groups", "cells_per_group", "key_order", "pairs_total",
-                "rebuilds", "list_capacity"]
+                "rebuilds", "list_capacity", "relabelled"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
 
     def profile(self, reps=3):

@@ -71,6 +71,8 @@ def compare_bodies(gpu, orc, sc=None):
         return errs
     assert np.array_equal(g["alive"], o["alive"])
     alive = o["alive"] == 1
+    if not alive.any():
+        return errs
     fs = np.zeros(k)
     ts = np.zeros(k)
     vs = np.zeros(k)
