@@ -44,6 +44,13 @@ def parse():
     ap.add_argument("--key-order", type=int, default=0)
     ap.add_argument("--dx", type=float, default=0.01)
     ap.add_argument("--skin", type=float, default=0.3, help="Verlet skin in units of h")
+    ap.add_argument("--workload", default="tank3d", choices=["tank3d", "batch", "serve"],
+                    help="tank3d: the 1.28M-particle tank (default); batch: 256 mixed scenes in one "
+                         "batch; serve: Poisson job arrivals served by continuous batching")
+    ap.add_argument("--scenes", type=int, default=256, help="batch: number of scenes")
+    ap.add_argument("--jobs", type=int, default=32, help="serve: number of jobs")
+    ap.add_argument("--job-steps", type=int, default=1000, help="serve: steps per job")
+    ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
     return ap.parse_args()
 
 
@@ -160,6 +167,127 @@ def cpu_baseline():
             "sample": "2 FP64 oracle steps of the full 1,280,908-particle tank scene (%.1f s)" % t}
 
 
+def bench_batch(args, rank, world, allmax, allsum, barrier):
+    """Many independent scenes of uneven size advanced together (one launch per stage over
+    all scenes, one CUDA graph per step), against the plain per-scene FP64 path."""
+    import numpy as np
+    import torch
+    from paper_2103_07925_gb300 import scenes as S
+    from paper_2103_07925_gb300.sph import Batch, Scene
+    from paper_2103_07925_gb300.tune import tune_batch
+    mix = S.batch_mix(count=args.scenes, seed=2103 + rank)
+    scs = [sc for sc, _ in mix]
+    nparts = int(sum(m["n"] for _, m in mix))
+    tuned = {}
+    if not args.no_tune:
+        tuned = tune_batch(None, scs, precision=32, steps=8, warmup=2)
+    B = Batch(capacity=len(scs), precision=32)
+    t0 = time.perf_counter()
+    ids = []
+    for sc in scs:
+        ov = dict(tuned[sc["params"]["dim"]].params) if sc["params"]["dim"] in tuned else {}
+        j = B.admit(sc, 0, **ov)
+        if j is None:
+            raise SystemExit("batch does not fit")
+        ids.append(j)
+    torch.cuda.synchronize()
+    t_admit = time.perf_counter() - t0
+    if tuned:  # layouts come from the tuner's cache; launch shapes are tuned on the batch itself
+        tuned = tune_batch(B, scs, precision=32)
+    B.step(args.warmup)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    q0 = B.info()["pairs_total"]
+    ms = B.time_steps(args.steps)
+    barrier()
+    clk = clocks.stop()
+    info = B.info()
+    pairs = info["pairs_total"] - q0
+    ms_max = allmax(ms)
+    value = allsum(len(scs) * args.steps) / (ms_max / 1e3)
+    # end to end: admission (host inputs to the device), the timed steps, read-back of positions
+    t1 = time.perf_counter()
+    outs = [B.read(j, "pos") for j in ids]
+    t_read = time.perf_counter() - t1
+    e2e_s = allmax(t_admit + ms / 1e3 + t_read)
+    h2d = int(sum(sum(np.asarray(v).nbytes for v in sc["particles"].values()) for sc in scs))
+    d2h = int(sum(o.nbytes for o in outs))
+    B.close()
+    # plain path: every scene alone, FP64 and FP32 (device time of a few steps each)
+    plain = {}
+    for prec in (64, 32):
+        tot_ms = 0.0
+        k = 2
+        for sc in scs:
+            g = Scene(sc, precision=prec)
+            g.step(1)
+            tot_ms += g.time_steps(k) / k
+            g.close()
+        plain[prec] = len(scs) / (allmax(tot_ms) / 1e3) * world
+    out = {"metric": "scene-steps/s, batched form (%d mixed 2D/3D scenes)" % len(scs), "value": value,
+           "unit": "scene-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batched mix: %d scenes, log N ~ normal around sqrt(1e4 x 5e5), clipped to "
+                                  "[1e4, 5e5], 2D/3D by a seeded coin, 0-50 bodies" % len(scs),
+                      "particles": nparts, "scenes_2d": sum(m["dim"] == 2 for _, m in mix),
+                      "bodies": int(sum(m["bodies"] for _, m in mix)),
+                      "tuned": {d: dict(t.params, **t.launch) for d, t in tuned.items()},
+                      "l2": "inputs larger than L2 (%.1f GB resident)" % (info["bytes"] / 1e9)},
+           "pairs_per_s": allsum(pairs) / (ms_max / 1e3),
+           "plain_fp64": {"value": plain[64], "unit": "scene-steps/s", "kind": "each scene alone, FP64"},
+           "plain_fp32": {"value": plain[32], "unit": "scene-steps/s", "kind": "each scene alone, FP32"},
+           "speedup_vs_plain_fp64": value / plain[64],
+           "gpu_launches": args.steps * info["kernels_per_step"],
+           "e2e": {"value": allsum(len(scs) * args.steps) / e2e_s, "unit": "scene-steps/s",
+                   "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+                   "note": "admission of all scenes + timed steps + read-back of positions"},
+           "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def bench_serve(args, rank, world, allmax, allsum, barrier):
+    """Poisson arrivals served by continuous batching, against one scene at a time."""
+    from paper_2103_07925_gb300.serve import Server, percentiles, serve_plain, serving_jobs
+    from paper_2103_07925_gb300.sph import Batch, Scene
+    jobs = serving_jobs(args.jobs, rate=20.0, steps=args.job_steps, seed=2103 + rank)
+    work = sum(j.steps for j in jobs)
+    res = {}
+    for name, cap in (("cap150GB", 150 << 30), ("cap2GB", 2 << 30)):
+        B = Batch(capacity=256, hbm_cap_bytes=cap, precision=32)
+        srv = Server(B, step_batch=10, fields=("pos",))
+        barrier()
+        t0 = time.perf_counter()
+        done = srv.run(jobs)
+        t = allmax(time.perf_counter() - t0)
+        B.close()
+        res[name] = dict(percentiles(done), scene_steps_per_s=allsum(work) / t, seconds=t,
+                         peak_jobs=srv.max_jobs, peak_bytes=srv.max_bytes, failed=sum(d.failed for d in done))
+    barrier()
+    t0 = time.perf_counter()
+    done = serve_plain(jobs, lambda sc, **kw: Scene(sc, precision=32, **kw), fields=("pos",))
+    t = allmax(time.perf_counter() - t0)
+    res["plain"] = dict(percentiles(done), scene_steps_per_s=allsum(work) / t, seconds=t,
+                        failed=sum(d.failed for d in done))
+    b = res["cap150GB"]
+    out = {"metric": "p50/p99 job latency, serving (Poisson 20/s) vs plain", "value": b["p50"], "unit": "s",
+           "n_gpus": world, "steps": args.job_steps, "warmup": 0, "ms_per_step": None,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "%d jobs, N log-uniform [5e3, 1e6], 0-100 bodies, %d steps each, Poisson "
+                                  "arrivals 20/s" % (len(jobs), args.job_steps),
+                      "particles": int(sum(len(j.scene["particles"]["mass"]) for j in jobs))},
+           "p99": b["p99"], "serving": res,
+           "e2e": {"value": b["p50"], "unit": "s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                   "note": "latency is end to end: host inputs in, positions out"}}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -197,6 +325,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
 
+    if args.workload == "batch":
+        bench_batch(args, rank, world, allmax, allsum, barrier)
+        return
+    if args.workload == "serve":
+        bench_serve(args, rank, world, allmax, allsum, barrier)
+        return
     from paper_2103_07925_gb300.sph import Scene
     hbm, smmax, peak_src = peaks()
     sc = workload(args.dx)

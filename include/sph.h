@@ -197,8 +197,20 @@ sph_status sph_neighbors(sph_scene* scene, int64_t* counts, int32_t* list, int64
  * [11] device bytes, [12] warp groups, [13] cells per group, [14] key order,
  * [15] ordered pairs evaluated by the force / heat sweep over all steps taken,
  * [16] neighbour-list rebuilds so far, [17] list capacity per particle, [18] particles that
- * changed phase so far.  out[] has 32 rows. */
+ * changed phase so far, [19] threads per block of the pair sweeps, [20] blocks per SM of
+ * the pair sweeps, [21] blocks per SM of the neighbour search.  out[] has 32 rows. */
 sph_status sph_info(sph_scene* scene, int64_t out[32]);
+
+/* Launch shape of the pair sweeps (density, extrapolation, force/heat) and of the
+ * neighbour search, for autotuning.  cfg[0] threads per block of the sweeps (a multiple
+ * of 32 in [32, 256]; default 256), cfg[1] resident blocks per SM of the sweeps and cfg[2]
+ * of the search (0: as many as the occupancy allows; larger values are clamped to that).
+ * n = number of entries given (missing entries take their defaults).  The shape changes
+ * how work is spread over the GPU, never which arithmetic a particle sees: results are
+ * bitwise the same for every shape.  SPH_ERR_INVALID on a bad shape. */
+sph_status sph_set_launch(sph_scene* scene, const int32_t* cfg, int32_t n);
+/* device time (ms, CUDA events on the scene's stream) of nsteps steps; the scene advances */
+sph_status sph_time_steps(sph_scene* scene, int32_t nsteps, double* ms);
 
 /* Tracing: run reps complete steps with the kernels launched one by one (no graph) and
  * CUDA events between them; ms_per_stage[SPH_PROFILE_STAGES] receives the mean device
@@ -259,15 +271,26 @@ sph_status sph_job_footprint(const sph_job_desc* job, size_t* bytes);
 sph_status sph_batch_admit(sph_batch* batch, const sph_job_desc* job, int64_t* job_id);
 /* advance every resident, unfinished job by up to nsteps (jobs stop at nsteps_total) */
 sph_status sph_batch_step(sph_batch* batch, int32_t nsteps);
-/* ids of jobs that reached nsteps_total since the last poll (n_done <= max_done) */
+/* ids of jobs that finished since the last poll (n_done <= max_done): jobs that reached
+ * nsteps_total, and jobs whose fluid velocities became non-finite (those stop advancing;
+ * sph_batch_job_state tells the two apart).  Synchronises the batch's stream. */
 sph_status sph_batch_poll(sph_batch* batch, int64_t* done_ids, int32_t max_done, int32_t* n_done);
+/* *state: 0 advancing, 1 finished (reached nsteps_total), 2 failed (non-finite velocity) */
+sph_status sph_batch_job_state(sph_batch* batch, int64_t job_id, int32_t* state);
 sph_status sph_batch_read_fields(sph_batch* batch, int64_t job_id, uint32_t field_mask,
                                  void* const* host_dst);
 sph_status sph_batch_job_diagnostics(sph_batch* batch, int64_t job_id, double out[16]);
 /* release a job's device memory and slot */
 sph_status sph_batch_release(sph_batch* batch, int64_t job_id);
-/* [0] resident jobs, [1] resident particles, [2] bytes in use, [3] steps taken */
+/* [0] resident jobs, [1] resident particles, [2] bytes in use, [3] steps taken,
+ * [4] jobs still advancing, [5] kernel launches per batch step (2D and 3D scenes
+ * together), [6] ordered pairs evaluated by the force / heat sweep so far, summed over
+ * the resident jobs */
 sph_status sph_batch_info(sph_batch* batch, int64_t out[8]);
+/* launch shape (as sph_set_launch) of the batch's 2D (dim 2) or 3D (dim 3) scenes */
+sph_status sph_batch_set_launch(sph_batch* batch, int32_t dim, const int32_t* cfg, int32_t n);
+/* device time (ms) of sph_batch_step(batch, nsteps), which it performs */
+sph_status sph_batch_time_steps(sph_batch* batch, int32_t nsteps, double* ms);
 void sph_batch_destroy(sph_batch* batch);
 
 #ifdef __cplusplus

@@ -118,6 +118,16 @@ sph_status sph_info(sph_scene* s, int64_t out[32]) {
   return s->e->info(0, out);
 }
 
+sph_status sph_set_launch(sph_scene* s, const int32_t* cfg, int32_t n) {
+  if (!s || (n > 0 && !cfg)) { set_error("null argument"); return SPH_ERR_INVALID; }
+  return s->e->set_launch(cfg, n);
+}
+
+sph_status sph_time_steps(sph_scene* s, int32_t nsteps, double* ms) {
+  if (!s) { set_error("null scene"); return SPH_ERR_INVALID; }
+  return s->e->time_steps(nsteps, ms);
+}
+
 sph_status sph_profile(sph_scene* s, int32_t reps, double* ms_per_stage) {
   if (!s || !ms_per_stage || reps < 1) { set_error("bad argument"); return SPH_ERR_INVALID; }
   return s->e->profile(reps, ms_per_stage);
@@ -241,6 +251,7 @@ sph_status sph_batch_poll(sph_batch* b, int64_t* done_ids, int32_t max_done, int
   *n_done = 0;
   for (int d = 0; d < 2; d++) {
     sph_status st = b->e[d]->sync();
+    if (st == SPH_OK) st = b->e[d]->check_failed();
     if (st != SPH_OK) return st;
     for (int i = 0; i < b->e[d]->nscenes() && *n_done < max_done; i++)
       if (b->e[d]->job_done(i) && !b->e[d]->job_reported(i)) {
@@ -259,6 +270,14 @@ static bool locate(sph_batch* b, int64_t id, int* d, int* idx) {
   }
   set_error("unknown job id %lld", (long long)id);
   return false;
+}
+
+sph_status sph_batch_job_state(sph_batch* b, int64_t job_id, int32_t* state) {
+  if (!b || !state) { set_error("null argument"); return SPH_ERR_INVALID; }
+  int d, i;
+  if (!locate(b, job_id, &d, &i)) return SPH_ERR_INVALID;
+  *state = b->e[d]->job_failed(i) ? 2 : (b->e[d]->job_done(i) ? 1 : 0);
+  return SPH_OK;
 }
 
 sph_status sph_batch_read_fields(sph_batch* b, int64_t job_id, uint32_t mask, void* const* dst) {
@@ -291,8 +310,37 @@ sph_status sph_batch_info(sph_batch* b, int64_t out[8]) {
     out[2] += (int64_t)b->e[d]->bytes_in_use();
     out[3] += b->e[d]->steps_taken();
     out[4] += b->e[d]->nactive();
+    out[5] += b->e[d]->kernels_per_step();
+    int64_t pc = 0;
+    sph_status st = b->e[d]->pairs_total(&pc);
+    if (st != SPH_OK) return st;
+    out[6] += pc;
   }
   return SPH_OK;
+}
+
+sph_status sph_batch_set_launch(sph_batch* b, int32_t dim, const int32_t* cfg, int32_t n) {
+  if (!b || (n > 0 && !cfg)) { set_error("null argument"); return SPH_ERR_INVALID; }
+  if (dim != 2 && dim != 3) { set_error("dim must be 2 or 3"); return SPH_ERR_INVALID; }
+  return b->e[dim - 2]->set_launch(cfg, n);
+}
+
+sph_status sph_batch_time_steps(sph_batch* b, int32_t nsteps, double* ms) {
+  if (!b || !ms || nsteps < 1) { set_error("time_steps needs a batch, nsteps >= 1 and an output"); return SPH_ERR_INVALID; }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) { set_error("cudaEventCreate failed"); return SPH_ERR_CUDA; }
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); set_error("cudaEventCreate failed"); return SPH_ERR_CUDA; }
+  sph_status st = cudaEventRecord(e0, b->stream) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+  for (int d = 0; d < 2 && st == SPH_OK; d++) st = b->e[d]->advance(nsteps);
+  if (st == SPH_OK && cudaEventRecord(e1, b->stream) != cudaSuccess) st = SPH_ERR_CUDA;
+  if (st == SPH_OK && cudaEventSynchronize(e1) != cudaSuccess) st = SPH_ERR_CUDA;
+  float t = 0.f;
+  if (st == SPH_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) st = SPH_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == SPH_ERR_CUDA) set_error("event timing failed");
+  *ms = t;
+  return st;
 }
 
 void sph_batch_destroy(sph_batch* b) {

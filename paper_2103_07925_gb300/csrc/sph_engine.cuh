@@ -45,7 +45,7 @@ struct HostScene {
   std::vector<void*> allocs;
   int64_t job_id = -1;
   int32_t nsteps_total = 0, steps_done = 0;
-  bool done = false, reported = false;
+  bool done = false, reported = false, failed = false;
   int n = 0, nfluid = 0, nrigid = 0, nwall = 0, K0 = 0;
 };
 
@@ -166,9 +166,15 @@ class Engine {
   cudaGraphExec_t graph = nullptr;
   bool graph_dirty = true;
   int grid_part = 0, grid_warp = 0, grid_blk = 0;
+  // launch shape of the pair sweeps (density, extrapolation, force) and of the search:
+  // threads per block of the sweeps, and resident waves of blocks per SM for both
+  int sweep_block = 256, sweep_waves = 0, search_waves = 0;
+  int grid_sweep = 0;
   int kernels_per_step = 0;
   int sms = 0;
   int64_t steps_taken = 0;
+  int* d_flags = nullptr;          // non-finite flags gathered from the scenes (cap)
+  std::vector<int> h_flags;
   // staging for reads
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
@@ -187,6 +193,8 @@ class Engine {
     SPH_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SPH_CU(cudaMalloc(&d_sc, sizeof(Scene<R>*) * cap));
     SPH_CU(cudaMalloc(&d_pfx, sizeof(int) * 7 * (cap + 1)));
+    SPH_CU(cudaMalloc(&d_flags, sizeof(int) * cap));
+    h_flags.assign(cap, 0);
     h_pfx.assign(7 * (cap + 1), 0);
     SPH_CU(cudaMemsetAsync(d_pfx, 0, sizeof(int) * 7 * (cap + 1), stream));
     int b1 = 0, b2 = 0;
@@ -195,7 +203,58 @@ class Engine {
     grid_part = sms * std::max(1, b1);
     grid_warp = sms * std::max(1, b2);
     grid_blk = sms * 8;
+    return apply_launch();
+  }
+
+  // grids of the sweeps and the search from the launch shape (0 waves: the occupancy limit)
+  sph_status apply_launch() {
+    int bs = 0, bw = 0;
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_force<R, DIM>, sweep_block, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, k_search<R, DIM>, 128, 0));
+    bs = std::max(1, bs);
+    bw = std::max(1, bw);
+    grid_sweep = sms * (sweep_waves > 0 ? std::min(sweep_waves, bs) : bs);
+    grid_warp = sms * (search_waves > 0 ? std::min(search_waves, bw) : bw);
+    graph_dirty = true;
     return SPH_OK;
+  }
+
+  sph_status set_launch(const int32_t* cfg, int32_t n) {
+    int b = n > 0 ? cfg[0] : 256, w = n > 1 ? cfg[1] : 0, v = n > 2 ? cfg[2] : 0;
+    if (b < 32 || b > 256 || b % 32 || w < 0 || v < 0) {
+      set_error("launch shape: block must be a multiple of 32 in [32, 256], waves >= 0");
+      return SPH_ERR_INVALID;
+    }
+    sweep_block = b;
+    sweep_waves = w;
+    search_waves = v;
+    return apply_launch();
+  }
+
+  void get_launch(int32_t* cfg) {
+    cfg[0] = sweep_block;
+    cfg[1] = grid_sweep / std::max(1, sms);
+    cfg[2] = grid_warp / std::max(1, sms);
+  }
+
+  // device time of n steps (graph replays) between two events on the engine's stream
+  sph_status time_steps(int32_t n, double* ms) {
+    if (n < 1 || !ms) { set_error("time_steps needs n >= 1 and an output"); return SPH_ERR_INVALID; }
+    cudaEvent_t a, b;
+    SPH_CU(cudaEventCreate(&a));
+    SPH_CU(cudaEventCreate(&b));
+    sph_status st = SPH_OK;
+    if (cudaEventRecord(a, stream) != cudaSuccess) st = SPH_ERR_CUDA;
+    if (st == SPH_OK) st = step(n, false);
+    if (st == SPH_OK && cudaEventRecord(b, stream) != cudaSuccess) st = SPH_ERR_CUDA;
+    if (st == SPH_OK && cudaEventSynchronize(b) != cudaSuccess) st = SPH_ERR_CUDA;
+    float t = 0.f;
+    if (st == SPH_OK && cudaEventElapsedTime(&t, a, b) != cudaSuccess) st = SPH_ERR_CUDA;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st == SPH_ERR_CUDA) set_error("event timing failed");
+    *ms = t;
+    return st;
   }
 
   void release_scene(size_t idx) {
@@ -212,6 +271,8 @@ class Engine {
     graph = nullptr;
     if (d_sc) cudaFree(d_sc);
     if (d_pfx) cudaFree(d_pfx);
+    if (d_flags) cudaFree(d_flags);
+    d_flags = nullptr;
     if (d_stage) cudaFree(d_stage);
     d_sc = nullptr; d_pfx = nullptr; d_stage = nullptr;
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -325,6 +386,22 @@ class Engine {
   sph_status diagnostics(int idx, double out[16]);
   sph_status neighbors(int idx, int64_t* counts, int32_t* list, int64_t cap_list, int64_t* total);
   sph_status check_status(int idx, bool* nonfinite);
+  // jobs whose velocities became non-finite leave the batch tables as failed
+  sph_status check_failed() {
+    int ns = (int)act.size();
+    if (!ns) return SPH_OK;
+    k_gather_failed<R><<<(ns + 127) / 128, 128, 0, stream>>>(d_sc, ns, d_flags);
+    SPH_CU(cudaGetLastError());
+    SPH_CU(cudaMemcpyAsync(h_flags.data(), d_flags, sizeof(int) * ns, cudaMemcpyDeviceToHost, stream));
+    SPH_CU(cudaStreamSynchronize(stream));
+    bool changed = false;
+    for (int s = 0; s < ns; s++)
+      if (h_flags[s]) {
+        meta[act[s]].done = meta[act[s]].failed = true;
+        changed = true;
+      }
+    return changed ? upload_tables() : SPH_OK;
+  }
   sph_status ensure_stage(size_t bytes) {
     if (bytes <= stage_bytes) return SPH_OK;
     if (d_stage) cudaFreeAsync(d_stage, stream);
@@ -620,9 +697,10 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   if (meta[idx].K0 > 0) k_body_mass<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
   int gw = grid_for((int64_t)S.ngroups * 32, 128, grid_warp);
+  int gsw = grid_for(n, sweep_block, grid_sweep);
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
-  k_extrap<R, DIM><<<gp, 256, 0, stream>>>(B);
-  k_force<R, DIM><<<gp, 256, 0, stream>>>(B);
+  k_extrap<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
+  k_force<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
   if (meta[idx].K0 > 0) k_body_reduce<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
   SPH_CU(cudaGetLastError());
@@ -666,6 +744,7 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   int gp = grid_for(np, 256, grid_part);
   int gs = grid_for(ns, 128, 1 << 20);
   int gw = grid_for(ng * 32, 128, grid_warp);
+  int gsw = grid_for(np, sweep_block, grid_sweep);
   int gb = grid_for(nb, 1, grid_blk);
   int gcb = grid_for(ncb, 1, grid_blk);
   int kcount = 0, stage = 0;
@@ -701,11 +780,11 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   rec();
-  k_density<R, DIM><<<gp, 256, 0, stream>>>(B);
+  k_density<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
   rec();
-  k_extrap<R, DIM><<<gp, 256, 0, stream>>>(B);
+  k_extrap<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
   rec();
-  k_force<R, DIM><<<gp, 256, 0, stream>>>(B);
+  k_force<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
   rec();
   if (any_body) { k_body_reduce<R><<<gb, 128, 0, stream>>>(B, 1); kcount++; }
   rec();

@@ -44,8 +44,14 @@ struct EngineImpl final : EngineIface {
     out[16] = st[6];
     out[17] = S.maxnb;
     out[18] = st[9];
+    int32_t lc[3];
+    e.get_launch(lc);
+    out[19] = lc[0]; out[20] = lc[1]; out[21] = lc[2];
     return SPH_OK;
   }
+  sph_status set_launch(const int32_t* cfg, int32_t n) override { return e.set_launch(cfg, n); }
+  void get_launch(int32_t* cfg) override { e.get_launch(cfg); }
+  sph_status time_steps(int32_t n, double* ms) override { return e.time_steps(n, ms); }
   sph_status profile(int32_t reps, double* ms) override { return e.profile(reps, ms); }
   sph_status sync() override {
     cudaError_t err = cudaStreamSynchronize(e.stream);
@@ -63,9 +69,25 @@ struct EngineImpl final : EngineIface {
   }
   bool job_done(int idx) override { return e.meta[idx].done; }
   bool job_reported(int idx) override { return e.meta[idx].reported; }
+  bool job_failed(int idx) override { return e.meta[idx].failed; }
+  sph_status check_failed() override { return e.check_failed(); }
   void set_reported(int idx) override { e.meta[idx].reported = true; }
   int64_t job_id(int idx) override { return e.meta[idx].job_id; }
   int64_t steps_taken() override { return e.steps_taken; }
+  int kernels_per_step() override { return e.act.empty() ? 0 : e.kernels_per_step; }
+  sph_status pairs_total(int64_t* out) override {
+    *out = 0;
+    for (auto& S : e.hs) {
+      unsigned long long pc[2] = {0, 0};
+      if (cudaMemcpyAsync(pc, S.pairs, sizeof(pc), cudaMemcpyDeviceToHost, e.stream) != cudaSuccess ||
+          cudaStreamSynchronize(e.stream) != cudaSuccess) {
+        set_error("cannot read the scene counters");
+        return SPH_ERR_CUDA;
+      }
+      *out += (int64_t)pc[1];
+    }
+    return SPH_OK;
+  }
   size_t footprint(int64_t n, int64_t nc, int64_t kc, int64_t nr, bool trans) override {
     return Engine<R, DIM>::footprint(n, nc, kc, nr, trans);
   }

@@ -42,7 +42,7 @@ __device__ __forceinline__ void quintic(R q, R& w, R& dw) {
 }
 template <class R>
 __device__ __forceinline__ R quintic_w(R q) {
-  R t3 = R(3) - q;
+  R t3 = fmax(R(3) - q, R(0));  // (3 - q)_+: a contracted 3 - r/h may round below zero at the edge
   R t2 = fmax(R(2) - q, R(0));
   R t1 = fmax(R(1) - q, R(0));
   R a2 = t3 * t3, b2 = t2 * t2, c2 = t1 * t1;
@@ -50,7 +50,7 @@ __device__ __forceinline__ R quintic_w(R q) {
 }
 template <class R>
 __device__ __forceinline__ R quintic_dw(R q) {
-  R t3 = R(3) - q;
+  R t3 = fmax(R(3) - q, R(0));
   R t2 = fmax(R(2) - q, R(0));
   R t1 = fmax(R(1) - q, R(0));
   R a2 = t3 * t3, b2 = t2 * t2, c2 = t1 * t1;
@@ -820,6 +820,12 @@ __global__ void k_final(BatchView<R> B) {
       S.P.vz[i] = (R)(S.bu[3 * k + 2] + c[2]);
     }
   }
+}
+
+// non-finite flag of every scene in the batch tables (one copy to the host per poll)
+template <class R>
+__global__ void k_gather_failed(Scene<R>* const* sc, int ns, int* out) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) out[s] = sc[s]->status[0];
 }
 
 template <class R>

@@ -232,11 +232,13 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
       R aw[3] = {R(0), R(0), R(0)};
       if (kind == KRIGID) { aw[0] = S.P.ax[i]; aw[1] = S.P.ay[i]; aw[2] = S.P.az[i]; }
       R ga = (S.gR[0] - aw[0]) * Rv[0] + (S.gR[1] - aw[1]) * Rv[1] + (S.gR[2] - aw[2]) * Rv[2];
-      R inv = R(1) / S0;
-      S.prs[i] = (P0 + ga) * inv;
-      S.vex[i] = R(2) * uw[0] - U[0] * inv;
-      S.vey[i] = R(2) * uw[1] - U[1] * inv;
-      S.vez[i] = R(2) * uw[2] - U[2] * inv;
+      // divide by the weight sum rather than multiply by its reciprocal: with only edge
+      // neighbours the sum can be subnormal in FP32 and its reciprocal overflow, while each
+      // quotient is a weighted mean bounded by the neighbours' values
+      S.prs[i] = (P0 + ga) / S0;
+      S.vex[i] = R(2) * uw[0] - U[0] / S0;
+      S.vey[i] = R(2) * uw[1] - U[1] / S0;
+      S.vez[i] = R(2) * uw[2] - U[2] / S0;
     } else {
       S.prs[i] = R(0);
       S.vex[i] = uw[0]; S.vey[i] = uw[1]; S.vez[i] = uw[2];

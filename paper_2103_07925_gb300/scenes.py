@@ -180,13 +180,15 @@ def tank2d_disc(dx=0.0125, seed=2103, steps_dt=None, jitter=1e-3, fill=0.65,
 def tank3d_spheres(dx=0.01, n_spheres=64, seed=7925, r_range=(0.04, 0.08),
                    dens_range=(1.5, 3.0), c=45.0, rho0=1.0, nu=1e-3, g=-9.81,
                    size=(1.0, 1.0, 2.0), fill=1.0, gap=2.0, jitter=1e-3,
-                   precision=64, dt_mode=1):
+                   precision=64, dt_mode=1, allow_fewer=False, max_tries=200000):
     """3D tank (1 x 1 x 2), fluid to z = 1, ``n_spheres`` rigid spheres, walls open-top.
 
     At dx = 0.01: 1,000,000 fluid lattice sites minus the spheres, 280,908 wall
     particles (floor and four sides up to z = 2, three layers).  Sphere radii are
     uniform in ``r_range``, density ratios uniform in ``dens_range``,
     centres seeded and non-overlapping with a surface gap of ``gap``*dx.
+    With ``allow_fewer`` the
+    placement stops after ``max_tries`` attempts with the spheres placed so far.
     """
     rng = np.random.default_rng(seed)
     nx, ny, nz_tank = (int(round(s / dx)) for s in size)
@@ -196,7 +198,9 @@ def tank3d_spheres(dx=0.01, n_spheres=64, seed=7925, r_range=(0.04, 0.08),
     tries = 0
     while len(centers) < n_spheres:
         tries += 1
-        if tries > 200000:
+        if tries > max_tries:
+            if allow_fewer:
+                break
             raise RuntimeError("could not place spheres")
         r = rng.uniform(r_lo, r_hi)
         m = r + gap * dx
@@ -206,6 +210,7 @@ def tank3d_spheres(dx=0.01, n_spheres=64, seed=7925, r_range=(0.04, 0.08),
         if ok:
             centers.append(cpos)
             radii.append(r)
+    n_spheres = len(centers)
     dens = rng.uniform(dens_range[0], dens_range[1], size=n_spheres) * rho0
     sites = lattice([0.0, 0.0, 0.0], [nx, ny, nzf], dx)
     owner = np.full(len(sites), -1, dtype=np.int64)
@@ -469,3 +474,91 @@ def strong_scaling_cube(dx=0.2, L=30.0, D=2.5, per_axis=6, rho_s=10.0, rho_f=1.0
     p = default_params(3, dx, [-3 * dx] * 3, [L + 3 * dx] * 3, gravity=[0.0, 0.0, g],
                        dt_mode=0, dt_fixed=dt, precision=precision)
     return b.finish(p, mats)
+
+
+# --------------------------------------------------------------------------- batched mix
+
+def tank2d_discs(dx=0.0125, n_discs=1, seed=2103, r_range=(0.03, 0.06), dens_range=(1.5, 3.0),
+                 jitter=1e-3, fill=0.65, c=10.0, rho0=1.0, eta=0.01, g=-1.0, precision=64):
+    """The 2D tank of ``tank2d_disc`` with ``n_discs`` seeded, non-overlapping discs in the
+    fluid (radii uniform in ``r_range`` but at least 2 dx, density ratios in ``dens_range``)."""
+    rng = np.random.default_rng(seed)
+    n = int(round(1.0 / dx))
+    nf = int(round(fill / dx))
+    sites = lattice([0.0, 0.0], [n, nf], dx)
+    owner = np.full(len(sites), -1, dtype=np.int64)
+    centers, radii = [], []
+    tries = 0
+    while len(centers) < n_discs and tries < 100000:
+        tries += 1
+        r = max(rng.uniform(*r_range), 2.0 * dx)
+        m = r + 2 * dx
+        if nf * dx - 2 * m <= 0:
+            break
+        cpos = np.array([rng.uniform(m, n * dx - m), rng.uniform(m, nf * dx - m)])
+        if all(np.linalg.norm(cpos - c2) >= r + r2 + 2 * dx for c2, r2 in zip(centers, radii)):
+            centers.append(cpos)
+            radii.append(r)
+    for k, (cc, r) in enumerate(zip(centers, radii)):
+        owner[np.sum((sites - cc) ** 2, axis=1) <= r * r] = k
+    dens = rng.uniform(dens_range[0], dens_range[1], size=len(centers)) * rho0
+    mats = [material(FLUID, rho0, c=c, eta=eta), material(WALL, rho0), material(RIGID, 2.0 * rho0)]
+    b = _Builder(2)
+    b.add(_jitter(rng, _pad3(sites[owner < 0]), jitter * dx, 2), 0, rho0 * dx * dx, rho0, 300.0)
+    for k in range(len(centers)):
+        kb = b.add_body()
+        b.add(sites[owner == k], 2, dens[k] * dx * dx, dens[k], 300.0, body=kb)
+    b.add(wall_shell(2, [n, n], dx, layers=3), 1, rho0 * dx * dx, rho0, 300.0)
+    lo, hi = -3 * dx, n * dx + 3 * dx
+    p = default_params(2, dx, [lo, lo], [hi, hi], gravity=[0.0, g, 0.0], dt_mode=1, precision=precision)
+    return b.finish(p, mats)
+
+
+def _count_2d(dx, fill=0.65):
+    n, nf = int(round(1.0 / dx)), int(round(fill / dx))
+    return n * nf + (n + 6) ** 2 - n * n
+
+
+def _count_3d(dx):
+    n, nz = int(round(1.0 / dx)), int(round(2.0 / dx))
+    return n ** 3 + (n + 6) ** 2 * (nz + 3) - n * n * nz
+
+
+def dx_for_count(dim, n_target):
+    """Lattice spacing at which the cfg-1 (2D) or cfg-2 (3D) template holds about n_target
+    particles (bisection on the exact site count of the template)."""
+    f = _count_2d if dim == 2 else _count_3d
+    lo, hi = 1e-4, 0.2
+    for _ in range(60):
+        mid = math.sqrt(lo * hi)
+        if f(mid) > n_target:
+            lo = mid
+        else:
+            hi = mid
+    return hi
+
+
+def batch_mix(count=256, seed=2103, n_lo=1e4, n_hi=5e5, max_bodies=50, precision=32):
+    """Independent scenes of uneven size for the batched form: log N normal around
+    sqrt(n_lo n_hi) with sigma ln(n_hi/n_lo)/4, clipped to [n_lo, n_hi]; 2D or 3D by a seeded
+    coin; 0..max_bodies bodies; each scene is the 2D disc tank or the 3D sphere tank at the
+    spacing that gives its N.  Returns a list of (scene, spec) pairs."""
+    rng = np.random.default_rng(seed)
+    mu, sig = math.log(math.sqrt(n_lo * n_hi)), math.log(n_hi / n_lo) / 4.0
+    out = []
+    for q in range(count):
+        n_t = float(np.clip(math.exp(rng.normal(mu, sig)), n_lo, n_hi))
+        dim = 2 if rng.uniform() < 0.5 else 3
+        nb = int(rng.integers(0, max_bodies + 1))
+        dx = dx_for_count(dim, n_t)
+        s = int(rng.integers(0, 2 ** 31 - 1))
+        if dim == 2:
+            sc = tank2d_discs(dx=dx, n_discs=nb, seed=s, precision=precision)
+        else:
+            r_lo, r_hi = max(0.04, 1.5 * dx), max(0.08, 2.0 * dx)
+            sc = tank3d_spheres(dx=dx, n_spheres=nb, seed=s, r_range=(r_lo, r_hi), precision=precision,
+                                allow_fewer=True, max_tries=20000)
+            nb = len(sc["bodies"]["quat"])
+        out.append((sc, dict(index=q, dim=dim, bodies=nb, dx=dx, target=n_t,
+                             n=int(len(sc["particles"]["mass"])))))
+    return out

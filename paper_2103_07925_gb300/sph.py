@@ -27,7 +27,8 @@ EXPORTS = ["sph_create_scene", "sph_step", "sph_step_async", "sph_read_fields", 
            "sph_last_error", "sph_batch_create", "sph_job_footprint", "sph_batch_admit",
            "sph_batch_step", "sph_batch_poll", "sph_batch_read_fields", "sph_batch_job_diagnostics",
            "sph_batch_release", "sph_batch_info", "sph_batch_destroy", "sph_profile",
-           "sph_profile_stage_name", "sph_density_static"]
+           "sph_profile_stage_name", "sph_density_static", "sph_set_launch", "sph_time_steps",
+           "sph_batch_set_launch", "sph_batch_time_steps", "sph_batch_job_state"]
 PROFILE_STAGES = 20
 
 
@@ -106,6 +107,11 @@ def lib():
             "sph_batch_job_diagnostics": [vp, i64, C.POINTER(C.c_double)],
             "sph_batch_release": [vp, i64],
             "sph_batch_info": [vp, C.POINTER(i64)],
+            "sph_set_launch": [vp, C.POINTER(i32), i32],
+            "sph_time_steps": [vp, i32, C.POINTER(C.c_double)],
+            "sph_batch_set_launch": [vp, i32, C.POINTER(i32), i32],
+            "sph_batch_time_steps": [vp, i32, C.POINTER(C.c_double)],
+            "sph_batch_job_state": [vp, i64, C.POINTER(i32)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -272,8 +278,20 @@ class Scene:
         _check(lib().sph_info(self.h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         keys = ["n", "n_fluid", "n_rigid", "n_wall", "n_bodies", "n_cells", "cells_x", "cells_y", "cells_z",
                 "steps", "kernels_per_step", "bytes", "groups", "cells_per_group", "key_order", "pairs_total",
-                "rebuilds", "list_capacity", "relabelled"]
+                "rebuilds", "list_capacity", "relabelled", "sweep_block", "sweep_blocks_per_sm",
+                "search_blocks_per_sm"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
+
+    def set_launch(self, sweep_block=256, sweep_waves=0, search_waves=0):
+        """Launch shape of the pair sweeps and the search (see sph_set_launch)."""
+        cfg = (C.c_int32 * 3)(sweep_block, sweep_waves, search_waves)
+        _check(lib().sph_set_launch(self.h, cfg, 3))
+
+    def time_steps(self, n):
+        """Device time (ms) of n steps, measured with CUDA events; the scene advances."""
+        ms = C.c_double()
+        _check(lib().sph_time_steps(self.h, n, C.byref(ms)))
+        return ms.value
 
     def profile(self, reps=3):
         """Mean device time per stage (ms) over reps steps launched kernel by kernel."""
@@ -327,11 +345,27 @@ class Batch:
     def step(self, n):
         _check(lib().sph_batch_step(self.h, n))
 
+    def set_launch(self, dim, sweep_block=256, sweep_waves=0, search_waves=0):
+        cfg = (C.c_int32 * 3)(sweep_block, sweep_waves, search_waves)
+        _check(lib().sph_batch_set_launch(self.h, dim, cfg, 3))
+
+    def time_steps(self, n):
+        """Device time (ms) of step(n), measured with CUDA events."""
+        ms = C.c_double()
+        _check(lib().sph_batch_time_steps(self.h, n, C.byref(ms)))
+        return ms.value
+
     def poll(self, max_done=4096):
         ids = np.zeros(max_done, dtype=np.int64)
         nd = C.c_int32()
         _check(lib().sph_batch_poll(self.h, ids.ctypes.data, max_done, C.byref(nd)))
         return [int(x) for x in ids[:nd.value]]
+
+    def state(self, job_id):
+        """'advancing', 'finished' or 'failed' (non-finite velocities)."""
+        st = C.c_int32()
+        _check(lib().sph_batch_job_state(self.h, job_id, C.byref(st)))
+        return ("advancing", "finished", "failed")[st.value]
 
     def read(self, job_id, *names):
         n = self._n[job_id]
@@ -357,7 +391,7 @@ class Batch:
         out = np.zeros(8, dtype=np.int64)
         _check(lib().sph_batch_info(self.h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         return dict(jobs=int(out[0]), particles=int(out[1]), bytes=int(out[2]), steps=int(out[3]),
-                    active=int(out[4]))
+                    active=int(out[4]), kernels_per_step=int(out[5]), pairs_total=int(out[6]))
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,0 +1,127 @@
+"""Batched and continuously batched scenes on the GPU: every scene's result is the same
+alone (its own scene object, its own CUDA graph) and in a mix of 2D and 3D scenes of
+uneven sizes advanced together, including scenes admitted while others are running and
+scenes with phase transitions; admission honours the memory cap."""
+import numpy as np
+import pytest
+
+from paper_2103_07925_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+FIELDS = ("pos", "vel", "rho", "pres", "temp", "dtemp", "mat", "body")
+
+
+def _mix():
+    from tests.test_gpu_relabel import _cycle
+    # bodies 0.2 apart: no particle pair sits exactly at the contact distance dx, where the
+    # contact law jumps by d_c v_n and an FP32 distance may fall on the other side of dx
+    hot = S.periodic_box(dim=3, n=10, dx=0.1, bodies=2, body_radius=0.15, kappa=0.05, T_amp=5.0)
+    return [
+        ("tank2d", S.tank2d_disc(dx=0.025), 7),
+        ("tank3d", S.tank3d_spheres(dx=0.05, n_spheres=3, r_range=(0.1, 0.15), size=(1.0, 1.0, 1.5), fill=0.8), 5),
+        ("box3d_heat", hot, 9),
+        ("box2d", S.periodic_box(dim=2, n=30, bodies=4, body_radius=0.2), 6),
+        ("cycle2d", _cycle(), 8),
+        ("hydro2d", S.hydrostatic_tank2d(), 4),
+    ]
+
+
+def _alone(sc, steps, precision):
+    from paper_2103_07925_gb300.sph import Scene
+    g = Scene(sc, precision=precision)
+    g.step(steps)
+    out = g.read(*FIELDS)
+    g.close()
+    return out
+
+
+def _equal(a, b, name):
+    for f in FIELDS:
+        np.testing.assert_array_equal(a[f], b[f], err_msg="%s: %s" % (name, f))
+
+
+def _run_until_done(B, ids, limit=100):
+    done = set()
+    for _ in range(limit):
+        B.step(1)
+        done |= set(B.poll())
+        if done >= set(ids):
+            return done
+    raise AssertionError("jobs did not finish")
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_each_result_is_the_same_alone_and_in_the_mix(precision):
+    from paper_2103_07925_gb300.sph import Batch
+    mix = _mix()
+    B = Batch(capacity=16, precision=precision)
+    ids = {}
+    for name, sc, steps in mix:
+        ids[name] = B.admit(sc, steps)
+        assert ids[name] is not None
+    _run_until_done(B, list(ids.values()))
+    for name, sc, steps in mix:
+        _equal(B.read(ids[name], *FIELDS), _alone(sc, steps, precision), name)
+    B.close()
+
+
+def test_jobs_admitted_while_others_run_match_alone():
+    from paper_2103_07925_gb300.sph import Batch
+    mix = _mix()
+    B = Batch(capacity=16, precision=32)
+    first, late = mix[:3], mix[3:]
+    ids = {name: B.admit(sc, steps) for name, sc, steps in first}
+    B.step(2)
+    ids.update({name: B.admit(sc, steps) for name, sc, steps in late})
+    _run_until_done(B, list(ids.values()))
+    for name, sc, steps in mix:
+        _equal(B.read(ids[name], *FIELDS), _alone(sc, steps, 32), name)
+    # a finished job stays readable until released; releasing it frees its memory
+    before = B.info()["bytes"]
+    B.release(ids["tank3d"])
+    assert B.info()["bytes"] < before
+    assert B.info()["jobs"] == len(mix) - 1
+    B.close()
+
+
+def test_admission_by_memory_footprint():
+    from paper_2103_07925_gb300.sph import Batch
+    a = S.tank2d_disc(dx=0.025)
+    b = S.periodic_box(dim=3, n=12, bodies=1)
+    fa, fb = Batch.footprint(a, precision=32), Batch.footprint(b, precision=32)
+    assert fa > 0 and fb > 0
+    B = Batch(capacity=8, hbm_cap_bytes=max(fa, fb) + min(fa, fb) // 2, precision=32)  # one at a time
+    ja = B.admit(a, 3)
+    assert ja is not None
+    assert B.admit(b, 3) is None  # does not fit beside a
+    _run_until_done(B, [ja])
+    B.release(ja)
+    jb = B.admit(b, 3)  # fits once a has left
+    assert jb is not None
+    _run_until_done(B, [jb])
+    _equal(B.read(jb, *FIELDS), _alone(b, 3, 32), "box3d")
+    B.close()
+
+
+def test_batch_fp32_against_oracle_on_sampled_scenes():
+    """FP32 in the mix against the FP64 oracle after one step (per-step field tolerance)."""
+    from oracle.oracle import OracleScene
+    from paper_2103_07925_gb300.sph import Batch
+    from tests.parity import compare_fields, field_scales
+    mix = _mix()
+    B = Batch(capacity=16, precision=32)
+    ids = {name: B.admit(sc, 1) for name, sc, _ in mix}
+    _run_until_done(B, list(ids.values()))
+    for name, sc, _ in mix[:4]:
+        o = OracleScene(sc)
+        o.step(1)
+
+        class View:
+            def read(self, f, _id=ids[name]):
+                return B.read(_id, f)
+
+        errs = compare_fields(View(), o, fields=["pos", "vel", "rho", "pres", "temp"], ints=["mat", "body"],
+                              scales=field_scales(sc))
+        bad = {f: e for f, e in errs.items() if not e < 1e-5}
+        assert not bad, (name, bad)
+    B.close()
