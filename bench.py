@@ -27,6 +27,10 @@ sys.path.insert(0, ROOT)
 METRIC = "SPH pair-interactions/s & steps/s at 1M particles; p50/p99 job latency vs plain"
 FLOP_PER_PAIR = 62      # FP32 pair arithmetic of the force/heat sweep, FMA = 2 (see the design notes)
 BYTES_PER_TARGET = 72   # algorithmic HBM bytes per target particle of the force sweep (FP32)
+# DRAM bytes (read + write) of one k_force launch on the default workload, from
+# `ncu --set full` of this kernel version (profiles/ncu_k_force_tank3d_fp32.md); None once
+# the kernel changes and until it is captured again
+K_FORCE_TRAFFIC = 851.8e6
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
@@ -257,9 +261,12 @@ def bench_serve(args, rank, world, allmax, allsum, barrier):
     jobs = serving_jobs(args.jobs, rate=20.0, steps=args.job_steps, seed=2103 + rank)
     work = sum(j.steps for j in jobs)
     res = {}
-    for name, cap in (("cap150GB", 150 << 30), ("cap2GB", 2 << 30)):
+    runs = (("sjf_cap150GB", 150 << 30, "sjf"), ("fifo_cap150GB", 150 << 30, "fifo"),
+            ("sjf_cap2GB", 2 << 30, "sjf"), ("fifo_cap2GB", 2 << 30, "fifo"))
+    for name, cap, policy in runs:
         B = Batch(capacity=256, hbm_cap_bytes=cap, precision=32)
-        srv = Server(B, step_batch=10, fields=("pos",))
+        srv = Server(B, step_batch=10, fields=("pos",), policy=policy,
+                     max_particles=2_000_000 if policy == "sjf" else None, max_wait=30.0)
         barrier()
         t0 = time.perf_counter()
         done = srv.run(jobs)
@@ -267,19 +274,21 @@ def bench_serve(args, rank, world, allmax, allsum, barrier):
         B.close()
         res[name] = dict(percentiles(done), scene_steps_per_s=allsum(work) / t, seconds=t,
                          peak_jobs=srv.max_jobs, peak_bytes=srv.max_bytes, failed=sum(d.failed for d in done))
-    barrier()
-    t0 = time.perf_counter()
-    done = serve_plain(jobs, lambda sc, **kw: Scene(sc, precision=32, **kw), fields=("pos",))
-    t = allmax(time.perf_counter() - t0)
-    res["plain"] = dict(percentiles(done), scene_steps_per_s=allsum(work) / t, seconds=t,
-                        failed=sum(d.failed for d in done))
-    b = res["cap150GB"]
+    for policy in ("fifo", "sjf"):
+        barrier()
+        t0 = time.perf_counter()
+        done = serve_plain(jobs, lambda sc, **kw: Scene(sc, precision=32, **kw), fields=("pos",), policy=policy)
+        t = allmax(time.perf_counter() - t0)
+        res["plain_" + policy] = dict(percentiles(done), scene_steps_per_s=allsum(work) / t, seconds=t,
+                                      failed=sum(d.failed for d in done))
+    b = res["sjf_cap150GB"]
     out = {"metric": "p50/p99 job latency, serving (Poisson 20/s) vs plain", "value": b["p50"], "unit": "s",
            "n_gpus": world, "steps": args.job_steps, "warmup": 0, "ms_per_step": None,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
            "config": {"workload": "%d jobs, N log-uniform [5e3, 1e6], 0-100 bodies, %d steps each, Poisson "
                                   "arrivals 20/s" % (len(jobs), args.job_steps),
+                      "policy": "shortest work first, 2M resident particles, 150 GB cap (all runs in 'serving')",
                       "particles": int(sum(len(j.scene["particles"]["mass"]) for j in jobs))},
            "p99": b["p99"], "serving": res,
            "e2e": {"value": b["p50"], "unit": "s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
@@ -386,7 +395,9 @@ def main():
            "list_rebuilds": g.info()["rebuilds"],
            "gpu_launches": args.steps * g.info()["kernels_per_step"],
            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                        "frac": achieved_tf / peak_tf, "traffic": None, "kernel": "k_force",
+                        "frac": achieved_tf / peak_tf,
+                        "traffic": K_FORCE_TRAFFIC if (args.dx == 0.01 and args.precision == 32) else None,
+                        "kernel": "k_force",
                         "peak_source": "FP32 FMA lanes x SMs x 2 x max SM clock (%s clocks)" % peak_src,
                         "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": hbm, "frac": hbm_ach / hbm,
                                 "peak_source": peak_src}},

@@ -55,42 +55,82 @@ def percentiles(done):
     return dict(p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)), mean=float(lat.mean()))
 
 
+def job_work(j):
+    """Particle-steps of a job (its cost on the device, up to a per-step overhead)."""
+    return len(j.scene["particles"]["mass"]) * j.steps if "particles" in j.scene else j.scene["n"] * j.steps
+
+
+def job_particles(j):
+    return len(j.scene["particles"]["mass"]) if "particles" in j.scene else j.scene["n"]
+
+
 class Server:
     """Continuous batching of scene jobs on one GPU.
 
-    Jobs are taken in arrival order; the head of the queue is admitted as soon as the batch
-    has a free slot and its footprint fits under the cap (no overtaking, so a large job is
-    never starved by small ones).  While jobs are resident the batch advances by
-    ``step_batch`` steps per iteration; finished jobs are read out (``fields``) and released,
-    which frees their memory for the next admissions.
+    Every resident job advances by one step per batch step, so a job's latency is its step
+    count times the duration of the batch steps it shares.  Two admission policies:
+
+    * ``fifo``: arrival order; the head of the queue is admitted as soon as a slot is free
+      and its footprint fits under the cap (no overtaking).
+    * ``sjf``: among the jobs that have arrived, the one with the least work (particles x
+      steps) first, while the resident particles stay within ``max_particles`` (a job larger
+      than the budget runs when the batch is otherwise empty).  A job that has waited longer
+      than ``max_wait`` seconds goes first, so that large jobs are not starved.
+
+    While jobs are resident the batch advances by ``step_batch`` steps per iteration;
+    finished jobs are read out (``fields``) and released, which frees their slot and memory.
     """
 
-    def __init__(self, batch, step_batch=10, fields=("pos", "vel"), clock=time.perf_counter, sleep=time.sleep):
+    def __init__(self, batch, step_batch=10, fields=("pos", "vel"), policy="fifo", max_particles=None,
+                 max_wait=float("inf"), clock=time.perf_counter, sleep=time.sleep):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy must be fifo or sjf")
         self.batch = batch
         self.step_batch = step_batch
         self.fields = tuple(fields)
+        self.policy = policy
+        self.max_particles = max_particles
+        self.max_wait = max_wait
         self.clock = clock
         self.sleep = sleep
         self.max_bytes = 0
         self.max_jobs = 0
 
+    def _pick(self, arrived, t):
+        """Index in ``arrived`` of the next job to admit."""
+        if self.policy == "fifo":
+            return 0
+        late = [q for q, j in enumerate(arrived) if t - j.arrival > self.max_wait]
+        if late:
+            return late[0]
+        return min(range(len(arrived)), key=lambda q: (job_work(arrived[q]), arrived[q].arrival))
+
     def run(self, jobs):
         queue = collections.deque(sorted(jobs, key=lambda j: j.arrival))
+        arrived = []    # arrived, not admitted (arrival order)
         resident = {}   # batch id -> (job, admitted time)
+        live = 0        # resident particles
         done = []
         t0 = self.clock()
         now = lambda: self.clock() - t0
-        while queue or resident:
+        while queue or arrived or resident:
             t = now()
-            # admissions: head of the queue while it has arrived and fits
             while queue and queue[0].arrival <= t:
-                j = queue[0]
+                arrived.append(queue.popleft())
+            # admissions in policy order while they fit
+            while arrived:
+                q = self._pick(arrived, t)
+                j = arrived[q]
+                n = job_particles(j)
+                if self.max_particles is not None and resident and live + n > self.max_particles:
+                    break
                 bid = self.batch.admit(j.scene, j.steps, **j.overrides)
                 if bid is None:
                     if not resident:
                         raise RuntimeError("job %d does not fit into an empty batch" % j.job_id)
                     break
-                queue.popleft()
+                arrived.pop(q)
+                live += n
                 resident[bid] = (j, now())
             info = self.batch.info()
             self.max_bytes = max(self.max_bytes, info["bytes"])
@@ -102,6 +142,7 @@ class Server:
             self.batch.step(self.step_batch)
             for bid in self.batch.poll():
                 j, ta = resident.pop(bid)
+                live -= job_particles(j)
                 failed = self.batch.state(bid) == "failed" if hasattr(self.batch, "state") else False
                 res = self.batch.read(bid, *self.fields) if self.fields else {}
                 if len(self.fields) == 1:
@@ -111,15 +152,22 @@ class Server:
         return done
 
 
-def serve_plain(jobs, make_scene, fields=("pos", "vel"), clock=time.perf_counter, sleep=time.sleep):
-    """The same arrivals served one scene at a time: create, run all steps, read, destroy."""
+def serve_plain(jobs, make_scene, fields=("pos", "vel"), policy="fifo", clock=time.perf_counter, sleep=time.sleep):
+    """The same arrivals served one scene at a time: create, run all steps, read, destroy.
+    ``policy`` picks the next job among those that have arrived (fifo or sjf, as above)."""
     done = []
     t0 = clock()
     now = lambda: clock() - t0
-    for j in sorted(jobs, key=lambda j: j.arrival):
-        wait = j.arrival - now()
-        if wait > 0:
-            sleep(wait)
+    queue = collections.deque(sorted(jobs, key=lambda j: j.arrival))
+    arrived = []
+    while queue or arrived:
+        while queue and queue[0].arrival <= now():
+            arrived.append(queue.popleft())
+        if not arrived:
+            sleep(max(0.0, queue[0].arrival - now()))
+            continue
+        q = 0 if policy == "fifo" else min(range(len(arrived)), key=lambda q: (job_work(arrived[q]), arrived[q].arrival))
+        j = arrived.pop(q)
         ta = now()
         g = make_scene(j.scene, **j.overrides)
         failed = False

@@ -151,3 +151,64 @@ def test_poisson_arrivals_have_the_requested_rate():
     a = poisson_arrivals(20000, 20.0, seed=1)
     assert np.all(np.diff(a) > 0)
     assert abs(len(a) / a[-1] - 20.0) < 0.5
+
+
+def test_sjf_admits_least_work_first_within_the_particle_budget():
+    clk = Clock()
+    fb = FakeBatch(clk, cap_bytes=10 ** 12, capacity=64)
+    sizes = [5000, 100, 3000, 200, 50]
+    done = Server(fb, step_batch=10, policy="sjf", max_particles=3000, clock=clk, sleep=clk.sleep).run(
+        _jobs(sizes, [0.0] * 5))
+    assert fb.order[:3] == ["j4", "j1", "j3"]  # least work first
+    assert len(done) == 5
+    lat = {d.job_id: d.latency for d in done}
+    assert lat[4] < lat[2] < lat[0]
+
+
+def test_sjf_budget_is_respected_and_oversized_job_runs_alone():
+    clk = Clock()
+
+    class Watch(FakeBatch):
+        peak_n = 0
+
+        def step(self, k):
+            live = sum(j["n"] for j in self.jobs.values() if not j["done"])
+            Watch.peak_n = max(Watch.peak_n, live)
+            super().step(k)
+
+    fb = Watch(clk, cap_bytes=10 ** 12, capacity=64)
+    done = Server(fb, step_batch=5, policy="sjf", max_particles=1000, clock=clk, sleep=clk.sleep).run(
+        _jobs([400, 400, 400, 2500], [0.0, 0.0, 0.0, 0.0]))
+    assert len(done) == 4
+    assert Watch.peak_n == 2500  # the oversized job alone; the small ones at most 800 together
+
+
+def test_sjf_aging_lets_a_large_job_through():
+    clk = Clock()
+    fb = FakeBatch(clk, cap_bytes=10 ** 12, capacity=64)
+    # a stream of small jobs would starve the large one without aging
+    sizes = [3000] + [100] * 30
+    arr = [0.0] + [0.001 * q for q in range(30)]
+    done = {d.job_id: d for d in Server(fb, step_batch=10, policy="sjf", max_particles=3000, max_wait=0.005,
+                                        clock=clk, sleep=clk.sleep).run(_jobs(sizes, arr))}
+    assert done[0].admitted < max(d.admitted for d in done.values())
+
+
+def test_plain_sjf_serves_small_jobs_first():
+    class PlainScene:
+        def __init__(self, clk, scene):
+            self.clk, self.sc = clk, scene
+
+        def step(self, k):
+            self.clk.t += k * 1e-6 * self.sc["n"]
+
+        def read(self, *names):
+            return self.sc["name"]
+
+        def close(self):
+            pass
+
+    clk = Clock()
+    done = serve_plain(_jobs([5000, 10, 20], [0.0, 0.0, 0.0]), lambda sc: PlainScene(clk, sc), fields=("pos",),
+                       policy="sjf", clock=clk, sleep=clk.sleep)
+    assert [d.job_id for d in done] == [1, 2, 0]
