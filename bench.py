@@ -46,11 +46,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--key-order", type=int, default=0)
-    ap.add_argument("--dx", type=float, default=0.01)
+    ap.add_argument("--dx", type=float, default=None, help="lattice spacing (default 0.01 tank, 0.005 powder)")
     ap.add_argument("--skin", type=float, default=0.3, help="Verlet skin in units of h")
-    ap.add_argument("--workload", default="tank3d", choices=["tank3d", "batch", "serve"],
-                    help="tank3d: the 1.28M-particle tank (default); batch: 256 mixed scenes in one "
-                         "batch; serve: Poisson job arrivals served by continuous batching")
+    ap.add_argument("--workload", default="tank3d", choices=["tank3d", "powder", "batch", "serve"],
+                    help="tank3d: the 1.28M-particle tank (default); powder: the 2.1M-particle powder "
+                         "bed with melting grains; batch: 256 mixed scenes in one batch; serve: Poisson "
+                         "job arrivals served by continuous batching")
     ap.add_argument("--scenes", type=int, default=256, help="batch: number of scenes")
     ap.add_argument("--jobs", type=int, default=32, help="serve: number of jobs")
     ap.add_argument("--job-steps", type=int, default=1000, help="serve: steps per job")
@@ -115,29 +116,38 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def workload(dx):
+DEFAULT_DX = {"tank3d": 0.01, "powder": 0.005}
+WORKLOAD_NAME = {"tank3d": "tank3d_64spheres (1x1x2 tank, fluid to z=1, dx=%g)",
+                 "powder": "powder_bed (1x0.5x0.5 box, gas, metal grains melting under a moving source, dx=%g)"}
+
+
+def workload(dx, name="tank3d"):
     from paper_2103_07925_gb300 import scenes
+    if name == "powder":
+        return scenes.powder_bed(dx=dx)
     if abs(dx - 0.01) < 1e-12:
         return scenes.tank3d_spheres()
     return scenes.tank3d_spheres(dx=dx)
 
 
 def run_reference(args):
-    """The FP64 CPU oracle on the host cores (rank 0 only), bounded samples per step."""
+    """The FP64 CPU oracle on the host cores (rank 0 only) on the same scene as our arm.
+    Bounded sample: at most 1 warm-up step and 10 timed steps, whatever --steps/--warmup
+    say (one oracle step of the 1.28M-particle tank takes about a second on 16 cores); the
+    value is a rate, so it does not depend on the number of steps timed."""
     from oracle.oracle import OracleScene
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # bounded sample: the full scene when the run is short, else a coarser copy of it
-    total = args.steps + args.warmup
-    dx = 0.01 if total <= 12 else (0.02 if total <= 200 else 0.03)
-    sc = workload(dx)
+    name = args.workload if args.workload in DEFAULT_DX else "tank3d"
+    dx = args.dx or DEFAULT_DX[name]
+    sc = workload(dx, name)
     o = OracleScene(sc)
-    o.step(args.warmup)
-    p0 = o.diagnostics()[15]
+    w, k = min(args.warmup, 1), max(1, min(args.steps, 10))
+    o.step(w)
     t0 = time.perf_counter()
     pairs = 0.0
-    for _ in range(args.steps):
+    for _ in range(k):
         o.step(1)
         pairs += o.diagnostics()[15]
     t = time.perf_counter() - t0
@@ -146,20 +156,20 @@ def run_reference(args):
     n = len(sc["particles"]["mass"])
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "pair-interactions/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+           "ms_per_step": 1e3 * t / k, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "tank3d_64spheres", "dx": dx, "particles": n, "l2": "inputs larger than L2"},
+           "config": {"workload": WORKLOAD_NAME[name] % dx, "particles": n,
+                      "l2": "inputs larger than L2"},
            "cpu_baseline": {"value": val, "unit": "pair-interactions/s", "cores": cores, "kind": "oracle",
-                            "sample": "%d oracle steps of the tank scene at dx=%g (%d particles)" % (args.steps, dx, n)},
-           "e2e": {"value": val, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-           "first_step_pairs": p0}
+                            "sample": "%d timed FP64 oracle steps (after %d warm-up) of the same %d-particle "
+                                      "scene" % (k, w, n)},
+           "e2e": {"value": val, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
-def cpu_baseline():
-    """Oracle timed on the host cores on a bounded sample (full scene, 2 steps)."""
+def cpu_baseline(sc):
+    """Oracle timed on the host cores on a bounded sample (the same scene, 2 steps)."""
     from oracle.oracle import OracleScene
-    sc = workload(0.01)
     o = OracleScene(sc)
     t0 = time.perf_counter()
     pairs = 0.0
@@ -168,7 +178,7 @@ def cpu_baseline():
         pairs += o.diagnostics()[15]
     t = time.perf_counter() - t0
     return {"value": pairs / t, "unit": "pair-interactions/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "2 FP64 oracle steps of the full 1,280,908-particle tank scene (%.1f s)" % t}
+            "sample": "2 FP64 oracle steps of the same %d-particle scene (%.1f s)" % (len(sc["particles"]["mass"]), t)}
 
 
 def bench_batch(args, rank, world, allmax, allsum, barrier):
@@ -342,7 +352,8 @@ def main():
         return
     from paper_2103_07925_gb300.sph import Scene
     hbm, smmax, peak_src = peaks()
-    sc = workload(args.dx)
+    dx = args.dx or DEFAULT_DX[args.workload]
+    sc = workload(dx, args.workload)
     stream = torch.cuda.Stream()
     skin = args.skin * sc["params"]["h"]
     g = Scene(sc, precision=args.precision, stream=stream.cuda_stream, key_order=args.key_order, skin=skin)
@@ -382,7 +393,7 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
-           "config": {"workload": "tank3d_64spheres (1x1x2 tank, fluid to z=1, dx=%g)" % args.dx,
+           "config": {"workload": WORKLOAD_NAME[args.workload] % dx,
                       "particles": info["n"], "fluid": info["n_fluid"], "rigid": info["n_rigid"],
                       "wall": info["n_wall"], "bodies": info["n_bodies"], "cells": info["n_cells"],
                       "precision": "FP32 pair sums, FP64 bodies" if args.precision == 32 else "FP64",
@@ -393,10 +404,12 @@ def main():
            "steps_per_s": steps_per_s * world,
            "pairs_per_step": pairs_per_step,
            "list_rebuilds": g.info()["rebuilds"],
+           "relabelled": g.info()["relabelled"],
            "gpu_launches": args.steps * g.info()["kernels_per_step"],
            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                         "frac": achieved_tf / peak_tf,
-                        "traffic": K_FORCE_TRAFFIC if (args.dx == 0.01 and args.precision == 32) else None,
+                        "traffic": K_FORCE_TRAFFIC if (args.workload == "tank3d" and dx == 0.01
+                                                       and args.precision == 32) else None,
                         "kernel": "k_force",
                         "peak_source": "FP32 FMA lanes x SMs x 2 x max SM clock (%s clocks)" % peak_src,
                         "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": hbm, "frac": hbm_ach / hbm,
@@ -449,7 +462,7 @@ def main():
                       "d2h_bytes_per_step": int(outp["pos"].nbytes + outp["vel"].nbytes), "steps": ke,
                       "ms_per_step": 1e3 * te / ke}
     if rank == 0 and world == 1 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline()
+        out["cpu_baseline"] = cpu_baseline(sc)
     g.close()
     if rank == 0:
         print(json.dumps(out))

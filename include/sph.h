@@ -215,7 +215,7 @@ sph_status sph_time_steps(sph_scene* scene, int32_t nsteps, double* ms);
 /* Tracing: run reps complete steps with the kernels launched one by one (no graph) and
  * CUDA events between them; ms_per_stage[SPH_PROFILE_STAGES] receives the mean device
  * time of each stage.  The scene advances by reps steps. */
-#define SPH_PROFILE_STAGES 20
+#define SPH_PROFILE_STAGES 21
 sph_status sph_profile(sph_scene* scene, int32_t reps, double* ms_per_stage);
 const char* sph_profile_stage_name(int32_t stage);
 

@@ -93,6 +93,7 @@ struct Scene {
   double* rb2;         // relabel: body-frame offsets in the new slot order
   R* fr2;              // relabel: slot forces in the new slot order
   int* aux;            // relabel: smallest input index of each new-body component (per root)
+  int* bst2;           // relabel: new slot range of every body (start, then end at + Kcap)
   double* rb;          // body-frame offset of every slot (3 per slot)
   int* slot_part;      // slot -> current sorted particle index
   R* fr;               // force on every slot (3 per slot)

@@ -203,6 +203,8 @@ class Engine {
     grid_part = sms * std::max(1, b1);
     grid_warp = sms * std::max(1, b2);
     grid_blk = sms * 8;
+    SPH_CU(cudaFuncSetAttribute(k_rl_slots_order<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                2 * kSortCap * (int)sizeof(int)));
     return apply_launch();
   }
 
@@ -356,7 +358,8 @@ class Engine {
     size_t bodies = (size_t)kcap * (60 * sizeof(double) + 3 * sizeof(int));
     size_t slots = (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R) + sizeof(int));
     // relabel scratch: offsets and forces in the new slot order, one root mark per particle
-    size_t relabel = trans ? (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R)) + (size_t)n * sizeof(int) : 0;
+    size_t relabel = trans ? (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R)) + (size_t)n * sizeof(int) +
+                                 (size_t)kcap * 2 * sizeof(int) : 0;
     return per * (size_t)n + cells + bodies + slots + relabel + 4096;
   }
 
@@ -576,6 +579,7 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     SPH_TRY(A(&S.rb2, 3 * (size_t)S.nslot));
     SPH_TRY(A(&S.fr2, 3 * (size_t)S.nslot));
     SPH_TRY(A(&S.aux, (size_t)n));
+    SPH_TRY(A(&S.bst2, 2 * (size_t)S.Kcap));
   }
   SPH_TRY(A(&S.bstart, (size_t)kc));
   SPH_TRY(A(&S.bend, (size_t)kc));
@@ -718,12 +722,10 @@ sph_status Engine<R, DIM>::remove_scene(int idx) {
   return upload_tables();
 }
 
-// stage names of a step, in launch order (sph_profile reports one time per stage)
-static const char* const kStageNames[] = {"umax", "dt", "body_kick_drift", "kick_drift", "decide", "bin",
-                                          "scan_blocks", "scan_top", "scan_cells", "scatter", "rank", "permute",
-                                          "flip", "search_density", "density", "extrap", "force", "body_reduce",
-                                          "final", "end_step"};
-constexpr int kStages = 20;
+// stages of a step, in launch order (sph_profile reports one time per stage; the names are
+// those of sph_profile_stage_name)
+constexpr int kStages = 21;
+static_assert(kStages == SPH_PROFILE_STAGES, "profiled stages");
 
 // Launch one step.  With ev != nullptr an event is recorded before the first stage and
 // after every stage (stages that do not apply record an empty interval).
@@ -805,7 +807,7 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
     k_rl_slots_count<R><<<gp, 256, 0, stream>>>(B);
     k_rl_slots_scan<R><<<gsb, 1024, 0, stream>>>(B);
     k_rl_slots_fill<R><<<gp, 256, 0, stream>>>(B);
-    k_rl_slots_order<R><<<grid_for(nb * 32, 128, grid_part), 128, 0, stream>>>(B);
+    k_rl_slots_order<R><<<gb, 512, 2 * kSortCap * sizeof(int), stream>>>(B);
     k_rl_slots_adopt<R><<<gsl, 256, 0, stream>>>(B);
     k_rl_bodies_pre<R><<<grid_for(nb, 128, grid_part), 128, 0, stream>>>(B);
     k_body_mass<R><<<gb, 128, 0, stream>>>(B, 1);
@@ -813,6 +815,7 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
     k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 1);
     kcount += 16;
   }
+  rec();
   k_end_step<R><<<gs, 128, 0, stream>>>(B);
   rec();
   kcount += 17;

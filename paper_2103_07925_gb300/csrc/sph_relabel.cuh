@@ -9,7 +9,8 @@
 //                  input index)
 //   k_rl_number    new body ids K + rank in that order
 //   k_rl_apply     relabel: materials, body ids, accelerations of melting particles
-//   k_rl_slots*    regroup the rigid slots by body (stable: input index order)
+//   k_rl_slots*    regroup the rigid slots by body: unchanged bodies keep their order, changed
+//                  bodies are sorted by input index
 //   k_rl_bodies    mass quantities of changed bodies (k_body_mass), velocity correction
 //                  u_k = u'_k + w_k x (r_k - r'_k), start state of new bodies
 // Every kernel returns at once when no particle changed phase in this step.
@@ -63,6 +64,27 @@ __global__ void k_rl_flag(BatchView<R> B) {
   }
 }
 
+// squared distance of a join candidate, decided in FP64 on both paths (the FP64 path
+// reuses its bit-exact pair distance; the FP32 path rebuilds absolute positions)
+template <class R>
+__device__ __forceinline__ double join_r2(const Scene<R>& S, int i, int j, R r2) {
+  if constexpr (sizeof(R) == 8) {
+    return (double)r2;
+  } else {
+    double xi[3], xj[3];
+    abs_pos<R>(S, i, xi);
+    abs_pos<R>(S, j, xj);
+    double d[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < S.dim; q++) {
+      d[q] = xi[q] - xj[q];
+      if (S.per[q]) {
+        if (d[q] > 0.5 * S.L[q]) d[q] -= S.L[q]; else if (d[q] < -0.5 * S.L[q]) d[q] += S.L[q];
+      }
+    }
+    return (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+  }
+}
+
 template <class R, int DIM>
 __global__ void k_rl_join(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
@@ -74,11 +96,12 @@ __global__ void k_rl_join(BatchView<R> B) {
     S.tkey[i] = -1;
     S.bucket[i] = -1;
     if (S.tloc[i] != 2) continue;
-    R best = R(0);
+    double best = 0.0;
     int bk = -1, bo = 0x7fffffff;
-    for_each_neighbor<R, DIM>(S, i, [&](int j, R r2) {
+    for_each_neighbor<R, DIM>(S, i, [&](int j, R r2R) {
       if (S.matR[S.P.mt[j]].kind != KRIGID || S.tloc[j] == 1) return;
       int kj = S.P.body[j], oj = S.P.orig[j];
+      double r2 = join_r2<R>(S, i, j, r2R);
       if (bk < 0 || r2 < best || (r2 == best && (kj < bk || (kj == bk && oj < bo)))) {
         best = r2; bk = kj; bo = oj;
       }
@@ -224,7 +247,8 @@ __global__ void k_rl_slots_count(BatchView<R> B) {
   }
 }
 
-// 2: slot ranges (exclusive scan over bodies, one block per scene), K grows by the new bodies
+// 2: new slot ranges (exclusive scan over bodies, one block per scene) into bst2 (start) and
+// bst2 + Kcap (end); bcur becomes the fill cursor; K grows by the new bodies
 template <class R>
 __global__ void __launch_bounds__(1024) k_rl_slots_scan(BatchView<R> B) {
   __shared__ int wsum[32];
@@ -256,8 +280,8 @@ __global__ void __launch_bounds__(1024) k_rl_slots_scan(BatchView<R> B) {
       __syncthreads();
       int excl = carry + wsum[threadIdx.x >> 5] + x - v;
       if (k < Knew) {
-        S.bstart[k] = excl;
-        S.bend[k] = excl + v;
+        S.bst2[k] = excl;
+        S.bst2[S.Kcap + k] = excl + v;
         S.bcur[k] = excl;
       }
       __syncthreads();
@@ -269,8 +293,9 @@ __global__ void __launch_bounds__(1024) k_rl_slots_scan(BatchView<R> B) {
   }
 }
 
-// 3: unordered fill of the slot ranges, then 4: order each body's slots by input index (the
-// order the slots were first built in; the first slot is the unwrapping reference)
+// 3: fill.  A body whose membership did not change keeps its slot order, shifted to its new
+// range (offsets and slot forces move along); a changed or new body is filled unordered and
+// sorted in step 4.
 template <class R>
 __global__ void k_rl_slots_fill(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
@@ -279,48 +304,91 @@ __global__ void k_rl_slots_fill(BatchView<R> B) {
     const Scene<R>& S = *B.sc[s];
     if (!relabel_now(S)) continue;
     int i = g - __ldg(B.pfx_part + s);
-    if (S.matR[S.P.mt[i]].kind == KRIGID) S.perm[atomicAdd(&S.bcur[S.P.body[i]], 1)] = i;
-  }
-}
-
-template <class R>
-__global__ void k_rl_slots_order(BatchView<R> B) {
-  int total = __ldg(B.pfx_body + B.nsc);
-  int lane = threadIdx.x & 31;
-  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  for (int g = gw; g < total; g += nw) {
-    int s = find_scene(B.pfx_body, B.nsc, g);
-    const Scene<R>& S = *B.sc[s];
-    if (!relabel_now(S)) continue;
-    int k = g - __ldg(B.pfx_body + s);
-    if (k >= *S.K) continue;
-    int a = S.bstart[k], e = S.bend[k], cnt = e - a;
-    for (int t0 = 0; t0 < cnt; t0 += 32) {
-      int t = t0 + lane;
-      int v = t < cnt ? S.perm[a + t] : 0;
-      int ov = t < cnt ? S.P.orig[v] : 0x7fffffff;
-      int rank = 0;
-      for (int u0 = 0; u0 < cnt; u0 += 32) {
-        int w = (u0 + lane) < cnt ? S.P.orig[S.perm[a + u0 + lane]] : 0x7fffffff;
-        int lim = min(32, cnt - u0);
-        for (int q = 0; q < lim; q++) rank += (__shfl_sync(FULL, w, q) < ov);
+    if (S.matR[S.P.mt[i]].kind != KRIGID) continue;
+    int k = S.P.body[i];
+    if (S.bchg[k] == 0) {
+      int old = S.P.slot[i];
+      int sl = S.bst2[k] + (old - S.bstart[k]);
+      S.slot_part[sl] = i;
+      for (int q = 0; q < 3; q++) {
+        S.rb2[3 * sl + q] = S.rb[3 * old + q];
+        S.fr2[3 * sl + q] = S.fr[3 * old + q];
       }
-      if (t < cnt) {
-        int sl = a + rank;
-        int old = S.P.slot[v];
-        // offsets of particles that were rigid before; a particle that was fluid in this
-        // step carries no rigid force (its offset comes from the new mass quantities)
-        for (int q = 0; q < 3; q++) {
-          S.rb2[3 * sl + q] = old >= 0 ? S.rb[3 * old + q] : 0.0;
-          S.fr2[3 * sl + q] = old >= 0 ? S.fr[3 * old + q] : R(0);
-        }
-        S.slot_part[sl] = v;
-      }
+    } else {
+      S.perm[atomicAdd(&S.bcur[k], 1)] = i;
     }
   }
 }
 
-// 5: adopt the new slots, offsets and slot forces
+// 4: every changed body's slots in input-index order (the order the slots were first built
+// in; the first slot is the unwrapping reference): one block per body, bitonic sort of
+// (input index, particle) in shared memory up to kSortCap slots, a block-wide rank count
+// above that
+constexpr int kSortCap = 8192;
+
+template <class R>
+__device__ __forceinline__ void rl_place(const Scene<R>& S, int sl, int v) {
+  int old = S.P.slot[v];
+  S.slot_part[sl] = v;
+  for (int q = 0; q < 3; q++) {
+    // offsets of particles that were rigid before; a particle that was fluid in this
+    // step carries no rigid force (its offset comes from the new mass quantities)
+    S.rb2[3 * sl + q] = old >= 0 ? S.rb[3 * old + q] : 0.0;
+    S.fr2[3 * sl + q] = old >= 0 ? S.fr[3 * old + q] : R(0);
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(512) k_rl_slots_order(BatchView<R> B) {
+  extern __shared__ int sm_sort[];
+  int* key = sm_sort;
+  int* val = sm_sort + kSortCap;
+  int total = __ldg(B.pfx_body + B.nsc);
+  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+    int s = find_scene(B.pfx_body, B.nsc, g);
+    const Scene<R>& S = *B.sc[s];
+    if (!relabel_now(S)) continue;
+    int k = g - __ldg(B.pfx_body + s);
+    if (k >= *S.K || S.bchg[k] == 0) continue;
+    int a = S.bst2[k], cnt = S.bst2[S.Kcap + k] - a;
+    if (cnt <= 0) continue;
+    if (cnt <= kSortCap) {
+      int p2 = 1;
+      while (p2 < cnt) p2 <<= 1;
+      for (int t = threadIdx.x; t < p2; t += blockDim.x) {
+        int v = t < cnt ? S.perm[a + t] : -1;
+        key[t] = t < cnt ? S.P.orig[v] : 0x7fffffff;
+        val[t] = v;
+      }
+      __syncthreads();
+      for (int w = 2; w <= p2; w <<= 1)
+        for (int j = w >> 1; j > 0; j >>= 1) {
+          for (int t = threadIdx.x; t < p2; t += blockDim.x) {
+            int u = t ^ j;
+            if (u > t) {
+              bool up = (t & w) == 0;
+              if ((key[t] > key[u]) == up) {
+                int tk = key[t]; key[t] = key[u]; key[u] = tk;
+                int tv = val[t]; val[t] = val[u]; val[u] = tv;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) rl_place(S, a + t, val[t]);
+      __syncthreads();
+    } else {
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        int v = S.perm[a + t], ov = S.P.orig[v], rank = 0;
+        for (int u = 0; u < cnt; u++) rank += S.P.orig[S.perm[a + u]] < ov;
+        rl_place(S, a + rank, v);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// 5: adopt the new slots, offsets, slot forces and slot ranges
 template <class R>
 __global__ void k_rl_slots_adopt(BatchView<R> B) {
   int total = __ldg(B.pfx_slot + B.nsc);
@@ -330,7 +398,11 @@ __global__ void k_rl_slots_adopt(BatchView<R> B) {
     if (!relabel_now(S)) continue;
     int sl = g - __ldg(B.pfx_slot + s);
     int K = *S.K;
-    if (K == 0 || sl >= S.bend[K - 1]) continue;
+    if (sl < K) {
+      S.bstart[sl] = S.bst2[sl];
+      S.bend[sl] = S.bst2[S.Kcap + sl];
+    }
+    if (K == 0 || sl >= S.bst2[S.Kcap + K - 1]) continue;
     int i = S.slot_part[sl];
     S.P.slot[i] = sl;
     for (int q = 0; q < 3; q++) {

@@ -562,3 +562,106 @@ def batch_mix(count=256, seed=2103, n_lo=1e4, n_hi=5e5, max_bodies=50, precision
         out.append((sc, dict(index=q, dim=dim, bodies=nb, dx=dx, target=n_t,
                              n=int(len(sc["particles"]["mass"])))))
     return out
+
+
+# --------------------------------------------------------------------------- powder bed
+
+def powder_bed(dx=0.005, size=(1.0, 0.5, 0.5), n_grains=2000, r_median=0.02, r_sigma=0.3,
+               r_clip=(0.01, 0.05), bed_frac=0.8, seed=2103, T0=300.0, T_melt=1700.0, mushy=20.0,
+               c_metal=1.0, nu=1e-3, Q0=1e10, src_radius=0.05, src_speed=0.5, src_depth=None,
+               g=-9.81, max_tries=4, precision=32):
+    """Powder bed with melting grains (the shape of Sec. 4.4 in 3D).
+
+    Box ``size`` (periodic in x and y) filled on a dx lattice: a three-layer wall slab
+    below z = 0 held at T0 (Dirichlet), an adiabatic three-layer lid above the box, metal
+    grains (rigid, density 1000): ``n_grains`` lognormal radii (median ``r_median``, log-sigma
+    ``r_sigma``, clipped to ``r_clip``) placed largest first by random sequential addition
+    (surface gap dx) in the lower ``bed_frac`` of the box; a grain that finds no room in
+    ``max_tries`` batches of 256 candidate centres is left out,
+    and gas (fluid, density 1) everywhere else.  Solid metal melts into liquid metal
+    (fluid, density 1000) at T_melt with latent heat L = 0.25 c_p (T_melt - T0) over a mushy
+    interval of width ``mushy``, and back.  Property ratios of the paper's example: metal
+    c_p = 1, kappa = 10; gas c_p = 0.01, kappa = 0.1.  Both fluids share p0 = rho0 c^2
+    (c_gas = c_metal sqrt(1000)).  A Gaussian surface source of power density Q0, radius
+    ``src_radius`` moves along x at ``src_speed`` over the top of the bed, heating metal
+    within ``src_depth`` (default 10 dx) below the bed top.
+    """
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = (int(round(s / dx)) for s in size)
+    Lx, Ly, Lz = nx * dx, ny * dx, nz * dx
+    zb = bed_frac * Lz
+    # radii drawn up front, placed largest first by random sequential addition (surface gap
+    # dx, periodic in x and y); each grain gets ``tries`` batches of candidate centres
+    radii_all = np.clip(r_median * np.exp(r_sigma * rng.normal(size=n_grains)), *r_clip)
+    radii_all = np.sort(np.maximum(radii_all, 1.5 * dx))[::-1]
+    C = np.zeros((0, 3))
+    Rr = np.zeros(0)
+    tries = 0
+    for r in radii_all:
+        if zb - 2 * r - dx <= 0:
+            continue
+        for _ in range(max_tries):
+            tries += 1
+            cand = np.column_stack([rng.uniform(0, Lx, 256), rng.uniform(0, Ly, 256),
+                                    rng.uniform(r + dx, zb - r, 256)])
+            if len(C):
+                d = cand[:, None, :] - C[None, :, :]
+                d[..., 0] -= Lx * np.round(d[..., 0] / Lx)
+                d[..., 1] -= Ly * np.round(d[..., 1] / Ly)
+                ok = np.all(np.einsum("ijk,ijk->ij", d, d) >= (r + Rr[None, :] + dx) ** 2, axis=1)
+            else:
+                ok = np.ones(256, dtype=bool)
+            if ok.any():
+                C = np.vstack([C, cand[int(np.argmax(ok))]])
+                Rr = np.append(Rr, r)
+                break
+    centers, radii = list(C), list(Rr)
+    sites = lattice([0.0, 0.0, 0.0], [nx, ny, nz], dx)
+    owner = np.full(len(sites), -1, dtype=np.int64)
+    for k, (c, r) in enumerate(zip(centers, radii)):
+        lo = np.floor((c - r) / dx).astype(int) - 1
+        hi = np.ceil((c + r) / dx).astype(int) + 1
+        ii, jj, kk = np.meshgrid(np.arange(lo[0], hi[0] + 1), np.arange(lo[1], hi[1] + 1),
+                                 np.arange(max(lo[2], 0), min(hi[2], nz - 1) + 1), indexing="ij")
+        ii, jj, kk = ii.ravel() % nx, jj.ravel() % ny, kk.ravel()
+        lin = ii + nx * (jj + ny * kk)
+        d = sites[lin] - c
+        d[:, 0] -= Lx * np.round(d[:, 0] / Lx)
+        d[:, 1] -= Ly * np.round(d[:, 1] / Ly)
+        inside = np.sum(d * d, axis=1) <= r * r
+        owner[lin[inside & (owner[lin] < 0)]] = k
+    rho_m, rho_g = 1000.0, 1.0
+    c_gas = c_metal * math.sqrt(rho_m / rho_g)
+    L = 0.25 * 1.0 * (T_melt - T0)
+    mats = [material(FLUID, rho_g, c=c_gas, eta=rho_g * nu, cp=0.01, kappa=0.1),
+            material(WALL, rho_g, cp=1.0, kappa=10.0),
+            material(RIGID, rho_m, cp=1.0, kappa=10.0, T_transition=T_melt, transitions_to=3,
+                     latent_heat=L, mushy_width=mushy),
+            material(FLUID, rho_m, c=c_metal, eta=rho_m * nu, cp=1.0, kappa=10.0, T_transition=T_melt,
+                     transitions_to=2, latent_heat=L, mushy_width=mushy)]
+    b = _Builder(3)
+    b.add(sites[owner < 0], 0, rho_g * dx ** 3, rho_g, T0)
+    order = np.argsort(owner[owner >= 0], kind="stable")
+    rig = sites[owner >= 0][order]
+    rid = owner[owner >= 0][order]
+    used = np.unique(rid)
+    remap = np.full(len(centers), -1, dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    for _ in range(len(used)):
+        b.add_body()
+    if len(rig):
+        b.add(rig, 2, rho_m * dx ** 3, rho_m, T0, body=remap[rid].astype(np.int32))
+    # substrate slab (Dirichlet T0) and adiabatic lid, three layers each
+    slab = lattice([0.0, 0.0, -3 * dx], [nx, ny, 3], dx)
+    b.add(slab, 1, rho_g * dx ** 3, rho_g, T0, wall_T=T0)
+    lid = lattice([0.0, 0.0, Lz], [nx, ny, 3], dx)
+    b.add(lid, 1, rho_g * dx ** 3, rho_g, T0, wall_T=NAN)
+    ztop = float(max((c[2] + r for c, r in zip(centers, radii)), default=zb))
+    p = default_params(3, dx, [0.0, 0.0, -3 * dx], [Lx, Ly, Lz + 3 * dx], periodic=[1, 1, 0],
+                       gravity=[0.0, 0.0, g], dt_mode=1, precision=precision,
+                       src_power=Q0, src_radius=src_radius, src_speed=[src_speed, 0.0, 0.0],
+                       src_origin=[0.2 * Lx, 0.5 * Ly, 0.0], src_depth=10 * dx if src_depth is None else src_depth,
+                       src_ztop=ztop, body_capacity=len(used) + 4096)
+    sc = b.finish(p, mats)
+    sc["info"] = dict(grains=len(used), grains_requested=n_grains, rigid=int(len(rig)), tries=tries)
+    return sc

@@ -29,7 +29,7 @@ EXPORTS = ["sph_create_scene", "sph_step", "sph_step_async", "sph_read_fields", 
            "sph_batch_release", "sph_batch_info", "sph_batch_destroy", "sph_profile",
            "sph_profile_stage_name", "sph_density_static", "sph_set_launch", "sph_time_steps",
            "sph_batch_set_launch", "sph_batch_time_steps", "sph_batch_job_state"]
-PROFILE_STAGES = 20
+PROFILE_STAGES = 21
 
 
 class SphError(RuntimeError):
