@@ -68,6 +68,11 @@ struct Scene {
   R *prs, *dT;         // pressure, rate (not permuted: recomputed every evaluation)
   R *vex, *vey, *vez;  // extrapolated velocity of wall and rigid particles
   R* vol;              // particle volume m / rho of the current evaluation
+  // FP32 scenes: what a pair sweep gathers from a neighbour, packed per particle after the
+  // density summation (three 16-byte loads per neighbour instead of twelve scalar ones):
+  // pa = (x, y, z, rho), pb = (u or extrapolated v_w, p or p_w), pc = (T, V, material |
+  // kind << 16, body)
+  float4 *pa, *pb, *pc;
   int* nbl;            // neighbour lists: entry k of particle i at nbl[k * n + i] = j << 5 | cell code
   int* nbc;            // neighbour count of each particle (may exceed maxnb: then cells are scanned)
   R *xr, *yr, *zr;     // positions at the last list rebuild (same frame as the bank)
@@ -103,7 +108,7 @@ struct Scene {
   int* status;         // [0] non-finite flag [1] relabel count [2] capacity error [3] table error
                        // [4] rebuild in this step [5] steps since rebuild [6] rebuild count
                        // [7] solidifiers without a rigid neighbour [8] new bodies this step
-                       // [9] relabelled particles so far
+                       // [9] relabelled particles so far [10] kinds changed since the lists were built
   int* pfx1;           // prefix tables of this scene alone (6 x 2 ints)
   Scene<R>** self;     // device array holding the address of this descriptor
   unsigned long long* pairs;  // [0] force-sweep pairs of the last evaluation

@@ -353,7 +353,7 @@ class Engine {
 
   static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans) {
     size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 9 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
-                 (DIM == 3 ? 192 : 64) * sizeof(int);
+                 (DIM == 3 ? 192 : 64) * sizeof(int) + (sizeof(R) == 4 ? 3 * sizeof(float4) : 0);
     size_t cells = (size_t)(ncells + 1) * 4 * sizeof(int) + (size_t)(ncells / 1024 + 2) * sizeof(int);
     size_t bodies = (size_t)kcap * (60 * sizeof(double) + 3 * sizeof(int));
     size_t slots = (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R) + sizeof(int));
@@ -542,6 +542,8 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   }
   R** rx[] = {&S.prs, &S.dT, &S.vex, &S.vey, &S.vez, &S.vol};
   for (R** f : rx) SPH_TRY(A(f, (size_t)n));
+  if (sizeof(R) == 4)
+    for (float4** f : {&S.pa, &S.pb, &S.pc}) SPH_TRY(A(f, (size_t)n));
   S.maxnb = list_capacity(DIM, (S.rc + S.skin) / S.dx);
   SPH_TRY(A(&S.nbl, (size_t)S.maxnb * n));
   SPH_TRY(A(&S.nbc, (size_t)n));

@@ -325,8 +325,11 @@ __global__ void k_decide(BatchView<R> B) {
   Scene<R>& S = *B.sc[s];
   R d2 = sizeof(R) == 8 ? (R)__longlong_as_double((long long)*S.disp) : (R)__int_as_float((int)*S.disp);
   int since = S.status[5] + 1;
-  bool rb = S.skin <= 0.0 || d2 > S.half_skin2 || (S.rebin_interval > 1 && since >= S.rebin_interval);
+  // particles that changed phase since the last build change which lists they belong to
+  bool rb = S.skin <= 0.0 || d2 > S.half_skin2 || (S.rebin_interval > 1 && since >= S.rebin_interval) ||
+            S.status[10] != 0;
   S.status[4] = rb ? 1 : 0;
+  if (rb) S.status[10] = 0;
   S.status[5] = rb ? 0 : since;
   if (rb) S.status[6] += 1;
   *S.disp = 0ull;

@@ -213,6 +213,7 @@ __global__ void k_rl_apply(BatchView<R> B) {
       S.P.body[i] = -1;
       S.P.slot[i] = -1;
       atomicAdd(&S.status[9], 1);
+      S.status[10] = 1;
     } else if (f == 2) {
       int k = S.tkey[i];
       if (k < 0) k = S.tkey[uf_find(S.bucket, i)];
@@ -221,6 +222,7 @@ __global__ void k_rl_apply(BatchView<R> B) {
       S.P.body[i] = k;
       S.P.ax[i] = R(0); S.P.ay[i] = R(0); S.P.az[i] = R(0);
       atomicAdd(&S.status[9], 1);
+      S.status[10] = 1;
     }
   }
 }

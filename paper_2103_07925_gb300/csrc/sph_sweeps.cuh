@@ -3,7 +3,8 @@
 //  k_search   one warp per target group: cell-list candidate tests (staged in shared
 //             memory), the neighbour list of every particle (index and cell-offset code
 //             per entry, layout list[k * n + i] so that a warp of consecutive targets
-//             reads one line per k), and the density summation + EOS of fluid targets
+//             reads one line per k; a wall particle lists its fluid neighbours only, the
+//             only ones it reads), and the density summation + EOS of fluid targets
 //             (Eq. densum, Eq. eos).
 //  k_extrap   one thread per wall / rigid target over its list: extrapolation of pressure
 //             and velocity from the fluid (Adami et al. 2012, cited in Sec. 3.3.4).
@@ -33,11 +34,23 @@ __device__ __forceinline__ void warp_add(int s, unsigned long long v, unsigned l
   }
 }
 
+// packed neighbour state of particle i (FP32 scenes), written where its density is final
+template <class R>
+__device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p, R vol) {
+  if constexpr (sizeof(R) == 4) {
+    int mt = S.P.mt[i];
+    S.pa[i] = make_float4(S.P.px[i], S.P.py[i], S.P.pz[i], rho);
+    S.pb[i] = make_float4(S.P.vx[i], S.P.vy[i], S.P.vz[i], p);
+    S.pc[i] = make_float4(S.P.T[i], vol, __int_as_float(mt | (S.matR[mt].kind << 16)), __int_as_float(S.P.body[i]));
+  }
+}
+
 // ---------------------------------------------------------------- search + density
 template <class R, int DIM>
 struct SearchPol {
   R *sx, *sy, *sz;
-  bool active, fluid;
+  int* sk;             // kind of every staged candidate
+  bool active, fluid, wall;
   int idx, tx, n, maxnb, cnt;
   int cox, cdy, cdz;
   int* list;
@@ -46,8 +59,10 @@ struct SearchPol {
   unsigned long long hits;
   __device__ void stage(const Scene<R>& S, int j, int lane) {
     sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
+    sk[lane] = S.matR[S.P.mt[j]].kind;
   }
-  __device__ bool accept(int) const { return true; }
+  // a wall particle only ever reads its fluid neighbours (extrapolation of Sec. 3.3.4)
+  __device__ bool accept(int k) const { return !wall || sk[k] == KFLUID; }
   __device__ void pair(const Scene<R>& S, int, int j, R, R, R, R r2) {
     int code = (cox - tx + 1) + 3 * (cdy + 1) + 9 * (cdz + 1);
     if (cnt < maxnb) list[(size_t)cnt * n + idx] = (j << 5) | code;
@@ -59,9 +74,11 @@ struct SearchPol {
 template <class R, int DIM>
 __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
   __shared__ R sm[4][3][32];
+  __shared__ int smk[4][32];
   int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   SearchPol<R, DIM> pol;
   pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
+  pol.sk = smk[wib];
   int total = __ldg(B.pfx_grp + B.nsc);
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int g = gw; g < total; g += nw) {
@@ -78,7 +95,9 @@ __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
       pol.active = valid;
       if (!__any_sync(FULL, valid)) continue;
       pol.idx = valid ? i : -1;
-      pol.fluid = valid && S.matR[S.P.mt[i]].kind == KFLUID;
+      int tkind = valid ? S.matR[S.P.mt[i]].kind : KFLUID;
+      pol.fluid = valid && tkind == KFLUID;
+      pol.wall = tkind == KWALL;
       pol.tx = 0;
       if (valid) {
         target_pos(S, i, G.cx0, pol.tp);
@@ -90,14 +109,17 @@ __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
       traverse<R, DIM>(S, G, pol, lane, S.rl2R);
       if (valid) {
         S.nbc[i] = pol.cnt;
-        R rho = S.P.rho[i];
+        R rho = S.P.rho[i], p = R(0);
         if (pol.fluid) {
           const MatR<R>& A = S.matR[S.P.mt[i]];
           rho = S.P.m[i] * (S.w0 + S.sig_w * pol.acc);
+          p = A.c2 * (rho - A.rho0);
           S.P.rho[i] = rho;
-          S.prs[i] = A.c2 * (rho - A.rho0);
+          S.prs[i] = p;
         }
-        S.vol[i] = qdiv<R>(S.P.m[i], rho);
+        R vol = qdiv<R>(S.P.m[i], rho);
+        S.vol[i] = vol;
+        write_pack<R>(S, i, rho, p, vol);
       }
     }
   }
@@ -124,6 +146,15 @@ __device__ __forceinline__ void list_delta(const Scene<R>& S, const R* ti, int j
     d[1] = (ti[1] - S.P.py[j]) - (R)oy * S.ellR[1];
     d[2] = DIM == 3 ? (ti[2] - S.P.pz[j]) - (R)oz * S.ellR[2] : R(0);
   }
+}
+
+// the same offset from a packed FP32 neighbour record
+template <int DIM>
+__device__ __forceinline__ void pack_delta(const Scene<float>& S, const float* ti, float4 a, int code, float* d) {
+  int ox = code % 3 - 1, oy = (code / 3) % 3 - 1, oz = code / 9 - 1;
+  d[0] = (ti[0] - a.x) - (float)ox * S.ellR[0];
+  d[1] = (ti[1] - a.y) - (float)oy * S.ellR[1];
+  d[2] = DIM == 3 ? (ti[2] - a.z) - (float)oz * S.ellR[2] : 0.f;
 }
 
 // scan of the 3^d cells around target i (targets whose list overflowed); calls
@@ -188,7 +219,9 @@ __global__ void __launch_bounds__(256) k_density(BatchView<R> B) {
       S.P.rho[i] = rho;
       S.prs[i] = A.c2 * (rho - A.rho0);
     }
-    S.vol[i] = qdiv<R>(S.P.m[i], rho);
+    R vol = qdiv<R>(S.P.m[i], rho);
+    S.vol[i] = vol;
+    write_pack<R>(S, i, rho, A.kind == KFLUID ? S.prs[i] : R(0), vol);
   }
 }
 
@@ -205,17 +238,34 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
     R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
     R S0 = R(0), P0 = R(0), Rv[3] = {R(0), R(0), R(0)}, U[3] = {R(0), R(0), R(0)};
     auto visit = [&](int j, int code) {
-      if (S.matR[S.P.mt[j]].kind != KFLUID) return;
-      R d[3];
-      list_delta<R, DIM>(S, ti, j, code, d);
-      R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
-      if (!(r2 < S.rc2R)) return;
-      R W = quintic_w<R>(sqrt(r2) * S.inv_h);
-      S0 += W;
-      P0 += S.prs[j] * W;
-      R rw = S.P.rho[j] * W;
-      Rv[0] += rw * d[0]; Rv[1] += rw * d[1]; Rv[2] += rw * d[2];
-      U[0] += S.P.vx[j] * W; U[1] += S.P.vy[j] * W; U[2] += S.P.vz[j] * W;
+      if constexpr (sizeof(R) == 4) {
+        float4 c = S.pc[j];
+        if ((__float_as_int(c.z) >> 16) != KFLUID) return;
+        float4 a = S.pa[j];
+        R d[3];
+        pack_delta<DIM>(S, ti, a, code, d);
+        R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+        if (!(r2 < S.rc2R)) return;
+        float4 b = S.pb[j];
+        R W = quintic_w<R>(sqrt(r2) * S.inv_h);
+        S0 += W;
+        P0 += b.w * W;
+        R rw = a.w * W;
+        Rv[0] += rw * d[0]; Rv[1] += rw * d[1]; Rv[2] += rw * d[2];
+        U[0] += b.x * W; U[1] += b.y * W; U[2] += b.z * W;
+      } else {
+        if (S.matR[S.P.mt[j]].kind != KFLUID) return;
+        R d[3];
+        list_delta<R, DIM>(S, ti, j, code, d);
+        R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+        if (!(r2 < S.rc2R)) return;
+        R W = quintic_w<R>(sqrt(r2) * S.inv_h);
+        S0 += W;
+        P0 += S.prs[j] * W;
+        R rw = S.P.rho[j] * W;
+        Rv[0] += rw * d[0]; Rv[1] += rw * d[1]; Rv[2] += rw * d[2];
+        U[0] += S.P.vx[j] * W; U[1] += S.P.vy[j] * W; U[2] += S.P.vz[j] * W;
+      }
     };
     int cnt = S.nbc[i];
     if (cnt <= S.maxnb) {
@@ -243,6 +293,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
       S.prs[i] = R(0);
       S.vex[i] = uw[0]; S.vey[i] = uw[1]; S.vez[i] = uw[2];
     }
+    if constexpr (sizeof(R) == 4) S.pb[i] = make_float4(S.vex[i], S.vey[i], S.vez[i], S.prs[i]);
   }
 }
 
@@ -314,8 +365,70 @@ __device__ __forceinline__ void force_pair(const Scene<R>& S, const Target<R>& t
   }
 }
 
+// force_pair on packed FP32 neighbour records (same arithmetic in the same order)
+template <int DIM>
+__device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const Target<float>& t, int j, const float* d,
+                                                  float r2, float4 a, float4 b, float4 c, float* acc, float& heat) {
+  int mk = __float_as_int(c.z);
+  int bk = mk >> 16;
+  const MatR<float>& Bm = S.matR[mk & 0xffff];
+  float inv_r = rsqrt_<float>(r2);
+  float r = r2 * inv_r;
+  float dW = S.sig_dw * quintic_dw<float>(r * S.inv_h);
+  float ex = d[0] * inv_r, ey = d[1] * inv_r, ez = d[2] * inv_r;
+  float Vj = c.y;
+  if (S.any_heat) {
+    float Tb = c.x;
+    if (!(bk == KWALL && isnan(Tb))) {
+      float kb = bk == KWALL ? t.kap : Bm.kappa;
+      float ks = t.kap + kb;
+      float kab = ks > 0.f ? qdiv<float>(4.f * t.kap * kb, ks) : 0.f;
+      heat += Vj * kab * (t.T - Tb) * inv_r * dW;
+    }
+  }
+  if (t.kind == KFLUID) {
+    float rhoj, pj = b.w, etaj;
+    if (bk == KFLUID) {
+      rhoj = a.w;
+      etaj = Bm.eta;
+    } else {  // wall / rigid: inverse EOS of fluid i for the extrapolated pressure
+      rhoj = t.M->rho0 * (pj * t.M->inv_p0 + 1.f);
+      etaj = t.eta;
+    }
+    float pt = qdiv<float>(rhoj * t.p + t.rho * pj, t.rho + rhoj);
+    float es = t.eta + etaj;
+    float et = es > 0.f ? qdiv<float>(2.f * t.eta * etaj, es) : 0.f;
+    float coef = (t.V2 + Vj * Vj) * dW;
+    float vis = et * inv_r;
+    acc[0] += coef * (-pt * ex + vis * (t.u[0] - b.x));
+    acc[1] += coef * (-pt * ey + vis * (t.u[1] - b.y));
+    acc[2] += coef * (-pt * ez + vis * (t.u[2] - b.z));
+  } else if (bk == KFLUID) {  // rigid target: -m_j a_jr seen from fluid particle j
+    float rhoj = a.w, pj = b.w;
+    float rs = Bm.rho0 * (t.p * Bm.inv_p0 + 1.f);
+    float pt = qdiv<float>(rs * pj + rhoj * t.p, rhoj + rs);
+    float coef = (Vj * Vj + t.V2) * dW;
+    float vis = Bm.eta * inv_r;
+    acc[0] -= coef * (pt * ex + vis * (b.x - t.ve[0]));
+    acc[1] -= coef * (pt * ey + vis * (b.y - t.ve[1]));
+    acc[2] -= coef * (pt * ez + vis * (b.z - t.ve[2]));
+  } else if (bk == KWALL || __float_as_int(c.w) != t.body) {
+    if (r < S.dxR) {  // Eq. contactforce with tension cut-off (particle velocities, not v_w)
+      float ev = ex * (t.u[0] - S.P.vx[j]) + ey * (t.u[1] - S.P.vy[j]) + ez * (t.u[2] - S.P.vz[j]);
+      float fn = S.kcR * (r - S.dxR) + S.dcR * ev;
+      float mn = fn < 0.f ? fn : 0.f;
+      acc[0] -= mn * ex; acc[1] -= mn * ey; acc[2] -= mn * ez;
+    }
+  }
+}
+
+// resident blocks per SM the force sweep is compiled for (register budget)
+#ifndef SPH_FORCE_MIN_BLOCKS
+#define SPH_FORCE_MIN_BLOCKS 4
+#endif
+
 template <class R, int DIM>
-__global__ void __launch_bounds__(256) k_force(BatchView<R> B) {
+__global__ void __launch_bounds__(256, SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
   int nthr = gridDim.x * blockDim.x;
   // uniform trip count so that the warp-wide pair counter sees every lane
@@ -344,12 +457,24 @@ __global__ void __launch_bounds__(256) k_force(BatchView<R> B) {
       R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
       R acc[3] = {R(0), R(0), R(0)}, heat = R(0);
       auto visit = [&](int j, int code) {
-        R d[3];
-        list_delta<R, DIM>(S, ti, j, code, d);
-        R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
-        if (r2 < S.rc2R) {
-          force_pair<R, DIM>(S, t, j, d, r2, acc, heat);
-          npairs++;
+        if constexpr (sizeof(R) == 4) {
+          float4 a = S.pa[j];
+          R d[3];
+          pack_delta<DIM>(S, ti, a, code, d);
+          R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+          if (r2 < S.rc2R) {
+            float4 b = S.pb[j], c = S.pc[j];
+            force_pair_packed<DIM>(S, t, j, d, r2, a, b, c, acc, heat);
+            npairs++;
+          }
+        } else {
+          R d[3];
+          list_delta<R, DIM>(S, ti, j, code, d);
+          R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+          if (r2 < S.rc2R) {
+            force_pair<R, DIM>(S, t, j, d, r2, acc, heat);
+            npairs++;
+          }
         }
       };
       int cnt = S.nbc[i];
