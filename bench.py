@@ -30,7 +30,7 @@ BYTES_PER_TARGET = 72   # algorithmic HBM bytes per target particle of the force
 # DRAM bytes (read + write) of one k_force launch on the default workload, from
 # `ncu --set full` of this kernel version (profiles/ncu_k_force_tank3d_fp32.md); None once
 # the kernel changes and until it is captured again
-K_FORCE_TRAFFIC = 851.8e6
+K_FORCE_TRAFFIC = None
 FP32_LANES_PER_SM = 128
 N_SM = 152
 

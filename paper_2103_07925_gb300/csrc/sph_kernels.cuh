@@ -280,6 +280,9 @@ __global__ void __launch_bounds__(256) k_kick_drift(BatchView<R> B) {
       S.P.ay[i] = (R)(S.ba[3 * k + 1] + t1[1] + t3[1]);
       S.P.az[i] = (R)(S.ba[3 * k + 2] + t1[2] + t3[2]);
     }
+    // packed position for the density sweep of a step without rebuild (FP32 scenes)
+    if constexpr (sizeof(R) == 4)
+      if (kind != KWALL) S.pa[i] = make_float4(S.P.px[i], S.P.py[i], S.P.pz[i], S.P.rho[i]);
     // displacement since the last list rebuild (skin criterion)
     R d2 = R(0);
     if (kind != KWALL && S.skin > 0.0) {

@@ -36,10 +36,13 @@ __device__ __forceinline__ void warp_add(int s, unsigned long long v, unsigned l
 
 // packed neighbour state of particle i (FP32 scenes), written where its density is final
 template <class R>
-__device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p, R vol) {
+__device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p, R vol, bool with_pos = true) {
   if constexpr (sizeof(R) == 4) {
     int mt = S.P.mt[i];
-    S.pa[i] = make_float4(S.P.px[i], S.P.py[i], S.P.pz[i], rho);
+    if (with_pos)
+      S.pa[i] = make_float4(S.P.px[i], S.P.py[i], S.P.pz[i], rho);
+    else
+      S.pa[i].w = rho;
     S.pb[i] = make_float4(S.P.vx[i], S.P.vy[i], S.P.vz[i], p);
     S.pc[i] = make_float4(S.P.T[i], vol, __int_as_float(mt | (S.matR[mt].kind << 16)), __int_as_float(S.P.body[i]));
   }
@@ -201,14 +204,26 @@ __global__ void __launch_bounds__(256) k_density(BatchView<R> B) {
       R acc = R(0);
       auto visit = [&](int j, int code) {
         R d[3];
-        list_delta<R, DIM>(S, ti, j, code, d);
+        if constexpr (sizeof(R) == 4)
+          pack_delta<DIM>(S, ti, S.pa[j], code, d);  // positions packed by the drift
+        else
+          list_delta<R, DIM>(S, ti, j, code, d);
         R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
         if (r2 < S.rc2R) acc += quintic_w<R>(sqrt(r2) * S.inv_h);
       };
       int cnt = S.nbc[i];
       if (cnt <= S.maxnb) {
         const int* L = S.nbl + i;
-        for (int k = 0; k < cnt; k++) {
+        int k = 0;
+        if constexpr (sizeof(R) == 4) {
+          int e = k < cnt ? __ldg(L + (size_t)k * S.n) : 0;
+          for (; k < cnt; k++) {
+            int en = k + 1 < cnt ? __ldg(L + (size_t)(k + 1) * S.n) : 0;
+            visit(e >> 5, e & 31);
+            e = en;
+          }
+        }
+        for (; k < cnt; k++) {
           int e = __ldg(L + (size_t)k * S.n);
           visit(e >> 5, e & 31);
         }
@@ -221,7 +236,8 @@ __global__ void __launch_bounds__(256) k_density(BatchView<R> B) {
     }
     R vol = qdiv<R>(S.P.m[i], rho);
     S.vol[i] = vol;
-    write_pack<R>(S, i, rho, A.kind == KFLUID ? S.prs[i] : R(0), vol);
+    // the positions of the packed records are read by this sweep: write only the density
+    write_pack<R>(S, i, rho, A.kind == KFLUID ? S.prs[i] : R(0), vol, false);
   }
 }
 
@@ -270,7 +286,31 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
     int cnt = S.nbc[i];
     if (cnt <= S.maxnb) {
       const int* L = S.nbl + i;
-      for (int k = 0; k < cnt; k++) {
+      int k = 0;
+      if constexpr (sizeof(R) == 4) {
+        // software pipeline as in the force sweep: next entry and all records in flight
+        int e = k < cnt ? __ldg(L + (size_t)k * S.n) : 0;
+        for (; k < cnt; k++) {
+          int en = k + 1 < cnt ? __ldg(L + (size_t)(k + 1) * S.n) : 0;
+          int j = e >> 5;
+          float4 c = S.pc[j], a = S.pa[j], b = S.pb[j];
+          if ((__float_as_int(c.z) >> 16) == KFLUID) {
+            R d[3];
+            pack_delta<DIM>(S, ti, a, e & 31, d);
+            R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+            if (r2 < S.rc2R) {
+              R W = quintic_w<R>(sqrt(r2) * S.inv_h);
+              S0 += W;
+              P0 += b.w * W;
+              R rw = a.w * W;
+              Rv[0] += rw * d[0]; Rv[1] += rw * d[1]; Rv[2] += rw * d[2];
+              U[0] += b.x * W; U[1] += b.y * W; U[2] += b.z * W;
+            }
+          }
+          e = en;
+        }
+      }
+      for (; k < cnt; k++) {
         int e = __ldg(L + (size_t)k * S.n);
         visit(e >> 5, e & 31);
       }
@@ -480,7 +520,26 @@ __global__ void __launch_bounds__(256, SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R
       int cnt = S.nbc[i];
       if (cnt <= S.maxnb) {
         const int* L = S.nbl + i;
-        for (int k = 0; k < cnt; k++) {
+        int k = 0;
+        if constexpr (sizeof(R) == 4) {
+          // software pipeline: the next list entry is loaded while this pair is evaluated,
+          // and the three records of a neighbour are loaded together (one latency per entry)
+          int e = k < cnt ? __ldg(L + (size_t)k * S.n) : 0;
+          for (; k < cnt; k++) {
+            int en = k + 1 < cnt ? __ldg(L + (size_t)(k + 1) * S.n) : 0;
+            int j = e >> 5;
+            float4 a = S.pa[j], b = S.pb[j], c = S.pc[j];
+            float d[3];
+            pack_delta<DIM>(S, ti, a, e & 31, d);
+            float r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+            if (r2 < S.rc2R) {
+              force_pair_packed<DIM>(S, t, j, d, r2, a, b, c, acc, heat);
+              npairs++;
+            }
+            e = en;
+          }
+        }
+        for (; k < cnt; k++) {
           int e = __ldg(L + (size_t)k * S.n);
           visit(e >> 5, e & 31);
         }
