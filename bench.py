@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--scenes", type=int, default=256, help="batch: number of scenes")
     ap.add_argument("--jobs", type=int, default=32, help="serve: number of jobs")
     ap.add_argument("--job-steps", type=int, default=1000, help="serve: steps per job")
-    ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (tank/powder: use --key-order and --skin; batch: default layout)")
     return ap.parse_args()
 
 
@@ -315,34 +316,14 @@ def main():
     import numpy as np
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2103_07925_gb300.replicas import from_env
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def allmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def allsum(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    rep, local = from_env("nccl")  # one replica per GPU; no collective on the data path
+    world, rank, dist = rep.world, rep.rank, rep.dist
+    barrier, allmax, allsum = rep.barrier, rep.max, rep.sum
 
     if args.workload == "batch":
         bench_batch(args, rank, world, allmax, allsum, barrier)
@@ -355,8 +336,21 @@ def main():
     dx = args.dx or DEFAULT_DX[args.workload]
     sc = workload(dx, args.workload)
     stream = torch.cuda.Stream()
-    skin = args.skin * sc["params"]["h"]
-    g = Scene(sc, precision=args.precision, stream=stream.cuda_stream, key_order=args.key_order, skin=skin)
+    # cell layout and launch shape: the autotuner's pick on this workload (steps 30-60 from
+    # the initial state), or the command-line layout with --no-tune
+    if args.no_tune:
+        layout = dict(key_order=args.key_order, skin=args.skin * sc["params"]["h"])
+        launch = dict(sweep_block=256, sweep_waves=0, search_waves=0)
+        tuned = None
+    else:
+        from paper_2103_07925_gb300.tune import tune_scene
+        t_tune = time.perf_counter()
+        tn = tune_scene(sc, precision=args.precision, steps=30, warmup=30, use_cache=False)
+        layout, launch = dict(tn.params), dict(tn.launch)
+        tuned = dict(layout, **launch, ms_per_step=tn.ms_per_step, seconds=time.perf_counter() - t_tune,
+                     trials=len(tn.table))
+    g = Scene(sc, precision=args.precision, stream=stream.cuda_stream, **layout)
+    g.set_launch(**launch)
     info = g.info()
     g.step(args.warmup)
     clocks = Clocks(local)
@@ -397,8 +391,10 @@ def main():
                       "particles": info["n"], "fluid": info["n_fluid"], "rigid": info["n_rigid"],
                       "wall": info["n_wall"], "bodies": info["n_bodies"], "cells": info["n_cells"],
                       "precision": "FP32 pair sums, FP64 bodies" if args.precision == 32 else "FP64",
-                      "key_order": "morton" if args.key_order == 0 else "row-major",
-                      "skin_h": args.skin,
+                      "key_order": "morton" if layout["key_order"] == 0 else "row-major",
+                      "cells_per_group": layout.get("cells_per_group", 0),
+                      "skin_h": layout["skin"] / sc["params"]["h"],
+                      "launch": launch, "tuned": tuned,
                       "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (info["bytes"] / 1e6),
                       "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
            "steps_per_s": steps_per_s * world,
@@ -418,7 +414,7 @@ def main():
     # plain FP64 path on the same workload
     if not args.no_fp64 and args.precision == 32:
         s64 = torch.cuda.Stream()
-        g64 = Scene(sc, precision=64, stream=s64.cuda_stream, key_order=args.key_order, skin=skin)
+        g64 = Scene(sc, precision=64, stream=s64.cuda_stream, **layout)
         g64.step(2)
         k64 = max(5, min(args.steps // 10, 30))
         q0 = g64.info()["pairs_total"]

@@ -463,6 +463,11 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const T
 }
 
 // resident blocks per SM the force sweep is compiled for (register budget)
+// 1: the velocity and material records of a list entry are loaded with its position
+// (speculatively, before the distance test); 0: only for pairs inside the support
+#ifndef SPH_FORCE_SPECULATE
+#define SPH_FORCE_SPECULATE 1
+#endif
 #ifndef SPH_FORCE_MIN_BLOCKS
 #define SPH_FORCE_MIN_BLOCKS 4
 #endif
@@ -528,11 +533,18 @@ __global__ void __launch_bounds__(256, SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R
           for (; k < cnt; k++) {
             int en = k + 1 < cnt ? __ldg(L + (size_t)(k + 1) * S.n) : 0;
             int j = e >> 5;
+#if SPH_FORCE_SPECULATE
             float4 a = S.pa[j], b = S.pb[j], c = S.pc[j];
+#else
+            float4 a = S.pa[j];
+#endif
             float d[3];
             pack_delta<DIM>(S, ti, a, e & 31, d);
             float r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
             if (r2 < S.rc2R) {
+#if !SPH_FORCE_SPECULATE
+              float4 b = S.pb[j], c = S.pc[j];
+#endif
               force_pair_packed<DIM>(S, t, j, d, r2, a, b, c, acc, heat);
               npairs++;
             }
