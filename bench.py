@@ -28,9 +28,9 @@ METRIC = "SPH pair-interactions/s & steps/s at 1M particles; p50/p99 job latency
 FLOP_PER_PAIR = 62      # FP32 pair arithmetic of the force/heat sweep, FMA = 2 (see the design notes)
 BYTES_PER_TARGET = 72   # algorithmic HBM bytes per target particle of the force sweep (FP32)
 # DRAM bytes (read + write) of one k_force launch on the default workload, from
-# `ncu --set full` of this kernel version (profiles/ncu_k_force_tank3d_fp32.md); None once
-# the kernel changes and until it is captured again
-K_FORCE_TRAFFIC = None
+# `ncu --set full` of this kernel version (profiles/ncu_k_force_tank3d_fp32.md), per cell
+# layout (key order, skin in h) it was captured with; emptied whenever the kernel changes
+K_FORCE_TRAFFIC = {(1, 0.3): 792.1e6}
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
@@ -404,8 +404,8 @@ def main():
            "gpu_launches": args.steps * g.info()["kernels_per_step"],
            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                         "frac": achieved_tf / peak_tf,
-                        "traffic": K_FORCE_TRAFFIC if (args.workload == "tank3d" and dx == 0.01
-                                                       and args.precision == 32) else None,
+                        "traffic": K_FORCE_TRAFFIC.get((layout["key_order"], round(layout["skin"] / sc["params"]["h"], 3)))
+                        if (args.workload == "tank3d" and dx == 0.01 and args.precision == 32) else None,
                         "kernel": "k_force",
                         "peak_source": "FP32 FMA lanes x SMs x 2 x max SM clock (%s clocks)" % peak_src,
                         "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": hbm, "frac": hbm_ach / hbm,
