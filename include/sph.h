@@ -168,8 +168,14 @@ enum {
 sph_status sph_read_fields(sph_scene* scene, uint32_t field_mask, void* const* host_dst,
                            int32_t original_order);
 
-/* Overwrite POS, VEL and TEMP of fluid particles from host arrays in input order
- * (used for restarts and the host-buffer benchmark); re-bins before the next step. */
+/* Overwrite POS, VEL and TEMP of fluid particles from host arrays in input order (FP64,
+ * n rows of 3 or 1; rows of other particles are ignored).  Ownership stays with the
+ * caller; the copy is enqueued on the scene's stream.  The next step starts from the
+ * written state with the accelerations of the last evaluation (its first half kick,
+ * Sec. 3.7), as a staggered coupling with an outside solver does.  A written particle stays
+ * in its cell frame: the Verlet-skin test of the next step decides whether the neighbour
+ * lists are rebuilt; a particle written more than 64 cells away forces a rebuild.
+ * SPH_ERR_INVALID for other fields. */
 sph_status sph_write_fields(sph_scene* scene, uint32_t field_mask, const void* const* host_src);
 
 /* Body state (k rows; each pointer nullable): com k*3, quat k*4, vel k*3, omega k*3,

@@ -96,15 +96,33 @@ __global__ void k_import_fluid(Scene<R>* const* sc, const double* pos, const dou
       if (sizeof(R) == 8) {
         S.P.px[i] = (R)x[0]; S.P.py[i] = (R)x[1]; S.P.pz[i] = (R)x[2];
       } else {
+        // offset from the origin of the particle's current cell (minimum image), as the
+        // drift leaves it: the lists and the displacement since their build stay in one
+        // frame, and the next rebin moves the particle to its new cell
         int c[3] = {0, 0, 0};
+        lin_xyz(S, key_lin(S, S.key[i]), c[0], c[1], c[2]);
+        double o[3] = {0.0, 0.0, 0.0};
+        bool far = false;
         for (int k = 0; k < S.dim; k++) {
-          double v = floor((x[k] - S.lo[k]) / S.ell[k]);
-          c[k] = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
+          o[k] = x[k] - (S.lo[k] + c[k] * S.ell[k]);
+          if (S.per[k]) {
+            if (o[k] > 0.5 * S.L[k]) o[k] -= S.L[k];
+            else if (o[k] < -0.5 * S.L[k]) o[k] += S.L[k];
+          }
+          far |= fabs(o[k]) > 64.0 * S.ell[k];
         }
-        S.key[i] = cell_key(S, c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]));
-        S.P.px[i] = (R)(x[0] - (S.lo[0] + c[0] * S.ell[0]));
-        S.P.py[i] = (R)(x[1] - (S.lo[1] + c[1] * S.ell[1]));
-        S.P.pz[i] = S.dim == 3 ? (R)(x[2] - (S.lo[2] + c[2] * S.ell[2])) : R(0);
+        if (far) {  // a jump across the box: new cell, and the lists are rebuilt next step
+          for (int k = 0; k < S.dim; k++) {
+            double v = floor((x[k] - S.lo[k]) / S.ell[k]);
+            c[k] = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
+            o[k] = x[k] - (S.lo[k] + c[k] * S.ell[k]);
+          }
+          S.key[i] = cell_key(S, c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]));
+          S.status[10] = 1;
+        }
+        S.P.px[i] = (R)o[0];
+        S.P.py[i] = (R)o[1];
+        S.P.pz[i] = (R)o[2];
       }
     }
     if (vel) { S.P.vx[i] = (R)vel[3 * o]; S.P.vy[i] = (R)vel[3 * o + 1]; S.P.vz[i] = (R)vel[3 * o + 2]; }

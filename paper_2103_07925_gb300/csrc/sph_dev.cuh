@@ -108,7 +108,8 @@ struct Scene {
   int* status;         // [0] non-finite flag [1] relabel count [2] capacity error [3] table error
                        // [4] rebuild in this step [5] steps since rebuild [6] rebuild count
                        // [7] solidifiers without a rigid neighbour [8] new bodies this step
-                       // [9] relabelled particles so far [10] kinds changed since the lists were built
+                       // [9] relabelled particles so far [10] lists stale (kinds changed, or a particle was moved
+                       // to another cell by a write) since they were built
   int* pfx1;           // prefix tables of this scene alone (6 x 2 ints)
   Scene<R>** self;     // device array holding the address of this descriptor
   unsigned long long* pairs;  // [0] force-sweep pairs of the last evaluation
