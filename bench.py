@@ -242,6 +242,26 @@ def bench_batch(args, rank, world, allmax, allsum, barrier):
             tot_ms += g.time_steps(k) / k
             g.close()
         plain[prec] = len(scs) / (allmax(tot_ms) / 1e3) * world
+    # FP64 check of the batched FP32 form on 8 sampled scenes: one step in a batch of the
+    # sample against each scene alone on the FP64 path
+    from paper_2103_07925_gb300.errors import field_scales, rel_err
+    pick = [int(q) for q in np.linspace(0, len(scs) - 1, 8)]
+    Bc = Batch(capacity=8, precision=32)
+    cids = [Bc.admit(scs[q], 1) for q in pick]
+    Bc.step(1)
+    Bc.poll()
+    flds = ("pos", "vel", "rho", "pres", "temp")
+    check = {f: 0.0 for f in flds}
+    for q, cid in zip(pick, cids):
+        r32 = Bc.read(cid, *flds)
+        g64 = Scene(scs[q], precision=64)
+        g64.step(1)
+        r64 = g64.read(*flds)
+        g64.close()
+        sca = field_scales(scs[q])
+        for f in flds:
+            check[f] = max(check[f], rel_err(r32[f], r64[f], scale=sca.get(f, 0.0)))
+    Bc.close()
     out = {"metric": "scene-steps/s, batched form (%d mixed 2D/3D scenes)" % len(scs), "value": value,
            "unit": "scene-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -256,6 +276,7 @@ def bench_batch(args, rank, world, allmax, allsum, barrier):
            "plain_fp64": {"value": plain[64], "unit": "scene-steps/s", "kind": "each scene alone, FP64"},
            "plain_fp32": {"value": plain[32], "unit": "scene-steps/s", "kind": "each scene alone, FP32"},
            "speedup_vs_plain_fp64": value / plain[64],
+           "fp64_check": {"scenes": pick, "max_error_after_1_step": check, "tolerance": 1e-5},
            "gpu_launches": args.steps * info["kernels_per_step"],
            "e2e": {"value": allsum(len(scs) * args.steps) / e2e_s, "unit": "scene-steps/s",
                    "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
@@ -429,6 +450,32 @@ def main():
         out["fp64"] = {"value": (q1 - q0) / (m64 / 1e3), "ms_per_step": m64 / k64, "steps": k64,
                        "steps_per_s": k64 / (m64 / 1e3)}
         g64.close()
+    # FP32 against the FP64 path on the same workload and layout: every output field after
+    # one step from the same initial state, body trajectories after 100 steps
+    if not args.no_fp64 and args.precision == 32:
+        from paper_2103_07925_gb300.errors import body_errors, edge_only_boundary, field_scales, rel_err
+        a32 = Scene(sc, precision=32, **layout)
+        a64 = Scene(sc, precision=64, **layout)
+        a32.set_launch(**launch)
+        a32.step(1)
+        a64.step(1)
+        flds = ("pos", "vel", "acc", "rho", "pres", "temp", "dtemp", "force", "vext")
+        f32, f64 = a32.read(*flds), a64.read(*flds)
+        sca = field_scales(sc)
+        step1 = {f: rel_err(f32[f], f64[f], scale=sca.get(f, 0.0)) for f in flds}
+        # wall / rigid particles whose fluid neighbours all sit at the support edge
+        edge = edge_only_boundary(sc, f64["pos"], sc["particles"]["material"])
+        step1_edge = {f: rel_err(f32[f], f64[f], mask=~edge, scale=sca.get(f, 0.0)) for f in ("pres", "vext")}
+        a32.step(99)
+        a64.step(99)
+        b100 = body_errors(a32.bodies(), a64.bodies(), sc, a64.read("body"))
+        out["fp32_vs_fp64"] = {"step1_fields": step1,
+                               "step1_without_edge_only_boundary": dict(step1_edge, particles_excluded=int(edge.sum())),
+                               "bodies_after_100_steps": b100,
+                               "tolerance": {"fields_per_step": 1e-5, "bodies_100_steps": 1e-3},
+                               "metric": "max |x32 - x64| / max(|x64|, RMS(x64), term scale of the field)"}
+        a32.close()
+        a64.close()
     # end to end through the C ABI with host buffers: the host holds the fluid state; every
     # step writes it from pinned memory, advances one step and reads the new state back
     # into the same pinned arrays (so the scene evolves as in the device-timed run)

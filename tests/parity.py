@@ -1,51 +1,10 @@
 """Helpers shared by the GPU parity tests (no method arithmetic here)."""
 import numpy as np
 
+from paper_2103_07925_gb300.errors import body_errors, field_scales, rel_err  # noqa: F401 (re-exported)
+
 FLOAT_FIELDS = ["pos", "vel", "acc", "rho", "pres", "temp", "dtemp", "force", "vext"]
 INT_FIELDS = ["mat", "body", "cell"]
-
-
-def rel_err(a, b, mask=None, scale=0.0):
-    """max |a - b| / max(|b|, RMS(b), scale); NaN positions must agree."""
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    if mask is not None:
-        a = a[mask]
-        b = b[mask]
-    na, nb = np.isnan(a), np.isnan(b)
-    if not np.array_equal(na, nb):
-        return np.inf
-    a = a[~na]
-    b = b[~nb]
-    if b.size == 0:
-        return 0.0
-    s = max(np.sqrt(np.mean(b * b)), scale, 1e-300)
-    den = np.maximum(np.abs(b), s)
-    return float(np.max(np.abs(a - b) / den))
-
-
-def field_scales(sc):
-    """Magnitude of the terms that make up each field at the scene's reference state.
-
-    The weakly compressible pressure p = c^2 (rho - rho0) is a small difference of large
-    numbers, so its rounding error is relative to p0 = rho0 c^2, not to p; the same
-    conditioning carries into accelerations (p0 / (rho0 h)), rigid forces (p0 h^(d-1)),
-    one step of velocity change (dt c^2 / h) and, for heat, temperature differences
-    (kappa T / (rho c_p h^2)).
-    """
-    p = sc["params"]
-    mats = sc["materials"]
-    h, d = p["h"], p["dim"]
-    fl = [m for m in mats if m["kind"] == 0]
-    c = max([m["c"] for m in fl] or [0.0])
-    p0 = max([m["rho0"] * m["c"] ** 2 for m in fl] or [0.0])
-    rho0 = min([m["rho0"] for m in fl] or [1.0])
-    dt = p["dt_fixed"] if p["dt_mode"] == 0 else 0.25 * h / max(c, 1e-300)
-    T = float(np.sqrt(np.mean(np.asarray(sc["particles"]["temperature"]) ** 2)))
-    kap = max([m["kappa"] / (m["rho0"] * m["cp"]) for m in mats if m["kind"] != 2 and m["cp"] > 0] or [0.0])
-    acc = p0 / (rho0 * h)
-    return {"pres": p0, "acc": acc, "force": p0 * h ** (d - 1), "vel": dt * acc, "vext": dt * acc,
-            "dtemp": kap * T / (h * h), "pos": 0.0, "rho": 0.0, "temp": 0.0}
 
 
 def compare_fields(gpu, orc, fields=FLOAT_FIELDS, ints=INT_FIELDS, scales=None):
@@ -60,46 +19,8 @@ def compare_fields(gpu, orc, fields=FLOAT_FIELDS, ints=INT_FIELDS, scales=None):
 
 
 def compare_bodies(gpu, orc, sc=None):
-    """Body state errors; with the scene given, force and torque are measured against the
-    pressure-force scale of the body's particles (N_k p0 h^(d-1), and times the radius of
-    gyration for torques) and velocities against one step of that acceleration."""
-    g, o = gpu.bodies(), orc.bodies()
-    k = len(o["mass"])
-    errs = {}
-    assert len(g["mass"]) == k
-    if k == 0:
-        return errs
-    assert np.array_equal(g["alive"], o["alive"])
-    alive = o["alive"] == 1
-    if not alive.any():
-        return errs
-    fs = np.zeros(k)
-    ts = np.zeros(k)
-    vs = np.zeros(k)
-    ws = np.zeros(k)
-    if sc is not None:
-        sca = field_scales(sc)
-        p = sc["params"]
-        dt = p["dt_fixed"] if p["dt_mode"] == 0 else sca["vel"] / max(sca["acc"], 1e-300)
-        body = orc.get("body")
-        nk = np.bincount(body[body >= 0], minlength=k).astype(float)
-        rg = np.sqrt(np.maximum(np.trace(o["inertia"], axis1=1, axis2=2), 0) / np.maximum(o["mass"], 1e-300))
-        fs = nk * sca["force"]
-        ts = fs * rg
-        lam = np.array([max(np.linalg.eigvalsh(I).min(), 1e-300) for I in o["inertia"]])
-        vs = dt * fs / np.maximum(o["mass"], 1e-300)
-        ws = dt * ts / lam
-    sc_of = {"force": fs, "torque": ts, "vel": vs, "omega": ws}
-    for f in ("com", "quat", "vel", "omega", "mass", "inertia", "force", "torque"):
-        a, b = g[f][alive], o[f][alive]
-        s = sc_of.get(f)
-        if s is None:
-            errs[f] = rel_err(a, b)
-        else:
-            s = s[alive].reshape((-1,) + (1,) * (b.ndim - 1))
-            den = np.maximum(np.maximum(np.abs(b), np.sqrt(np.mean(b * b))), s)
-            errs[f] = float(np.max(np.abs(a - b) / np.maximum(den, 1e-300)))
-    return errs
+    """Body state errors of a GPU scene against the oracle (see errors.body_errors)."""
+    return body_errors(gpu.bodies(), orc.bodies(), sc, orc.get("body"))
 
 
 def state_scene(sc, orc):

@@ -1,0 +1,76 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the benchmark times
+(row-major cells, Verlet skin 0.3 h, 256-thread sweeps): one step of the 1.28M-particle
+tank and of the 2.1M-particle powder bed against the FP64 oracle (all outputs; cells and
+neighbour counts bit-exact on the FP64 path)."""
+import numpy as np
+import pytest
+
+from paper_2103_07925_gb300 import scenes as S
+from tests.parity import compare_bodies, compare_fields, field_scales, rel_err  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+LAYOUT = dict(key_order=1, skin=0.003)
+
+
+@pytest.fixture(scope="module")
+def tank():
+    from oracle.oracle import OracleScene
+    sc = S.tank3d_spheres()
+    o = OracleScene(sc)
+    nb = o.neighbors()  # at the input positions, which both sides hold bit for bit
+    o.step(1)
+    return sc, o, nb
+
+
+def test_tank_full_size_fp64(tank):
+    from paper_2103_07925_gb300.sph import Scene
+    sc, o, (co, lo) = tank
+    g = Scene(sc, precision=64, key_order=1)
+    cg, lg = g.neighbors()
+    assert np.array_equal(cg, co)
+    assert np.array_equal(lg, lo)
+    g.step(1)
+    errs = compare_fields(g, o, scales=field_scales(sc))
+    bad = {f: e for f, e in errs.items() if not e < 1e-12}
+    assert not bad, bad
+    be = compare_bodies(g, o, sc)
+    bad = {f: e for f, e in be.items() if not e < 1e-12}
+    assert not bad, bad
+    g.close()
+
+
+def test_tank_full_size_fp32_in_bench_configuration(tank):
+    from paper_2103_07925_gb300.errors import edge_only_boundary
+    from paper_2103_07925_gb300.sph import Scene
+    sc, o, _ = tank
+    g = Scene(sc, precision=32, **LAYOUT)
+    g.set_launch(sweep_block=256, sweep_waves=0, search_waves=0)
+    g.step(1)
+    assert np.array_equal(g.read("mat"), o.get("mat"))
+    assert np.array_equal(g.read("body"), o.get("body"))
+    edge = edge_only_boundary(sc, o.get("pos"), sc["particles"]["material"])
+    assert edge.sum() < 1e-2 * len(edge)  # the deepest wall layer sits 3 dx (= r_c) from the fluid
+    sca = field_scales(sc)
+    for f in ("pos", "vel", "acc", "rho", "pres", "temp", "dtemp", "force", "vext"):
+        e = rel_err(g.read(f), o.get(f), mask=~edge if f in ("pres", "vext") else None, scale=sca.get(f, 0.0))
+        assert e < 1e-5, (f, e)
+    g.close()
+
+
+def test_powder_bed_full_size_fp32():
+    from oracle.oracle import OracleScene
+    from paper_2103_07925_gb300.sph import Scene
+    from tests.test_gpu_powder import _edge_only_boundary
+    sc = S.powder_bed()
+    g = Scene(sc, precision=32, **LAYOUT)
+    g.step(1)
+    o = OracleScene(sc)
+    o.step(1)
+    assert np.array_equal(g.read("mat"), o.get("mat"))
+    assert np.array_equal(g.read("body"), o.get("body"))
+    edge = _edge_only_boundary(sc, o)
+    sca = dict(field_scales(sc), enth=0.0)
+    for f in ("pos", "vel", "acc", "rho", "pres", "temp", "dtemp", "force", "vext", "enth"):
+        e = rel_err(g.read(f), o.get(f), mask=~edge if f in ("pres", "vext") else None, scale=sca.get(f, 0.0))
+        assert e < 1e-5, (f, e)
+    g.close()

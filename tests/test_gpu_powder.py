@@ -71,20 +71,10 @@ def _joins_valid(sc, g, o):
 
 
 def _edge_only_boundary(sc, o):
-    """Particles that were wall or rigid during the step (before its relabel) and whose nearest
-    fluid neighbour lies within 1e-5 r_c of r_c (positions do not change at the relabel)."""
-    from scipy.spatial import cKDTree
-    p = sc["params"]
-    rc = p["kernel_support"] * p["h"]
-    lo, hi = np.array(p["box_min"]), np.array(p["box_max"])
-    box = np.where(np.array(p["periodic"]) == 1, hi - lo, 1e6)
-    pos = o.get("pos") - lo
-    fl = np.isin(sc["particles"]["material"], [0, 3])
-    tree = cKDTree(np.mod(pos[fl], box), boxsize=box)
-    r, _ = tree.query(np.mod(pos[~fl], box), k=1)
-    out = np.zeros(len(pos), bool)
-    out[np.nonzero(~fl)[0]] = np.abs(r - rc) < 1e-5 * rc
-    return out
+    """Wall and rigid particles during the step (before its relabel) whose fluid neighbours
+    all sit at the support edge (positions do not change at the relabel)."""
+    from paper_2103_07925_gb300.errors import edge_only_boundary
+    return edge_only_boundary(sc, o.get("pos"), sc["particles"]["material"])
 
 
 def _compare(sc, precision, tol):
