@@ -65,6 +65,8 @@
  *      dH/dt of particles whose material takes part in a phase transition.
  *  R13 dt (Eq. timestepcond) is fixed when given, otherwise the minimum of the five
  *      conditions with |u|max over fluid particles at the start of the step.
+ *  R14 wall particles with a prescribed velocity move with it (the moving boundary
+ *      particles of the shear-flow examples, Sec. 4.2): x += dt u_w in the drift.
  */
 #include "sph_oracle.h"
 
@@ -1043,8 +1045,16 @@ static int step_once(orc_scene* s) {
   double dt = time_step(s);
   double half = 0.5 * dt;
   s->dt = dt;
-  /* kick and drift of fluid particles */
+  /* kick and drift of fluid particles; wall particles move with their prescribed
+   * velocity (R14) */
   for (int64_t i = 0; i < n; i++) {
+    if (is_kind(s, i, ORC_WALL)) {
+      const double* w = &s->wu[3 * i];
+      if (w[0] == 0.0 && w[1] == 0.0 && w[2] == 0.0) continue;
+      for (int q = 0; q < 3; q++) s->x[3 * i + q] = s->x[3 * i + q] + dt * w[q];
+      wrap(s, &s->x[3 * i]);
+      continue;
+    }
     if (!is_kind(s, i, ORC_FLUID)) continue;
     for (int q = 0; q < 3; q++) {
       s->u[3 * i + q] = s->u[3 * i + q] + half * s->a[3 * i + q];

@@ -665,3 +665,25 @@ def powder_bed(dx=0.005, size=(1.0, 0.5, 0.5), n_grains=2000, r_median=0.02, r_s
     sc = b.finish(p, mats)
     sc["info"] = dict(grains=len(used), grains_requested=n_grains, rigid=int(len(rig)), tries=tries)
     return sc
+
+
+# --------------------------------------------------------------------------- shear flow
+
+def couette2d(dx=0.01, width=0.1, height=0.2, U=1.0, c=10.0, rho0=1.0, nu=0.1, jitter=0.0, seed=7,
+              dt=None, precision=64):
+    """Plane Couette channel (the moving-wall set-up of the paper's shear-flow examples,
+    Sec. 4.2): periodic in x, fluid of height ``height`` at rest, three layers of wall
+    particles below (at rest) and above (moving along x with velocity U)."""
+    rng = np.random.default_rng(seed)
+    nx, ny = int(round(width / dx)), int(round(height / dx))
+    b = _Builder(2)
+    mats = [material(FLUID, rho0, c=c, eta=rho0 * nu), material(WALL, rho0)]
+    fl = lattice([0.0, 0.0], [nx, ny], dx)
+    b.add(_jitter(rng, _pad3(fl), jitter * dx, 2), 0, rho0 * dx * dx, rho0, 300.0)
+    b.add(lattice([0.0, -3 * dx], [nx, 3], dx), 1, rho0 * dx * dx, rho0, 300.0)
+    b.add(lattice([0.0, ny * dx], [nx, 3], dx), 1, rho0 * dx * dx, rho0, 300.0, wall_vel=[U, 0.0, 0.0])
+    if dt is None:  # the viscous condition of Eq. (timestepcond) binds
+        dt = min(0.25 * dx / c, 0.125 * dx * dx / nu)
+    p = default_params(2, dx, [0.0, -3 * dx], [nx * dx, (ny + 3) * dx], periodic=[1, 0, 0],
+                       dt_mode=0, dt_fixed=dt, precision=precision)
+    return b.finish(p, mats)

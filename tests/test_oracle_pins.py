@@ -500,3 +500,42 @@ def test_enthalpy_balance_with_source_over_melt_and_solidify():
         melted |= bool(np.any((o.get("mat") == 0) & (sc["particles"]["material"] == 1)))
     assert melted
     assert o.diagnostics()[7] > e0
+
+
+def _couette_series(y, t, U, H, nu, N=400):
+    """Start-up plane Couette flow (wall at y = 0 at rest, wall at y = H moving at U from
+    t = 0, fluid at rest): u = U y/H + (2U/pi) sum_n ((-1)^n / n) sin(n pi y/H) exp(-n^2 pi^2 nu t/H^2)."""
+    n = np.arange(1, N + 1)[:, None]
+    return U * y / H + (2 * U / np.pi) * np.sum(((-1.0) ** n / n) * np.sin(n * np.pi * y / H)
+                                                 * np.exp(-(n * np.pi) ** 2 * nu * t / H ** 2), axis=0)
+
+
+def test_moving_wall_couette_start_up_matches_series_and_converges():
+    """Moving boundary particles (R14): the start-up of plane Couette flow follows the
+    closed-form series, and the error falls as the spacing is refined."""
+    errs = []
+    for dx in (0.01, 0.005):
+        sc = S.couette2d(dx=dx)
+        o = O.OracleScene(sc)
+        o.step(int(round(0.01 / sc["params"]["dt_fixed"])))
+        t = o.diagnostics()[9]
+        x, v, fl = o.get("pos"), o.get("vel"), o.get("mat") == 0
+        errs.append(np.abs(v[fl, 0] - _couette_series(x[fl, 1], t, 1.0, 0.2, 0.1)).max())
+        assert np.abs(v[fl, 1]).max() < 1e-3
+    assert errs[0] < 5e-3 and errs[1] < 0.5 * errs[0], errs
+
+
+def test_moving_wall_reaches_linear_profile_and_translates():
+    sc = S.couette2d()
+    p = sc["params"]
+    tau = 0.2 ** 2 / (np.pi ** 2 * 0.1)
+    n = int(round(6 * tau / p["dt_fixed"]))
+    o = O.OracleScene(sc)
+    o.step(n)
+    x, v, mat = o.get("pos"), o.get("vel"), o.get("mat")
+    fl = mat == 0
+    assert np.abs(v[fl, 0] - x[fl, 1] / 0.2).max() < 2e-3
+    top = (mat == 1) & (x[:, 1] > 0.2)
+    x0 = sc["particles"]["pos"][top, 0]
+    shift = np.mod(x[top, 0] - x0, 0.1)
+    assert np.allclose(shift, np.mod(n * p["dt_fixed"], 0.1), atol=1e-12)
