@@ -247,7 +247,21 @@ __global__ void __launch_bounds__(256) k_kick_drift(BatchView<R> B) {
     const Scene<R>& S = *B.sc[s];
     int i = g - __ldg(B.pfx_part + s);
     int kind = g < total ? S.matR[S.P.mt[i]].kind : KWALL;
-    if (kind == KFLUID) {
+    // wall particles with a prescribed velocity move with it (moving boundaries)
+    bool moving_wall = g < total && kind == KWALL && (S.P.vx[i] != R(0) || S.P.vy[i] != R(0) || S.P.vz[i] != R(0));
+    if (moving_wall) {
+      R dt = (R)S.st[0];
+      if (sizeof(R) == 8) {
+        double x[3] = {(double)S.P.px[i] + (double)dt * (double)S.P.vx[i],
+                       (double)S.P.py[i] + (double)dt * (double)S.P.vy[i],
+                       (double)S.P.pz[i] + (double)dt * (double)S.P.vz[i]};
+        store_pos<R>(S, i, x);
+      } else {
+        S.P.px[i] = S.P.px[i] + dt * S.P.vx[i];
+        S.P.py[i] = S.P.py[i] + dt * S.P.vy[i];
+        S.P.pz[i] = S.P.pz[i] + dt * S.P.vz[i];
+      }
+    } else if (kind == KFLUID) {
       R dt = (R)S.st[0], half = R(0.5) * dt;
       R ux = S.P.vx[i] + half * S.P.ax[i];
       R uy = S.P.vy[i] + half * S.P.ay[i];
@@ -282,10 +296,10 @@ __global__ void __launch_bounds__(256) k_kick_drift(BatchView<R> B) {
     }
     // packed position for the density sweep of a step without rebuild (FP32 scenes)
     if constexpr (sizeof(R) == 4)
-      if (kind != KWALL) S.pa[i] = make_float4(S.P.px[i], S.P.py[i], S.P.pz[i], S.P.rho[i]);
+      if (kind != KWALL || moving_wall) S.pa[i] = make_float4(S.P.px[i], S.P.py[i], S.P.pz[i], S.P.rho[i]);
     // displacement since the last list rebuild (skin criterion)
     R d2 = R(0);
-    if (kind != KWALL && S.skin > 0.0) {
+    if ((kind != KWALL || moving_wall) && S.skin > 0.0) {
       R d[3] = {S.P.px[i] - S.xr[i], S.P.py[i] - S.yr[i], S.P.pz[i] - S.zr[i]};
       for (int k = 0; k < S.dim; k++)
         if (sizeof(R) == 8 && S.per[k]) {
