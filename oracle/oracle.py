@@ -17,8 +17,8 @@ _lib = None
 
 ORC_MAXMAT = 32
 FIELDS = dict(pos=0, vel=1, acc=2, rho=3, pres=4, temp=5, dtemp=6, mat=7, body=8, force=9,
-              vext=10, cell=11, enth=12)
-_VEC = {"pos", "vel", "acc", "force", "vext"}
+              vext=10, cell=11, enth=12, bacc=13)
+_VEC = {"pos", "vel", "acc", "force", "vext", "bacc"}
 _INT = {"mat", "body", "cell"}
 
 
@@ -38,7 +38,7 @@ class _Params(C.Structure):
                 ("materials", _Mat * ORC_MAXMAT), ("body_capacity", C.c_int32),
                 ("src_power", C.c_double), ("src_radius", C.c_double), ("src_speed", C.c_double * 3),
                 ("src_origin", C.c_double * 3), ("src_depth", C.c_double), ("src_ztop", C.c_double),
-                ("skin", C.c_double), ("force_brute", C.c_int32)]
+                ("skin", C.c_double), ("force_brute", C.c_int32), ("p_background", C.c_double)]
 
 
 def lib():
@@ -116,6 +116,7 @@ def _params(scene, force_brute=False):
     P.src_ztop = p.get("src_ztop", 0.0)
     P.skin = p.get("skin", 0.0)
     P.force_brute = 1 if force_brute else 0
+    P.p_background = p.get("p_background", 0.0)
     return P
 
 

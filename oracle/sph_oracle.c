@@ -67,6 +67,17 @@
  *      conditions with |u|max over fluid particles at the start of the step.
  *  R14 wall particles with a prescribed velocity move with it (the moving boundary
  *      particles of the shear-flow examples, Sec. 4.2): x += dt u_w in the drift.
+ *  R15 transport-velocity formulation (Sec. 3.3.2 applies it after Adami, Hu and Adams
+ *      2013, without printing it), on when the background pressure p_b > 0: fluid
+ *      particles are advected with u~ = u^{n+1/2} + dt/2 a~^n, where
+ *      a~_i = -(p_b / m_i) sum_j (V_i^2 + V_j^2) dW/dr e_ij over neighbours of every kind;
+ *      the momentum equation gains (1/m_i) sum_j (V_i^2 + V_j^2) 1/2 (A_i + A_j) . e_ij dW/dr
+ *      with A = rho u (u~ - u) (an outer product; A = 0 for wall and rigid particles), which
+ *      enters the coupling force on rigid particles like every other term of a_ir.
+ *      A particle that melts starts with a~ = 0.  p_b = 0 gives the scheme without it.
+ *      Pins: a~ = 0 on a regular lattice, exact momentum with the A term (antisymmetry),
+ *      regularisation growing with p_b, Couette profile; the overall sign of the A term
+ *      follows Adami et al. and is pinned only through these (parity partially unpinned).
  */
 #include "sph_oracle.h"
 
@@ -90,6 +101,8 @@ struct orc_scene {
   double rc, rc2, dt_ref;
   int64_t n;
   double *x, *u, *a, *rho, *p, *T, *dT, *m, *H, *vext, *f, *rb, *wu, *wT;
+  double *ab, *tv; /* R15: background acceleration a~ and u~ - u of the current half step */
+  int tvf;
   int32_t *mat, *body;
   /* bodies */
   int32_t K, Kcap;
@@ -636,6 +649,32 @@ static void pair_term(const orc_scene* s, int64_t i, int64_t j, double* out) {
     double uij = s->u[3 * i + k] - uj[k];
     out[k] = coef * (-pt * e[k] + et * uij / r);
   }
+  if (s->tvf) { /* R15: 1/2 (A_i + A_j) . e_ij, A = rho u (u~ - u); A_j = 0 for boundaries */
+    double si = 0.0, sj = 0.0;
+    for (int k = 0; k < 3; k++) si += s->tv[3 * i + k] * e[k];
+    if (B->kind == ORC_FLUID)
+      for (int k = 0; k < 3; k++) sj += s->tv[3 * j + k] * e[k];
+    for (int k = 0; k < 3; k++) {
+      double Ae = rhoi * s->u[3 * i + k] * si + (B->kind == ORC_FLUID ? s->rho[j] * s->u[3 * j + k] * sj : 0.0);
+      out[k] += coef * 0.5 * Ae;
+    }
+  }
+}
+
+/* R15: -(p_b / m_i) sum_j (V_i^2 + V_j^2) dW/dr e_ij for fluid particle i, all neighbours */
+static void background_acc(orc_scene* s, int64_t i, double* out) {
+  double sum[3] = {0, 0, 0};
+  double Vi = s->m[i] / s->rho[i];
+  for (int64_t q = s->nstart[i]; q < s->nstart[i + 1]; q++) {
+    int64_t j = s->nlist[q];
+    double d[3];
+    min_image(s, &s->x[3 * i], &s->x[3 * j], d);
+    double r = sqrt(norm2(s, d));
+    double Vj = s->m[j] / s->rho[j];
+    double c = (Vi * Vi + Vj * Vj) * dwij(s, r) / r;
+    for (int k = 0; k < 3; k++) sum[k] += c * d[k];
+  }
+  for (int k = 0; k < 3; k++) out[k] = -s->P.p_background / s->m[i] * sum[k];
 }
 
 /* Eq. contactforce for the rigid particle r against particle j (rigid of another body or wall) */
@@ -674,6 +713,7 @@ static void forces(orc_scene* s) {
         s->a[3 * i + k] = s->P.gravity[k] + acc[k] / s->m[i];
         s->f[3 * i + k] = 0.0;
       }
+      if (s->tvf) background_acc(s, i, &s->ab[3 * i]);
     } else {
       for (int64_t q = s->nstart[i]; q < s->nstart[i + 1]; q++) {
         int64_t j = s->nlist[q];
@@ -863,7 +903,11 @@ static int relabel(orc_scene* s) {
     cross3(&s->bal[3 * k], rr, t1);
     cross3(&s->bw[3 * k], rr, t2);
     cross3(&s->bw[3 * k], t2, t3);
-    for (int q = 0; q < 3; q++) s->a[3 * i + q] = s->ba[3 * k + q] + t1[q] + t3[q];
+    for (int q = 0; q < 3; q++) {
+      s->a[3 * i + q] = s->ba[3 * k + q] + t1[q] + t3[q];
+      s->ab[3 * i + q] = 0.0; /* R15 */
+      s->tv[3 * i + q] = 0.0;
+    }
     changed[k] = 1;
     s->mat[i] = M(s, i)->transitions_to;
     s->body[i] = -1;
@@ -978,6 +1022,8 @@ orc_scene* orc_create(const orc_params* P, int64_t n, const double* pos, const d
   s->p = dalloc(n); s->T = dalloc(n); s->dT = dalloc(n); s->m = dalloc(n); s->H = dalloc(n);
   s->vext = dalloc(3 * n); s->f = dalloc(3 * n); s->rb = dalloc(3 * n); s->wu = dalloc(3 * n);
   s->wT = dalloc(n);
+  s->ab = dalloc(3 * n); s->tv = dalloc(3 * n);
+  s->tvf = P->p_background > 0.0;
   s->mat = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
   s->body = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
   s->nstart = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
@@ -1058,7 +1104,12 @@ static int step_once(orc_scene* s) {
     if (!is_kind(s, i, ORC_FLUID)) continue;
     for (int q = 0; q < 3; q++) {
       s->u[3 * i + q] = s->u[3 * i + q] + half * s->a[3 * i + q];
-      s->x[3 * i + q] = s->x[3 * i + q] + dt * s->u[3 * i + q];
+      if (s->tvf) { /* R15: advection with u~ = u^{n+1/2} + dt/2 a~^n */
+        s->tv[3 * i + q] = half * s->ab[3 * i + q];
+        s->x[3 * i + q] = s->x[3 * i + q] + dt * (s->u[3 * i + q] + s->tv[3 * i + q]);
+      } else {
+        s->x[3 * i + q] = s->x[3 * i + q] + dt * s->u[3 * i + q];
+      }
     }
     wrap(s, &s->x[3 * i]);
   }
@@ -1153,6 +1204,10 @@ void orc_get(orc_scene* s, int32_t field, void* out) {
         for (int q = 0; q < 3; q++) d[3 * i + q] = is_kind(s, i, ORC_FLUID) ? 0.0 : s->vext[3 * i + q];
       break;
     case ORC_F_ENTH: memcpy(d, s->H, sizeof(double) * (size_t)n); break;
+    case ORC_F_BACC: /* R15: background acceleration a~ of fluid particles */
+      for (int64_t i = 0; i < n; i++)
+        for (int q = 0; q < 3; q++) d[3 * i + q] = is_kind(s, i, ORC_FLUID) ? s->ab[3 * i + q] : 0.0;
+      break;
     case ORC_F_CELL:
       for (int64_t i = 0; i < n; i++) {
         int32_t c[3];
@@ -1237,7 +1292,7 @@ void orc_destroy(orc_scene* s) {
   if (!s) return;
   double* arrs[] = {s->x, s->u, s->a, s->rho, s->p, s->T, s->dT, s->m, s->H, s->vext, s->f, s->rb,
                     s->wu, s->wT, s->bm, s->br, s->bq, s->bu, s->bw, s->ba, s->bal, s->bf, s->bt,
-                    s->bIb, s->bIw};
+                    s->bIb, s->bIw, s->ab, s->tv};
   for (size_t q = 0; q < sizeof arrs / sizeof arrs[0]; q++) free(arrs[q]);
   free(s->mat); free(s->body); free(s->alive); free(s->nstart); free(s->nlist);
   free(s);

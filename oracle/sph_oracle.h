@@ -49,6 +49,7 @@ typedef struct {
   double src_power, src_radius, src_speed[3], src_origin[3], src_depth, src_ztop;
   double skin;         /* cells of the neighbour search have edge >= r_c + skin */
   int32_t force_brute; /* 1: brute-force O(N^2) neighbour search */
+  double p_background; /* background pressure of the transport-velocity formulation (R15); 0: off */
 } orc_params;
 
 typedef struct orc_scene orc_scene;
@@ -56,7 +57,7 @@ typedef struct orc_scene orc_scene;
 /* field ids for orc_get */
 enum {
   ORC_F_POS = 0, ORC_F_VEL, ORC_F_ACC, ORC_F_RHO, ORC_F_PRES, ORC_F_TEMP, ORC_F_DTEMP,
-  ORC_F_MAT, ORC_F_BODY, ORC_F_FORCE, ORC_F_VEXT, ORC_F_CELL, ORC_F_ENTH
+  ORC_F_MAT, ORC_F_BODY, ORC_F_FORCE, ORC_F_VEXT, ORC_F_CELL, ORC_F_ENTH, ORC_F_BACC
 };
 
 orc_scene* orc_create(const orc_params* P, int64_t n, const double* pos, const double* vel,

@@ -5,6 +5,7 @@ paper prints, closed forms, conservation laws of the discrete equations,
 quadrature, brute force on tiny inputs, or special cases with textbook
 solutions.  CPU only.
 """
+import copy
 import json
 import math
 import os
@@ -539,3 +540,71 @@ def test_moving_wall_reaches_linear_profile_and_translates():
     x0 = sc["particles"]["pos"][top, 0]
     shift = np.mod(x[top, 0] - x0, 0.1)
     assert np.allclose(shift, np.mod(n * p["dt_fixed"], 0.1), atol=1e-12)
+
+
+# --------------------------------------------------------------------------- transport velocity (R15)
+
+def _with_pb(sc, factor=1.0):
+    """The scene with the background pressure p_b = factor * p0 of its fluid."""
+    fl = [m for m in sc["materials"] if m["kind"] == 0][0]
+    sc["params"]["p_background"] = factor * fl["rho0"] * fl["c"] ** 2
+    return sc
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_background_acceleration_vanishes_on_a_regular_lattice(dim):
+    """The transport-velocity terms vanish for distributions with the kernel's partition of
+    unity (Sec. 3.3.2): on a periodic lattice a~ = 0 to rounding and the lattice stays at rest."""
+    sc = _with_pb(S.periodic_box(dim=dim, n=8 if dim == 3 else 16, dx=0.1, vel_amp=0.0, jitter=0.0))
+    o = O.OracleScene(sc)
+    fl = sc["materials"][0]
+    scale = fl["rho0"] * fl["c"] ** 2 / (fl["rho0"] * 0.1)  # p_b / (rho h)
+    assert np.abs(o.get("bacc")).max() < 1e-12 * scale
+    o.step(20)
+    assert np.abs(o.get("vel")).max() < 1e-12 * 10.0
+    assert np.abs(o.get("pos") - sc["particles"]["pos"]).max() < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_linear_momentum_conserved_with_transport_velocity(dim):
+    """1/2 (A_i + A_j) . grad W_ij is antisymmetric in i, j: total momentum stays exact."""
+    sc = _with_pb(S.periodic_box(dim=dim, n=10 if dim == 3 else 20, dx=0.1, bodies=2 if dim == 3 else 3,
+                                 body_radius=0.16, vel_amp=0.2, jitter=0.1, seed=4))
+    o = O.OracleScene(sc)
+    d0 = o.diagnostics()
+    scale = np.abs(sc["particles"]["mass"][:, None] * sc["particles"]["vel"]).sum()
+    for _ in range(5):
+        o.step(10)
+        d = o.diagnostics()
+        assert np.all(np.abs(d[:3] - d0[:3]) <= 1e-13 * scale), (d[:3], d0[:3])
+    assert np.abs(o.get("bacc")).max() > 0.0
+
+
+def _disorder(o, sc):
+    """Spread of the kernel sum sum_j V_j W_ij over fluid particles (0 on a lattice up to the
+    lattice constant): the partition-of-unity defect the background pressure reduces."""
+    rho, m = o.get("rho"), sc["particles"]["mass"]
+    return float(np.std(rho / m))
+
+
+def test_transport_velocity_regularises_a_disordered_distribution():
+    """The background pressure drives a disordered distribution towards the partition of
+    unity (Sec. 3.3.2): faster with p_b = p0 than without, faster still with 2 p0."""
+    base = S.periodic_box(dim=2, n=24, dx=0.1, vel_amp=0.0, jitter=0.3, eta=0.05, seed=9)
+    runs = {}
+    for pb in (0.0, 1.0, 2.0):
+        sc = _with_pb(copy.deepcopy(base), pb)
+        o = O.OracleScene(sc)
+        d0 = _disorder(o, sc)
+        o.step(100)
+        runs[pb] = _disorder(o, sc) / d0
+    assert runs[1.0] < 0.9 * runs[0.0] and runs[2.0] < 0.95 * runs[1.0], runs
+
+
+def test_couette_with_transport_velocity_keeps_the_linear_profile():
+    sc = _with_pb(S.couette2d())
+    tau = 0.2 ** 2 / (np.pi ** 2 * 0.1)
+    o = O.OracleScene(sc)
+    o.step(int(round(6 * tau / sc["params"]["dt_fixed"])))
+    x, v, fl = o.get("pos"), o.get("vel"), o.get("mat") == 0
+    assert np.abs(v[fl, 0] - x[fl, 1] / 0.2).max() < 5e-3
