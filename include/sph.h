@@ -79,10 +79,16 @@ typedef struct {
  *  cells_per_group  cells along x handled by one warp (0 = automatic; row-major only)
  *  body_capacity    maximum number of bodies including those created by solidification
  *                   (0: initial count + 1024)
- *  src_*            optional moving Gaussian surface heat source (not in the paper; see
- *                   the design notes): power density src_power, radius src_radius, centre
- *                   src_origin + src_speed t, acting within src_depth below src_ztop on
- *                   phases that take part in a transition. */
+ *  src_*            optional moving Gaussian surface heat source (not in the paper; a heat
+ *                   input for powder-bed scenes): power density src_power, radius
+ *                   src_radius, centre src_origin + src_speed t, acting within src_depth
+ *                   below src_ztop on phases that take part in a transition
+ *  p_background     background pressure p_b of the transport-velocity formulation that
+ *                   Sec. 3.3.2 applies (after Adami, Hu and Adams 2013): fluid particles
+ *                   are advected with u~ = u^{n+1/2} + dt/2 a~, a~_i = -(p_b / m_i)
+ *                   sum_j (V_i^2 + V_j^2) dW/dr e_ij, and the momentum equation gains
+ *                   (1/m_i) sum_j (V_i^2 + V_j^2) 1/2 (A_i + A_j) . e_ij dW/dr with
+ *                   A = rho u (u~ - u) (zero for wall and rigid particles).  0: off. */
 typedef struct {
   int32_t dim;
   double dx, h, kernel_support;
@@ -101,6 +107,7 @@ typedef struct {
   int32_t n_materials;
   const sph_material* materials;
   double src_power, src_radius, src_speed[3], src_origin[3], src_depth, src_ztop;
+  double p_background;
 } sph_params;
 
 /* Particles (Sec. 3.1.2: phase, position, velocity, mass, density, temperature, body).
@@ -160,7 +167,8 @@ enum {
   SPH_F_VEXT = 10, /* n*3 double: extrapolated velocity of wall and rigid particles */
   SPH_F_CELL = 11, /* n int32: row-major cell index cx + nx (cy + ny cz) */
   SPH_F_ENTH = 12, /* n double: specific enthalpy (enthalpy phases) */
-  SPH_F_COUNT = 13
+  SPH_F_BACC = 13, /* n*3 double: background acceleration a~ of fluid particles (p_background > 0) */
+  SPH_F_COUNT = 14
 };
 
 /* Copy fields to host.  original_order = 1 returns rows in input order, 0 in the

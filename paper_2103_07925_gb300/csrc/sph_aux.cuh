@@ -179,6 +179,12 @@ __global__ void k_export(Scene<R>* const* sc, ExportArgs a) {
     }
     if (a.fi[SPH_F_CELL]) a.fi[SPH_F_CELL][o] = key_lin(S, S.key[i]);
     if (a.f[SPH_F_ENTH]) a.f[SPH_F_ENTH][o] = S.P.H[i];
+    if (a.f[SPH_F_BACC]) {
+      bool b = S.tvf && kind == KFLUID;
+      a.f[SPH_F_BACC][3 * o] = b ? (double)S.P.bx[i] : 0.0;
+      a.f[SPH_F_BACC][3 * o + 1] = b ? (double)S.P.by[i] : 0.0;
+      a.f[SPH_F_BACC][3 * o + 2] = b ? (double)S.P.bz[i] : 0.0;
+    }
   }
 }
 

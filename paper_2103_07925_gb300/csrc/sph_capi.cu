@@ -202,7 +202,7 @@ static sph_status footprint_of(const sph_job_desc* job, int prec, size_t* bytes)
   if (trans) nr = n;
   EngineIface* e = make_engine(prec, p->dim);
   if (!e) { set_error("out of host memory"); return SPH_ERR_OOM; }
-  *bytes = e->footprint(n, nc, kcap < 1 ? 1 : kcap, nr < 1 ? 1 : nr, trans);
+  *bytes = e->footprint(n, nc, kcap < 1 ? 1 : kcap, nr < 1 ? 1 : nr, trans, p->p_background > 0.0);
   delete e;
   return SPH_OK;
 }

@@ -40,6 +40,9 @@ struct PBank {  // particle fields (one bank)
   R *ax, *ay, *az;     // fluid acceleration; rigid: kinematic acceleration used by Eq. R4
   R *rho, *T, *H, *m;  // density, temperature (walls: prescribed or NaN), enthalpy, mass
   int *mt, *body, *slot, *orig;  // material, body id, rigid slot, input index
+  // transport-velocity formulation (null when off): background acceleration a~ of the
+  // last evaluation and u~ - u of the current half step
+  R *bx, *by, *bz, *tx, *ty, *tz;
 };
 
 template <class R>
@@ -59,6 +62,9 @@ struct Scene {
   R kcR, dcR, dxR;
   double src_Q, src_r, src_v[3], src_x0[3], src_depth, src_ztop;
   int dt_mode, rebin_interval, has_transition, has_enthalpy, has_source, any_heat;
+  int tvf;             // transport-velocity formulation on (p_background > 0)
+  double pbg;          // background pressure p_b
+  R pbgR;
   double dt_fixed, dt_cond;  // dt_cond: min of the velocity-independent conditions
   double cmax;
   MatD mat[MAXMAT];
@@ -73,6 +79,7 @@ struct Scene {
   // pa = (x, y, z, rho), pb = (u or extrapolated v_w, p or p_w), pc = (T, V, material |
   // kind << 16, body)
   float4 *pa, *pb, *pc;
+  float4* pd;          // (u~ - u, 0) when the transport-velocity formulation is on
   int* nbl;            // neighbour lists: entry k of particle i at nbl[k * n + i] = j << 5 | cell code
   int* nbc;            // neighbour count of each particle (may exceed maxnb: then cells are scanned)
   R *xr, *yr, *zr;     // positions at the last list rebuild (same frame as the bank)

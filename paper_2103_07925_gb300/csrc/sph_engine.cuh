@@ -134,6 +134,9 @@ inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
     }
   }
   S.has_source = p->src_power > 0 ? 1 : 0;
+  S.pbg = p->p_background > 0.0 ? p->p_background : 0.0;
+  S.pbgR = (R)S.pbg;
+  S.tvf = S.pbg > 0.0 ? 1 : 0;
   if (S.has_source) S.any_heat = 1;
   S.src_Q = p->src_power; S.src_r = p->src_radius; S.src_depth = p->src_depth; S.src_ztop = p->src_ztop;
   for (int d = 0; d < 3; d++) { S.src_v[d] = p->src_speed[d]; S.src_x0[d] = p->src_origin[d]; }
@@ -211,7 +214,7 @@ class Engine {
   // grids of the sweeps and the search from the launch shape (0 waves: the occupancy limit)
   sph_status apply_launch() {
     int bs = 0, bw = 0;
-    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_force<R, DIM>, sweep_block, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_force<R, DIM, false>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, k_search<R, DIM>, 128, 0));
     bs = std::max(1, bs);
     bw = std::max(1, bw);
@@ -351,7 +354,7 @@ class Engine {
     return SPH_OK;
   }
 
-  static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans) {
+  static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans, bool tvf) {
     size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 9 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
                  (DIM == 3 ? 192 : 64) * sizeof(int) + (sizeof(R) == 4 ? 3 * sizeof(float4) : 0);
     size_t cells = (size_t)(ncells + 1) * 4 * sizeof(int) + (size_t)(ncells / 1024 + 2) * sizeof(int);
@@ -360,7 +363,9 @@ class Engine {
     // relabel scratch: offsets and forces in the new slot order, one root mark per particle
     size_t relabel = trans ? (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R)) + (size_t)n * sizeof(int) +
                                  (size_t)kcap * 2 * sizeof(int) : 0;
-    return per * (size_t)n + cells + bodies + slots + relabel + 4096;
+    // transport-velocity state: a~ and u~ - u in both banks, and the packed u~ - u (FP32)
+    size_t tv = tvf ? (size_t)n * (12 * sizeof(R) + (sizeof(R) == 4 ? sizeof(float4) : 0)) : 0;
+    return per * (size_t)n + cells + bodies + slots + relabel + tv + 4096;
   }
 
   // ---------------------------------------------------------------------------- create
@@ -539,11 +544,19 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     for (R** f : rf) SPH_TRY(A(f, (size_t)n));
     int** ifs[] = {&B->mt, &B->body, &B->slot, &B->orig};
     for (int** f : ifs) SPH_TRY(A(f, (size_t)n));
+    if (S.tvf) {
+      R** tf[] = {&B->bx, &B->by, &B->bz, &B->tx, &B->ty, &B->tz};
+      for (R** f : tf) {
+        SPH_TRY(A(f, (size_t)n));
+        SPH_CU(cudaMemsetAsync(*f, 0, sizeof(R) * n, stream));
+      }
+    }
   }
   R** rx[] = {&S.prs, &S.dT, &S.vex, &S.vey, &S.vez, &S.vol};
   for (R** f : rx) SPH_TRY(A(f, (size_t)n));
   if (sizeof(R) == 4)
     for (float4** f : {&S.pa, &S.pb, &S.pc}) SPH_TRY(A(f, (size_t)n));
+  if (sizeof(R) == 4 && S.tvf) SPH_TRY(A(&S.pd, (size_t)n));
   S.maxnb = list_capacity(DIM, (S.rc + S.skin) / S.dx);
   SPH_TRY(A(&S.nbl, (size_t)S.maxnb * n));
   SPH_TRY(A(&S.nbc, (size_t)n));
@@ -706,7 +719,8 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   int gsw = grid_for(n, sweep_block, grid_sweep);
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   k_extrap<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
-  k_force<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
+  if (S.tvf) k_force<R, DIM, true><<<gsw, sweep_block, 0, stream>>>(B);
+  else k_force<R, DIM, false><<<gsw, sweep_block, 0, stream>>>(B);
   if (meta[idx].K0 > 0) k_body_reduce<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
   SPH_CU(cudaGetLastError());
@@ -739,8 +753,9 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   int64_t np = h_pfx[ns], nc = h_pfx[(cap + 1) + ns], ng = h_pfx[2 * (cap + 1) + ns];
   int64_t nb = h_pfx[3 * (cap + 1) + ns], ncb = h_pfx[4 * (cap + 1) + ns];
   bool any_dt = false, any_body = false;
-  bool any_transition = false;
+  bool any_transition = false, any_tvf = false;
   for (int a : act) {
+    any_tvf |= hs[a].tvf != 0;
     any_dt |= hs[a].dt_mode == 1;
     any_body |= meta[a].K0 > 0 || hs[a].has_transition != 0;
     any_transition |= hs[a].has_transition != 0;
@@ -788,7 +803,8 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_extrap<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
   rec();
-  k_force<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
+  if (any_tvf) k_force<R, DIM, true><<<gsw, sweep_block, 0, stream>>>(B);
+  else k_force<R, DIM, false><<<gsw, sweep_block, 0, stream>>>(B);
   rec();
   if (any_body) { k_body_reduce<R><<<gb, 128, 0, stream>>>(B, 1); kcount++; }
   rec();
@@ -902,8 +918,8 @@ sph_status Engine<R, DIM>::read_fields(int idx, uint32_t mask, void* const* dst,
   if (!dst) { set_error("null destination array"); return SPH_ERR_INVALID; }
   const Scene<R>& S = hs[idx];
   size_t n = (size_t)S.n;
-  static const int comps[SPH_F_COUNT] = {3, 3, 3, 1, 1, 1, 1, 1, 1, 3, 3, 1, 1};
-  static const int isint[SPH_F_COUNT] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 0, 0, 1, 0};
+  static const int comps[SPH_F_COUNT] = {3, 3, 3, 1, 1, 1, 1, 1, 1, 3, 3, 1, 1, 3};
+  static const int isint[SPH_F_COUNT] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 0, 0, 1, 0, 0};
   size_t bytes = 0;
   for (int f = 0; f < SPH_F_COUNT; f++)
     if (mask & (1u << f)) {

@@ -267,14 +267,21 @@ __global__ void __launch_bounds__(256) k_kick_drift(BatchView<R> B) {
       R uy = S.P.vy[i] + half * S.P.ay[i];
       R uz = S.P.vz[i] + half * S.P.az[i];
       S.P.vx[i] = ux; S.P.vy[i] = uy; S.P.vz[i] = uz;
+      // transport-velocity formulation: advection with u~ = u^{n+1/2} + dt/2 a~^n
+      R wx = ux, wy = uy, wz = uz;
+      if (S.tvf) {
+        R tx = half * S.P.bx[i], ty = half * S.P.by[i], tz = half * S.P.bz[i];
+        S.P.tx[i] = tx; S.P.ty[i] = ty; S.P.tz[i] = tz;
+        wx = ux + tx; wy = uy + ty; wz = uz + tz;
+      }
       if (sizeof(R) == 8) {
-        double x[3] = {(double)S.P.px[i] + (double)dt * ux, (double)S.P.py[i] + (double)dt * uy,
-                       (double)S.P.pz[i] + (double)dt * uz};
+        double x[3] = {(double)S.P.px[i] + (double)dt * wx, (double)S.P.py[i] + (double)dt * wy,
+                       (double)S.P.pz[i] + (double)dt * wz};
         store_pos<R>(S, i, x);
       } else {
-        S.P.px[i] = S.P.px[i] + dt * ux;
-        S.P.py[i] = S.P.py[i] + dt * uy;
-        S.P.pz[i] = S.P.pz[i] + dt * uz;
+        S.P.px[i] = S.P.px[i] + dt * wx;
+        S.P.py[i] = S.P.py[i] + dt * wy;
+        S.P.pz[i] = S.P.pz[i] + dt * wz;
       }
     } else if (kind == KRIGID) {
       int k = S.P.body[i], sl = S.P.slot[i];
@@ -569,6 +576,10 @@ __global__ void k_permute(BatchView<R> B, int force) {
     Q.ax[j] = P.ax[i]; Q.ay[j] = P.ay[i]; Q.az[j] = P.az[i];
     Q.rho[j] = P.rho[i]; Q.T[j] = P.T[i]; Q.H[j] = P.H[i]; Q.m[j] = P.m[i];
     Q.mt[j] = P.mt[i];
+    if (S.tvf) {
+      Q.bx[j] = P.bx[i]; Q.by[j] = P.by[i]; Q.bz[j] = P.bz[i];
+      Q.tx[j] = P.tx[i]; Q.ty[j] = P.ty[i]; Q.tz[j] = P.tz[i];
+    }
     int b = P.body[i], sl = P.slot[i], o = P.orig[i];
     Q.body[j] = b; Q.slot[j] = sl; Q.orig[j] = o;
     S.key[j] = S.tkey[i];

@@ -212,6 +212,10 @@ __global__ void k_rl_apply(BatchView<R> B) {
       S.P.mt[i] = S.mat[S.P.mt[i]].to;
       S.P.body[i] = -1;
       S.P.slot[i] = -1;
+      if (S.tvf) {  // a new fluid particle starts with a~ = 0
+        S.P.bx[i] = R(0); S.P.by[i] = R(0); S.P.bz[i] = R(0);
+        S.P.tx[i] = R(0); S.P.ty[i] = R(0); S.P.tz[i] = R(0);
+      }
       atomicAdd(&S.status[9], 1);
       S.status[10] = 1;
     } else if (f == 2) {

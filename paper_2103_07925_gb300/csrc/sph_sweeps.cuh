@@ -45,6 +45,7 @@ __device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p,
       S.pa[i].w = rho;
     S.pb[i] = make_float4(S.P.vx[i], S.P.vy[i], S.P.vz[i], p);
     S.pc[i] = make_float4(S.P.T[i], vol, __int_as_float(mt | (S.matR[mt].kind << 16)), __int_as_float(S.P.body[i]));
+    if (S.tvf) S.pd[i] = make_float4(S.P.tx[i], S.P.ty[i], S.P.tz[i], 0.f);
   }
 }
 
@@ -344,10 +345,12 @@ struct Target {
   const MatR<R>* M;
   R rho, p, V2, eta, kap, T;
   R u[3], ve[3];
+  R tv[3];   // u~ - u (transport-velocity formulation)
+  R bs[3];   // sum_j (V_i^2 + V_j^2) dW/dr e_ij of the background acceleration
 };
 
-template <class R, int DIM>
-__device__ __forceinline__ void force_pair(const Scene<R>& S, const Target<R>& t, int j, const R* d, R r2,
+template <class R, int DIM, bool TVF>
+__device__ __forceinline__ void force_pair(const Scene<R>& S, Target<R>& t, int j, const R* d, R r2,
                                            R* acc, R& heat) {
   const MatR<R>& Bm = S.matR[S.P.mt[j]];
   int bk = Bm.kind;
@@ -386,6 +389,15 @@ __device__ __forceinline__ void force_pair(const Scene<R>& S, const Target<R>& t
     acc[0] += coef * (-pt * ex + vis * (t.u[0] - uj[0]));
     acc[1] += coef * (-pt * ey + vis * (t.u[1] - uj[1]));
     acc[2] += coef * (-pt * ez + vis * (t.u[2] - uj[2]));
+    if (TVF && S.tvf) {  // 1/2 (A_i + A_j) . e_ij with A = rho u (u~ - u), zero for boundaries
+      R si = t.tv[0] * ex + t.tv[1] * ey + t.tv[2] * ez;
+      R sj = bk == KFLUID ? S.P.tx[j] * ex + S.P.ty[j] * ey + S.P.tz[j] * ez : R(0);
+      R rj = bk == KFLUID ? rhoj : R(0);
+      acc[0] += coef * R(0.5) * (t.rho * t.u[0] * si + rj * uj[0] * sj);
+      acc[1] += coef * R(0.5) * (t.rho * t.u[1] * si + rj * uj[1] * sj);
+      acc[2] += coef * R(0.5) * (t.rho * t.u[2] * si + rj * uj[2] * sj);
+      t.bs[0] += coef * ex; t.bs[1] += coef * ey; t.bs[2] += coef * ez;
+    }
   } else if (bk == KFLUID) {  // rigid target: -m_j a_jr seen from fluid particle j
     R rhoj = S.P.rho[j], pj = S.prs[j];
     R rs = Bm.rho0 * (t.p * Bm.inv_p0 + R(1));
@@ -395,6 +407,12 @@ __device__ __forceinline__ void force_pair(const Scene<R>& S, const Target<R>& t
     acc[0] -= coef * (pt * ex + vis * (S.P.vx[j] - t.ve[0]));
     acc[1] -= coef * (pt * ey + vis * (S.P.vy[j] - t.ve[1]));
     acc[2] -= coef * (pt * ez + vis * (S.P.vz[j] - t.ve[2]));
+    if (TVF && S.tvf) {  // the A_j term of a_jr (A = 0 for the rigid particle)
+      R sj = S.P.tx[j] * ex + S.P.ty[j] * ey + S.P.tz[j] * ez;
+      acc[0] += coef * R(0.5) * rhoj * S.P.vx[j] * sj;
+      acc[1] += coef * R(0.5) * rhoj * S.P.vy[j] * sj;
+      acc[2] += coef * R(0.5) * rhoj * S.P.vz[j] * sj;
+    }
   } else if (bk == KWALL || S.P.body[j] != t.body) {
     if (r < S.dxR) {  // Eq. contactforce with tension cut-off
       R ev = ex * (t.u[0] - S.P.vx[j]) + ey * (t.u[1] - S.P.vy[j]) + ez * (t.u[2] - S.P.vz[j]);
@@ -406,8 +424,8 @@ __device__ __forceinline__ void force_pair(const Scene<R>& S, const Target<R>& t
 }
 
 // force_pair on packed FP32 neighbour records (same arithmetic in the same order)
-template <int DIM>
-__device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const Target<float>& t, int j, const float* d,
+template <int DIM, bool TVF>
+__device__ __forceinline__ void force_pair_packed(const Scene<float>& S, Target<float>& t, int j, const float* d,
                                                   float r2, float4 a, float4 b, float4 c, float* acc, float& heat) {
   int mk = __float_as_int(c.z);
   int bk = mk >> 16;
@@ -443,6 +461,18 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const T
     acc[0] += coef * (-pt * ex + vis * (t.u[0] - b.x));
     acc[1] += coef * (-pt * ey + vis * (t.u[1] - b.y));
     acc[2] += coef * (-pt * ez + vis * (t.u[2] - b.z));
+    if (TVF && S.tvf) {  // 1/2 (A_i + A_j) . e_ij with A = rho u (u~ - u), zero for boundaries
+      float si = t.tv[0] * ex + t.tv[1] * ey + t.tv[2] * ez, sj = 0.f, rj = 0.f;
+      if (bk == KFLUID) {
+        float4 w = S.pd[j];
+        sj = w.x * ex + w.y * ey + w.z * ez;
+        rj = rhoj;
+      }
+      acc[0] += coef * 0.5f * (t.rho * t.u[0] * si + rj * b.x * sj);
+      acc[1] += coef * 0.5f * (t.rho * t.u[1] * si + rj * b.y * sj);
+      acc[2] += coef * 0.5f * (t.rho * t.u[2] * si + rj * b.z * sj);
+      t.bs[0] += coef * ex; t.bs[1] += coef * ey; t.bs[2] += coef * ez;
+    }
   } else if (bk == KFLUID) {  // rigid target: -m_j a_jr seen from fluid particle j
     float rhoj = a.w, pj = b.w;
     float rs = Bm.rho0 * (t.p * Bm.inv_p0 + 1.f);
@@ -452,6 +482,13 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const T
     acc[0] -= coef * (pt * ex + vis * (b.x - t.ve[0]));
     acc[1] -= coef * (pt * ey + vis * (b.y - t.ve[1]));
     acc[2] -= coef * (pt * ez + vis * (b.z - t.ve[2]));
+    if (TVF && S.tvf) {  // the A_j term of a_jr (A = 0 for the rigid particle)
+      float4 w = S.pd[j];
+      float sj = w.x * ex + w.y * ey + w.z * ez;
+      acc[0] += coef * 0.5f * rhoj * b.x * sj;
+      acc[1] += coef * 0.5f * rhoj * b.y * sj;
+      acc[2] += coef * 0.5f * rhoj * b.z * sj;
+    }
   } else if (bk == KWALL || __float_as_int(c.w) != t.body) {
     if (r < S.dxR) {  // Eq. contactforce with tension cut-off (particle velocities, not v_w)
       float ev = ex * (t.u[0] - S.P.vx[j]) + ey * (t.u[1] - S.P.vy[j]) + ez * (t.u[2] - S.P.vz[j]);
@@ -472,8 +509,10 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const T
 #define SPH_FORCE_MIN_BLOCKS 4
 #endif
 
-template <class R, int DIM>
-__global__ void __launch_bounds__(256, SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R> B) {
+// TVF: instantiation with the transport-velocity terms (launched when a resident scene
+// uses them; the plain instantiation keeps its register budget)
+template <class R, int DIM, bool TVF>
+__global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
   int nthr = gridDim.x * blockDim.x;
   // uniform trip count so that the warp-wide pair counter sees every lane
@@ -499,6 +538,9 @@ __global__ void __launch_bounds__(256, SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R
       t.T = S.P.T[i];
       t.u[0] = S.P.vx[i]; t.u[1] = S.P.vy[i]; t.u[2] = S.P.vz[i];
       t.ve[0] = S.vex[i]; t.ve[1] = S.vey[i]; t.ve[2] = S.vez[i];
+      t.tv[0] = t.tv[1] = t.tv[2] = R(0);
+      t.bs[0] = t.bs[1] = t.bs[2] = R(0);
+      if (TVF && S.tvf && kind == KFLUID) { t.tv[0] = S.P.tx[i]; t.tv[1] = S.P.ty[i]; t.tv[2] = S.P.tz[i]; }
       R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
       R acc[3] = {R(0), R(0), R(0)}, heat = R(0);
       auto visit = [&](int j, int code) {
@@ -509,7 +551,7 @@ __global__ void __launch_bounds__(256, SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R
           R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
           if (r2 < S.rc2R) {
             float4 b = S.pb[j], c = S.pc[j];
-            force_pair_packed<DIM>(S, t, j, d, r2, a, b, c, acc, heat);
+            force_pair_packed<DIM, TVF>(S, t, j, d, r2, a, b, c, acc, heat);
             npairs++;
           }
         } else {
@@ -517,7 +559,7 @@ __global__ void __launch_bounds__(256, SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R
           list_delta<R, DIM>(S, ti, j, code, d);
           R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
           if (r2 < S.rc2R) {
-            force_pair<R, DIM>(S, t, j, d, r2, acc, heat);
+            force_pair<R, DIM, TVF>(S, t, j, d, r2, acc, heat);
             npairs++;
           }
         }
@@ -545,7 +587,7 @@ __global__ void __launch_bounds__(256, SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R
 #if !SPH_FORCE_SPECULATE
               float4 b = S.pb[j], c = S.pc[j];
 #endif
-              force_pair_packed<DIM>(S, t, j, d, r2, a, b, c, acc, heat);
+              force_pair_packed<DIM, TVF>(S, t, j, d, r2, a, b, c, acc, heat);
               npairs++;
             }
             e = en;
@@ -563,6 +605,10 @@ __global__ void __launch_bounds__(256, SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R
         S.P.ax[i] = S.gR[0] + acc[0] * im;
         S.P.ay[i] = S.gR[1] + acc[1] * im;
         S.P.az[i] = S.gR[2] + acc[2] * im;
+        if (TVF && S.tvf) {  // a~_i = -(p_b / m_i) sum_j (V_i^2 + V_j^2) dW/dr e_ij
+          R c = -S.pbgR * im;
+          S.P.bx[i] = c * t.bs[0]; S.P.by[i] = c * t.bs[1]; S.P.bz[i] = c * t.bs[2];
+        }
       } else {
         int sl = S.P.slot[i];
         S.fr[3 * sl] = acc[0];

@@ -17,8 +17,8 @@ LIB_PATH = os.path.join(HERE, "libsph.so")
 
 FLUID, RIGID, WALL = 0, 1, 2
 FIELDS = dict(pos=0, vel=1, acc=2, rho=3, pres=4, temp=5, dtemp=6, mat=7, body=8, force=9,
-              vext=10, cell=11, enth=12)
-_VEC = {"pos", "vel", "acc", "force", "vext"}
+              vext=10, cell=11, enth=12, bacc=13)
+_VEC = {"pos", "vel", "acc", "force", "vext", "bacc"}
 _INT = {"mat", "body", "cell"}
 STATUS = {0: "SPH_OK", -1: "SPH_ERR_INVALID", -2: "SPH_ERR_OOM", -3: "SPH_ERR_CUDA",
           -4: "SPH_ERR_NONFINITE", -5: "SPH_ERR_TIMEOUT", -6: "SPH_ERR_CAPACITY"}
@@ -53,7 +53,7 @@ class Params(C.Structure):
                 ("body_capacity", C.c_int32), ("n_materials", C.c_int32),
                 ("materials", C.POINTER(Material)), ("src_power", C.c_double), ("src_radius", C.c_double),
                 ("src_speed", C.c_double * 3), ("src_origin", C.c_double * 3), ("src_depth", C.c_double),
-                ("src_ztop", C.c_double)]
+                ("src_ztop", C.c_double), ("p_background", C.c_double)]
 
 
 class ParticlesIn(C.Structure):
@@ -161,6 +161,7 @@ class _Inputs:
                   "precision", "skin", "rebin_interval", "key_order", "cells_per_group", "body_capacity",
                   "src_power", "src_radius", "src_depth", "src_ztop"):
             setattr(P, k, p[k])
+        P.p_background = p.get("p_background", 0.0)
         for d in range(3):
             P.box_min[d] = p["box_min"][d]
             P.box_max[d] = p["box_max"][d]
@@ -225,7 +226,7 @@ class Scene:
         for nm in names:
             if nm not in out:
                 out[nm] = _alloc_field(nm, self.n)
-        dst = (C.c_void_p * 13)()
+        dst = (C.c_void_p * len(FIELDS))()
         mask = 0
         for nm, a in out.items():
             f = FIELDS[nm]
@@ -235,7 +236,7 @@ class Scene:
         return out if len(names) != 1 else out[names[0]]
 
     def write(self, pos=None, vel=None, temp=None):
-        src = (C.c_void_p * 13)()
+        src = (C.c_void_p * len(FIELDS))()
         mask = 0
         keep = []
         for nm, a in (("pos", pos), ("vel", vel), ("temp", temp)):
@@ -370,7 +371,7 @@ class Batch:
     def read(self, job_id, *names):
         n = self._n[job_id]
         out = {nm: _alloc_field(nm, n) for nm in names}
-        dst = (C.c_void_p * 13)()
+        dst = (C.c_void_p * len(FIELDS))()
         mask = 0
         for nm, a in out.items():
             dst[FIELDS[nm]] = a.ctypes.data
