@@ -52,6 +52,9 @@ def parse():
                     help="tank3d: the 1.28M-particle tank (default); powder: the 2.1M-particle powder "
                          "bed with melting grains; batch: 256 mixed scenes in one batch; serve: Poisson "
                          "job arrivals served by continuous batching")
+    ap.add_argument("--p-background", type=float, default=0.0,
+                    help="tank/powder: background pressure of the transport-velocity formulation, in "
+                         "units of p0 = rho0 c^2 of the first fluid (the paper's examples use 1); 0: off")
     ap.add_argument("--scenes", type=int, default=256, help="batch: number of scenes")
     ap.add_argument("--jobs", type=int, default=32, help="serve: number of jobs")
     ap.add_argument("--job-steps", type=int, default=1000, help="serve: steps per job")
@@ -356,6 +359,9 @@ def main():
     hbm, smmax, peak_src = peaks()
     dx = args.dx or DEFAULT_DX[args.workload]
     sc = workload(dx, args.workload)
+    if args.p_background > 0:
+        fl = [m for m in sc["materials"] if m["kind"] == 0][0]
+        sc["params"]["p_background"] = args.p_background * fl["rho0"] * fl["c"] ** 2
     stream = torch.cuda.Stream()
     # cell layout and launch shape: the autotuner's pick on this workload (steps 30-60 from
     # the initial state), or the command-line layout with --no-tune
@@ -412,6 +418,7 @@ def main():
                       "particles": info["n"], "fluid": info["n_fluid"], "rigid": info["n_rigid"],
                       "wall": info["n_wall"], "bodies": info["n_bodies"], "cells": info["n_cells"],
                       "precision": "FP32 pair sums, FP64 bodies" if args.precision == 32 else "FP64",
+                      "p_background_over_p0": args.p_background,
                       "key_order": "morton" if layout["key_order"] == 0 else "row-major",
                       "cells_per_group": layout.get("cells_per_group", 0),
                       "skin_h": layout["skin"] / sc["params"]["h"],
@@ -426,7 +433,8 @@ def main():
            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                         "frac": achieved_tf / peak_tf,
                         "traffic": K_FORCE_TRAFFIC.get((layout["key_order"], round(layout["skin"] / sc["params"]["h"], 3)))
-                        if (args.workload == "tank3d" and dx == 0.01 and args.precision == 32) else None,
+                        if (args.workload == "tank3d" and dx == 0.01 and args.precision == 32
+                            and args.p_background == 0) else None,
                         "kernel": "k_force",
                         "peak_source": "FP32 FMA lanes x SMs x 2 x max SM clock (%s clocks)" % peak_src,
                         "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": hbm, "frac": hbm_ach / hbm,
