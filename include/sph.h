@@ -47,13 +47,24 @@ typedef enum {
  * temperature crosses T_transition (Sec. 3.6): a rigid phase melts above it, a fluid
  * phase solidifies below it.  latent_heat > 0 switches that pair of phases to the
  * enthalpy form of the apparent-capacity extension named in the paper's remark on
- * latent heat, with a mushy interval of width mushy_width around T_transition. */
+ * latent heat, with a mushy interval of width mushy_width around T_transition.
+ *
+ * Concentration (the paper's remark on chemically induced transitions): every fluid and
+ * rigid phase carries a concentration C with dC/dt = (1/rho) div(D grad C), discretised
+ * as the heat equation of Sec. 3.5 (Cleary and Monaghan) with diffusivity D in place of
+ * kappa and no capacity; wall particles do not take part.  C_fixed (not NaN) holds the
+ * concentration of a phase at that value at all times (a reservoir, the gastric juice of
+ * Sec. 4.5).  transition_by = 1 makes transitions_to fire when the concentration crosses
+ * C_transition instead of the temperature crossing T_transition (a rigid phase turns
+ * fluid above it, a fluid phase turns rigid below it). */
 typedef struct {
   int32_t kind;
   double rho0, c, eta, cp, kappa;
   double T_transition;
   int32_t transitions_to;
   double latent_heat, mushy_width;
+  double diffusivity, C_transition, C_fixed;
+  int32_t transition_by;  /* 0: temperature, 1: concentration */
 } sph_material;
 
 /* Scene parameters.
@@ -118,12 +129,15 @@ typedef struct {
  *  body             body id of rigid particles (0 .. k-1), ignored otherwise
  *  wall_velocity    prescribed velocity of wall particles (nullable: zero)
  *  wall_temperature prescribed (Dirichlet) temperature of wall particles, NaN =
- *                   adiabatic (nullable: all adiabatic) */
+ *                   adiabatic (nullable: all adiabatic)
+ *  concentration    initial concentration C (nullable: zero; phases with C_fixed start
+ *                   at C_fixed) */
 typedef struct {
   int64_t n;
   const double *pos, *vel, *mass, *density, *temperature;
   const int32_t *material, *body;
   const double *wall_velocity, *wall_temperature;
+  const double* concentration;
 } sph_particles_in;
 
 /* Rigid bodies (Sec. 3.4).  Mass, centre of mass and inertia are always derived from
@@ -168,7 +182,9 @@ enum {
   SPH_F_CELL = 11, /* n int32: row-major cell index cx + nx (cy + ny cz) */
   SPH_F_ENTH = 12, /* n double: specific enthalpy (enthalpy phases) */
   SPH_F_BACC = 13, /* n*3 double: background acceleration a~ of fluid particles (p_background > 0) */
-  SPH_F_COUNT = 14
+  SPH_F_CONC = 14, /* n double: concentration (walls: 0) */
+  SPH_F_DCONC = 15, /* n double: dC/dt of the last evaluation */
+  SPH_F_COUNT = 16
 };
 
 /* Copy fields to host.  original_order = 1 returns rows in input order, 0 in the

@@ -17,7 +17,7 @@ _lib = None
 
 ORC_MAXMAT = 32
 FIELDS = dict(pos=0, vel=1, acc=2, rho=3, pres=4, temp=5, dtemp=6, mat=7, body=8, force=9,
-              vext=10, cell=11, enth=12, bacc=13)
+              vext=10, cell=11, enth=12, bacc=13, conc=14, dconc=15)
 _VEC = {"pos", "vel", "acc", "force", "vext", "bacc"}
 _INT = {"mat", "body", "cell"}
 
@@ -26,7 +26,8 @@ class _Mat(C.Structure):
     _fields_ = [("kind", C.c_int32), ("rho0", C.c_double), ("c", C.c_double), ("eta", C.c_double),
                 ("cp", C.c_double), ("kappa", C.c_double), ("T_transition", C.c_double),
                 ("transitions_to", C.c_int32), ("latent_heat", C.c_double),
-                ("mushy_width", C.c_double)]
+                ("mushy_width", C.c_double), ("diffusivity", C.c_double), ("C_transition", C.c_double),
+                ("C_fixed", C.c_double), ("transition_by", C.c_int32)]
 
 
 class _Params(C.Structure):
@@ -51,7 +52,7 @@ def lib():
         lp = C.POINTER(C.c_int64)
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [C.POINTER(_Params), C.c_int64, dp, dp, dp, dp, dp, ip, ip, dp, dp,
-                                 C.c_int32, dp, dp, dp]
+                                 C.c_int32, dp, dp, dp, dp]
         L.orc_error.restype = C.c_char_p
         L.orc_step.argtypes = [C.c_void_p, C.c_int32]
         L.orc_step.restype = C.c_int
@@ -109,6 +110,10 @@ def _params(scene, force_brute=False):
         for k in ("kind", "rho0", "c", "eta", "cp", "kappa", "T_transition", "transitions_to",
                   "latent_heat", "mushy_width"):
             setattr(M, k, m[k])
+        M.diffusivity = m.get("diffusivity", 0.0)
+        M.C_transition = m.get("C_transition", float("nan"))
+        M.C_fixed = m.get("C_fixed", float("nan"))
+        M.transition_by = m.get("transition_by", 0)
     P.body_capacity = p.get("body_capacity", 0)
     P.src_power = p["src_power"]
     P.src_radius = p["src_radius"]
@@ -131,12 +136,15 @@ class OracleScene:
                       ("pos", "vel", "mass", "density", "temperature", "wall_velocity", "wall_temperature")]
         self._keep += [np.ascontiguousarray(pt[k], dtype=np.int32) for k in ("material", "body")]
         self._keep += [np.ascontiguousarray(bd[k], dtype=np.float64).reshape(-1) for k in ("quat", "vel", "omega")]
-        pos, vel, mass, dens, temp, wv, wt, mat, body, q, bv, bw = self._keep
+        conc = np.ascontiguousarray(pt["concentration"] if "concentration" in pt else np.zeros(len(pt["mass"])),
+                                    dtype=np.float64)
+        self._keep.append(conc)
+        pos, vel, mass, dens, temp, wv, wt, mat, body, q, bv, bw, conc = self._keep
         self.n = len(mass)
         self.P = _params(scene, force_brute)
         k = len(bd["quat"])
         h = L.orc_create(C.byref(self.P), self.n, _dp(pos), _dp(vel), _dp(mass), _dp(dens), _dp(temp),
-                         _ip(mat), _ip(body), _dp(wv), _dp(wt), k, _dp(q), _dp(bv), _dp(bw))
+                         _ip(mat), _ip(body), _dp(wv), _dp(wt), k, _dp(q), _dp(bv), _dp(bw), _dp(conc))
         if not h:
             raise RuntimeError(L.orc_error().decode())
         self.h = h

@@ -78,6 +78,13 @@
  *      Pins: a~ = 0 on a regular lattice, exact momentum with the A term (antisymmetry),
  *      regularisation growing with p_b, Couette profile; the overall sign of the A term
  *      follows Adami et al. and is pinned only through these (parity partially unpinned).
+ *  R16 concentration (the remark on chemically induced transitions): fluid and rigid
+ *      particles carry C with dC_a/dt = (1/rho_a) sum_b V_b 4 D_a D_b / (D_a + D_b)
+ *      (C_a - C_b) / r_ab dW/dr, the form of the heat equation of Sec. 3.5 with the
+ *      diffusivity in place of kappa and no capacity; wall particles do not take part.  A
+ *      phase with a fixed concentration (not NaN) keeps it at all times and acts as a
+ *      reservoir.  A phase with transition_by = 1 changes phase when C crosses C_transition
+ *      (rigid above, fluid below), evaluated with the temperature rule at the step's end.
  */
 #include "sph_oracle.h"
 
@@ -102,6 +109,7 @@ struct orc_scene {
   int64_t n;
   double *x, *u, *a, *rho, *p, *T, *dT, *m, *H, *vext, *f, *rb, *wu, *wT;
   double *ab, *tv; /* R15: background acceleration a~ and u~ - u of the current half step */
+  double *C, *dC;  /* R16: concentration and its rate */
   int tvf;
   int32_t *mat, *body;
   /* bodies */
@@ -617,6 +625,29 @@ static void heat_rates(orc_scene* s, double t) {
   }
 }
 
+/* R16: dC/dt of fluid and rigid particles (walls do not take part) */
+static void conc_rates(orc_scene* s) {
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t a = 0; a < s->n; a++) {
+    const orc_material* A = M(s, a);
+    if (A->kind == ORC_WALL) { s->dC[a] = 0.0; continue; }
+    double Ca = s->C[a], Da = A->diffusivity, sum = 0.0;
+    for (int64_t q = s->nstart[a]; q < s->nstart[a + 1]; q++) {
+      int64_t b = s->nlist[q];
+      const orc_material* B = M(s, b);
+      if (B->kind == ORC_WALL) continue;
+      double Db = B->diffusivity;
+      double Dab = (Da + Db > 0.0) ? 4.0 * Da * Db / (Da + Db) : 0.0;
+      double d[3];
+      min_image(s, &s->x[3 * a], &s->x[3 * b], d);
+      double r = sqrt(norm2(s, d));
+      double Vb = s->m[b] / s->rho[b];
+      sum += Vb * Dab * (Ca - s->C[b]) / r * dwij(s, r);
+    }
+    s->dC[a] = sum / s->rho[a];
+  }
+}
+
 /* one pair term (V_i^2 + V_j^2)[-p~ dW e + eta~ u_ij / r dW] seen from fluid particle i (R5) */
 static void pair_term(const orc_scene* s, int64_t i, int64_t j, double* out) {
   const orc_material* A = M(s, i);
@@ -783,6 +814,7 @@ static int evaluate(orc_scene* s, double t) {
   density_eos(s);
   extrapolate(s);
   heat_rates(s, t);
+  conc_rates(s);
   forces(s);
   body_accelerations(s);
   return 0;
@@ -866,8 +898,10 @@ static int relabel(orc_scene* s) {
     const orc_material* A = M(s, i);
     if (A->transitions_to < 0) continue;
     double Ti = uses_enthalpy(s, s->mat[i]) ? T_of_H(s, s->mat[i], s->H[i]) : s->T[i];
-    if (A->kind == ORC_RIGID && Ti > A->T_transition) { flag[i] = 1; nflag++; }
-    else if (A->kind == ORC_FLUID && Ti < A->T_transition) { flag[i] = 2; nflag++; }
+    double v = A->transition_by == 1 ? s->C[i] : Ti;              /* R16 */
+    double vt = A->transition_by == 1 ? A->C_transition : A->T_transition;
+    if (A->kind == ORC_RIGID && v > vt) { flag[i] = 1; nflag++; }
+    else if (A->kind == ORC_FLUID && v < vt) { flag[i] = 2; nflag++; }
   }
   if (!nflag) { free(flag); return 0; }
   int8_t* changed = (int8_t*)calloc((size_t)s->Kcap, 1);
@@ -993,7 +1027,7 @@ orc_scene* orc_create(const orc_params* P, int64_t n, const double* pos, const d
                       const double* mass, const double* density, const double* temperature,
                       const int32_t* material, const int32_t* body, const double* wall_velocity,
                       const double* wall_temperature, int32_t k, const double* quat,
-                      const double* bvel, const double* bomega) {
+                      const double* bvel, const double* bomega, const double* concentration) {
   if (P->dim != 2 && P->dim != 3) { set_err("oracle: dim must be 2 or 3"); return NULL; }
   if (P->n_materials < 1 || P->n_materials > ORC_MAXMAT) { set_err("oracle: bad material count"); return NULL; }
   for (int q = 0; q < P->n_materials; q++) {
@@ -1023,6 +1057,8 @@ orc_scene* orc_create(const orc_params* P, int64_t n, const double* pos, const d
   s->vext = dalloc(3 * n); s->f = dalloc(3 * n); s->rb = dalloc(3 * n); s->wu = dalloc(3 * n);
   s->wT = dalloc(n);
   s->ab = dalloc(3 * n); s->tv = dalloc(3 * n);
+  s->C = dalloc(n); s->dC = dalloc(n);
+  if (concentration) memcpy(s->C, concentration, sizeof(double) * (size_t)n);
   s->tvf = P->p_background > 0.0;
   s->mat = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
   s->body = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
@@ -1043,6 +1079,8 @@ orc_scene* orc_create(const orc_params* P, int64_t n, const double* pos, const d
     if (M(s, i)->kind != ORC_RIGID) s->body[i] = -1;
     wrap(s, &s->x[3 * i]);
     if (uses_enthalpy(s, s->mat[i])) s->H[i] = H_of_T(s, s->mat[i], s->T[i]);
+    if (M(s, i)->kind == ORC_WALL) s->C[i] = 0.0;
+    else if (!isnan(M(s, i)->C_fixed)) s->C[i] = M(s, i)->C_fixed;
   }
   /* bodies */
   s->K = k;
@@ -1146,6 +1184,11 @@ static int step_once(orc_scene* s) {
       s->T[i] = s->T[i] + dt * s->dT[i];
     }
   }
+  /* concentration update (R16): reservoirs keep their value */
+  for (int64_t i = 0; i < n; i++) {
+    if (is_kind(s, i, ORC_WALL)) continue;
+    s->C[i] = isnan(M(s, i)->C_fixed) ? s->C[i] + dt * s->dC[i] : M(s, i)->C_fixed;
+  }
   /* final kick */
   for (int64_t i = 0; i < n; i++) {
     if (!is_kind(s, i, ORC_FLUID)) continue;
@@ -1204,6 +1247,8 @@ void orc_get(orc_scene* s, int32_t field, void* out) {
         for (int q = 0; q < 3; q++) d[3 * i + q] = is_kind(s, i, ORC_FLUID) ? 0.0 : s->vext[3 * i + q];
       break;
     case ORC_F_ENTH: memcpy(d, s->H, sizeof(double) * (size_t)n); break;
+    case ORC_F_CONC: memcpy(d, s->C, sizeof(double) * (size_t)n); break;
+    case ORC_F_DCONC: memcpy(d, s->dC, sizeof(double) * (size_t)n); break;
     case ORC_F_BACC: /* R15: background acceleration a~ of fluid particles */
       for (int64_t i = 0; i < n; i++)
         for (int q = 0; q < 3; q++) d[3 * i + q] = is_kind(s, i, ORC_FLUID) ? s->ab[3 * i + q] : 0.0;
@@ -1292,7 +1337,7 @@ void orc_destroy(orc_scene* s) {
   if (!s) return;
   double* arrs[] = {s->x, s->u, s->a, s->rho, s->p, s->T, s->dT, s->m, s->H, s->vext, s->f, s->rb,
                     s->wu, s->wT, s->bm, s->br, s->bq, s->bu, s->bw, s->ba, s->bal, s->bf, s->bt,
-                    s->bIb, s->bIw, s->ab, s->tv};
+                    s->bIb, s->bIw, s->ab, s->tv, s->C, s->dC};
   for (size_t q = 0; q < sizeof arrs / sizeof arrs[0]; q++) free(arrs[q]);
   free(s->mat); free(s->body); free(s->alive); free(s->nstart); free(s->nlist);
   free(s);

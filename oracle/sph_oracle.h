@@ -32,6 +32,8 @@ typedef struct {
   double T_transition;
   int32_t transitions_to;
   double latent_heat, mushy_width;
+  double diffusivity, C_transition, C_fixed; /* concentration (R16) */
+  int32_t transition_by;                     /* 0 temperature, 1 concentration */
 } orc_material;
 
 typedef struct {
@@ -57,14 +59,14 @@ typedef struct orc_scene orc_scene;
 /* field ids for orc_get */
 enum {
   ORC_F_POS = 0, ORC_F_VEL, ORC_F_ACC, ORC_F_RHO, ORC_F_PRES, ORC_F_TEMP, ORC_F_DTEMP,
-  ORC_F_MAT, ORC_F_BODY, ORC_F_FORCE, ORC_F_VEXT, ORC_F_CELL, ORC_F_ENTH, ORC_F_BACC
+  ORC_F_MAT, ORC_F_BODY, ORC_F_FORCE, ORC_F_VEXT, ORC_F_CELL, ORC_F_ENTH, ORC_F_BACC, ORC_F_CONC, ORC_F_DCONC
 };
 
 orc_scene* orc_create(const orc_params* P, int64_t n, const double* pos, const double* vel,
                       const double* mass, const double* density, const double* temperature,
                       const int32_t* material, const int32_t* body, const double* wall_velocity,
                       const double* wall_temperature, int32_t k, const double* quat,
-                      const double* bvel, const double* bomega);
+                      const double* bvel, const double* bomega, const double* concentration);
 const char* orc_error(void);
 int orc_step(orc_scene* s, int32_t nsteps);
 void orc_get(orc_scene* s, int32_t field, void* out);

@@ -29,12 +29,15 @@ NAN = float("nan")
 
 
 def material(kind, rho0, c=0.0, eta=0.0, cp=1.0, kappa=0.0,
-             T_transition=NAN, transitions_to=-1, latent_heat=0.0, mushy_width=0.0):
-    """One material (phase) record; ``eta`` is the dynamic viscosity rho0*nu."""
+             T_transition=NAN, transitions_to=-1, latent_heat=0.0, mushy_width=0.0,
+             diffusivity=0.0, C_transition=NAN, C_fixed=NAN, transition_by=0):
+    """One material (phase) record; ``eta`` is the dynamic viscosity rho0*nu; the
+    concentration fields follow the paper's remark on chemically induced transitions."""
     return dict(kind=int(kind), rho0=float(rho0), c=float(c), eta=float(eta), cp=float(cp),
                 kappa=float(kappa), T_transition=float(T_transition),
                 transitions_to=int(transitions_to), latent_heat=float(latent_heat),
-                mushy_width=float(mushy_width))
+                mushy_width=float(mushy_width), diffusivity=float(diffusivity),
+                C_transition=float(C_transition), C_fixed=float(C_fixed), transition_by=int(transition_by))
 
 
 def default_params(dim, dx, box_min, box_max, **kw):
@@ -101,7 +104,7 @@ class _Builder:
         self.parts = []  # list of dict chunks
         self.bodies = []
 
-    def add(self, pos, mat, mass, density, T, body=-1, vel=None, wall_T=NAN, wall_vel=None):
+    def add(self, pos, mat, mass, density, T, body=-1, vel=None, wall_T=NAN, wall_vel=None, conc=0.0):
         pos = np.asarray(pos, dtype=np.float64)
         if pos.ndim == 1:
             pos = pos.reshape(1, -1)
@@ -115,7 +118,8 @@ class _Builder:
                   material=np.full(n, int(mat), dtype=np.int32),
                   body=np.full(n, int(body), dtype=np.int32) if np.isscalar(body) else np.asarray(body, np.int32),
                   wall_velocity=np.zeros((n, 3)) if wall_vel is None else np.broadcast_to(np.asarray(wall_vel, float), (n, 3)).copy(),
-                  wall_temperature=np.full(n, float(wall_T)) if np.isscalar(wall_T) else np.asarray(wall_T, float))
+                  wall_temperature=np.full(n, float(wall_T)) if np.isscalar(wall_T) else np.asarray(wall_T, float),
+                  concentration=np.full(n, float(conc)) if np.isscalar(conc) else np.asarray(conc, float))
         self.parts.append(ch)
         return n
 
@@ -125,8 +129,8 @@ class _Builder:
 
     def finish(self, params, materials):
         keys = ["pos", "vel", "mass", "density", "temperature", "material", "body",
-                "wall_velocity", "wall_temperature"]
-        parts = {k: np.concatenate([c[k] for c in self.parts], axis=0) for k in keys}
+                "wall_velocity", "wall_temperature", "concentration"]
+        parts = {k: np.concatenate([c.get(k, np.zeros(len(c["mass"]))) for c in self.parts], axis=0) for k in keys}
         parts["material"] = parts["material"].astype(np.int32)
         parts["body"] = parts["body"].astype(np.int32)
         k = len(self.bodies)
@@ -687,3 +691,59 @@ def couette2d(dx=0.01, width=0.1, height=0.2, U=1.0, c=10.0, rho0=1.0, nu=0.1, j
     p = default_params(2, dx, [0.0, -3 * dx], [nx * dx, (ny + 3) * dx], periodic=[1, 0, 0],
                        dt_mode=0, dt_fixed=dt, precision=precision)
     return b.finish(p, mats)
+
+
+# --------------------------------------------------------------------------- concentration
+
+def gastric2d(dx=0.1, width=8.0, height=4.0, n_boluses=6, d_range=(1.0, 1.6), seed=11, c=50.0,
+              nu_juice=1.0, nu_chyme=2.0, D_juice=1.0, D_bolus=0.25, D_chyme=0.25, C_t=0.8,
+              p_background=0.0, dt=None, precision=64):
+    """Food boluses in gastric juice (the shape of Sec. 4.5, without its moving constriction):
+    a closed 2D box of juice (fluid, concentration held at 1), rigid boluses (C = 0 at
+    start) that turn into chyme (fluid) where their concentration exceeds C_t, all of
+    density 1.  Defaults are scaled down from the paper's 40 x 16 box and 60 boluses."""
+    rng = np.random.default_rng(seed)
+    nx, ny = int(round(width / dx)), int(round(height / dx))
+    sites = lattice([0.0, 0.0], [nx, ny], dx)
+    owner = np.full(len(sites), -1, dtype=np.int64)
+    centers, radii = [], []
+    tries = 0
+    while len(centers) < n_boluses and tries < 20000:
+        tries += 1
+        r = 0.5 * rng.uniform(*d_range)
+        cpos = np.array([rng.uniform(r + 2 * dx, nx * dx - r - 2 * dx), rng.uniform(r + 2 * dx, ny * dx - r - 2 * dx)])
+        if all(np.linalg.norm(cpos - c2) >= r + r2 + 2 * dx for c2, r2 in zip(centers, radii)):
+            centers.append(cpos)
+            radii.append(r)
+    for k, (cc, r) in enumerate(zip(centers, radii)):
+        owner[np.sum((sites - cc) ** 2, axis=1) <= r * r] = k
+    mats = [material(FLUID, 1.0, c=c, eta=nu_juice, diffusivity=D_juice, C_fixed=1.0),
+            material(WALL, 1.0),
+            material(RIGID, 1.0, diffusivity=D_bolus, C_transition=C_t, transitions_to=3, transition_by=1),
+            material(FLUID, 1.0, c=c, eta=nu_chyme, diffusivity=D_chyme)]
+    b = _Builder(2)
+    b.add(_pad3(sites[owner < 0]), 0, dx * dx, 1.0, 300.0, conc=1.0)
+    for k in range(len(centers)):
+        kb = b.add_body()
+        b.add(sites[owner == k], 2, dx * dx, 1.0, 300.0, body=kb, conc=0.0)
+    b.add(wall_shell(2, [nx, ny], dx, 3), 1, dx * dx, 1.0, 300.0)
+    if dt is None:
+        dt = min(0.25 * dx / c, 0.125 * dx * dx / max(nu_juice, nu_chyme), 0.1 * dx * dx / max(D_juice, D_bolus))
+    p = default_params(2, dx, [-3 * dx, -3 * dx], [(nx + 3) * dx, (ny + 3) * dx], dt_mode=0, dt_fixed=dt,
+                       precision=precision, p_background=p_background, body_capacity=len(centers) + 64)
+    return b.finish(p, mats)
+
+
+def conc_slab(dim=2, n=(48, 8), dx=1.0 / 48, C0=0.5, A=0.2, D=1.0, rho0=1.0, c=1.0, precision=64, dt=None):
+    """Periodic fluid lattice at rest, C = C0 + A sin(2 pi x / Lx): 1D diffusion check."""
+    sites = lattice([0.0] * dim, list(n), dx)
+    Lx = n[0] * dx
+    C = C0 + A * np.sin(2 * np.pi * sites[:, 0] / Lx)
+    b = _Builder(dim)
+    b.add(_pad3(sites), 0, rho0 * dx ** dim, rho0, 300.0, conc=C)
+    L = [n[d] * dx for d in range(dim)]
+    if dt is None:
+        dt = 0.05 * rho0 * dx * dx / D
+    p = default_params(dim, dx, [0.0] * dim, L, periodic=[1] * dim + [0] * (3 - dim), dt_mode=0, dt_fixed=dt,
+                       precision=precision)
+    return b.finish(p, [material(FLUID, rho0, c=c, diffusivity=D)])

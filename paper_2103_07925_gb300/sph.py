@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libsph.so")
 
 FLUID, RIGID, WALL = 0, 1, 2
 FIELDS = dict(pos=0, vel=1, acc=2, rho=3, pres=4, temp=5, dtemp=6, mat=7, body=8, force=9,
-              vext=10, cell=11, enth=12, bacc=13)
+              vext=10, cell=11, enth=12, bacc=13, conc=14, dconc=15)
 _VEC = {"pos", "vel", "acc", "force", "vext", "bacc"}
 _INT = {"mat", "body", "cell"}
 STATUS = {0: "SPH_OK", -1: "SPH_ERR_INVALID", -2: "SPH_ERR_OOM", -3: "SPH_ERR_CUDA",
@@ -41,7 +41,9 @@ class SphError(RuntimeError):
 class Material(C.Structure):
     _fields_ = [("kind", C.c_int32), ("rho0", C.c_double), ("c", C.c_double), ("eta", C.c_double),
                 ("cp", C.c_double), ("kappa", C.c_double), ("T_transition", C.c_double),
-                ("transitions_to", C.c_int32), ("latent_heat", C.c_double), ("mushy_width", C.c_double)]
+                ("transitions_to", C.c_int32), ("latent_heat", C.c_double), ("mushy_width", C.c_double),
+                ("diffusivity", C.c_double), ("C_transition", C.c_double), ("C_fixed", C.c_double),
+                ("transition_by", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -59,7 +61,8 @@ class Params(C.Structure):
 class ParticlesIn(C.Structure):
     _fields_ = [("n", C.c_int64), ("pos", C.c_void_p), ("vel", C.c_void_p), ("mass", C.c_void_p),
                 ("density", C.c_void_p), ("temperature", C.c_void_p), ("material", C.c_void_p),
-                ("body", C.c_void_p), ("wall_velocity", C.c_void_p), ("wall_temperature", C.c_void_p)]
+                ("body", C.c_void_p), ("wall_velocity", C.c_void_p), ("wall_temperature", C.c_void_p),
+                ("concentration", C.c_void_p)]
 
 
 class BodiesIn(C.Structure):
@@ -156,6 +159,10 @@ class _Inputs:
             for k in ("kind", "rho0", "c", "eta", "cp", "kappa", "T_transition", "transitions_to",
                       "latent_heat", "mushy_width"):
                 setattr(self.mats[q], k, m[k])
+            self.mats[q].diffusivity = m.get("diffusivity", 0.0)
+            self.mats[q].C_transition = m.get("C_transition", float("nan"))
+            self.mats[q].C_fixed = m.get("C_fixed", float("nan"))
+            self.mats[q].transition_by = m.get("transition_by", 0)
         P = Params()
         for k in ("dim", "dx", "h", "kernel_support", "dt_mode", "dt_fixed", "k_contact", "d_contact",
                   "precision", "skin", "rebin_interval", "key_order", "cells_per_group", "body_capacity",
@@ -175,6 +182,8 @@ class _Inputs:
         pt = scene["particles"]
         self.keep = {k: _arr(pt[k], np.float64) for k in
                      ("pos", "vel", "mass", "density", "temperature", "wall_velocity", "wall_temperature")}
+        if "concentration" in pt:
+            self.keep["concentration"] = _arr(pt["concentration"], np.float64)
         self.keep["material"] = _arr(pt["material"], np.int32)
         self.keep["body"] = _arr(pt["body"], np.int32)
         n = len(self.keep["mass"])

@@ -608,3 +608,58 @@ def test_couette_with_transport_velocity_keeps_the_linear_profile():
     o.step(int(round(6 * tau / sc["params"]["dt_fixed"])))
     x, v, fl = o.get("pos"), o.get("vel"), o.get("mat") == 0
     assert np.abs(v[fl, 0] - x[fl, 1] / 0.2).max() < 5e-3
+
+
+# --------------------------------------------------------------------------- concentration (R16)
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_concentration_sine_decay(dim):
+    """C = C0 + A sin(k x) on a periodic lattice at rest decays as exp(-D k^2 t / rho)."""
+    n = (48, 8) if dim == 2 else (48, 8, 8)
+    sc = S.conc_slab(dim=dim, n=n, D=1.0)
+    o = O.OracleScene(sc)
+    rho = o.get("rho").mean()
+    x = sc["particles"]["pos"][:, 0]
+    k = 2 * math.pi
+    o.step(400)
+    t = 400 * sc["params"]["dt_fixed"]
+    A = 2 * np.mean((o.get("conc") - 0.5) * np.sin(k * x))
+    assert abs(A / (0.2 * math.exp(-k * k * t / rho)) - 1) < 1e-2
+
+
+def test_concentration_sum_conserved_in_a_closed_box():
+    sc = S.periodic_box(dim=3, n=10, dx=0.1, bodies=2, body_radius=0.2, vel_amp=0.1, jitter=0.1, seed=3)
+    rng = np.random.default_rng(1)
+    sc["particles"]["concentration"] = rng.uniform(0, 1, len(sc["particles"]["mass"]))
+    for m in sc["materials"]:
+        m["diffusivity"] = 0.5
+    o = O.OracleScene(sc)
+    m = sc["particles"]["mass"]
+    s0 = np.sum(m * o.get("conc"))
+    o.step(50)
+    assert abs(np.sum(m * o.get("conc")) - s0) < 1e-13 * s0
+    assert np.std(o.get("conc")) < np.std(sc["particles"]["concentration"])
+
+
+def test_reservoir_bounds_and_concentration_driven_transition():
+    """Juice held at C = 1 around boluses at C = 0: the concentration stays in [0, 1], rises
+    in the boluses from their surface inwards, and bolus particles above C_t turn into chyme."""
+    sc = S.gastric2d(dx=0.1, n_boluses=3)
+    o = O.OracleScene(sc)
+    mat0 = o.get("mat").copy()
+    n_bolus = int(np.sum(mat0 == 2))
+    nsteps = 0
+    for _ in range(40):
+        o.step(50)
+        nsteps += 50
+        C = o.get("conc")
+        assert C.min() >= -1e-12 and C.max() <= 1 + 1e-12
+        if np.sum(o.get("mat") == 3) > 0:
+            break
+    mat = o.get("mat")
+    chyme = mat == 3
+    assert chyme.any(), "no bolus particle reached C_t"
+    assert np.all(mat0[chyme] == 2)                      # chyme comes from boluses only
+    assert np.all(o.get("conc")[chyme] > 0.0)
+    assert np.sum(mat == 2) == n_bolus - int(chyme.sum())
+    assert np.all(o.get("body")[chyme] == -1)
