@@ -11,6 +11,7 @@ namespace sph {
 struct ImportArgs {
   const double *pos, *vel, *mass, *dens, *temp, *wvel, *wtemp;
   const int *mat, *body, *slot;
+  const double* conc;  // nullable: zero
 };
 
 // specific enthalpy of the apparent-capacity extension (H = 0 at T_t - w/2)
@@ -67,6 +68,12 @@ __global__ void k_import(Scene<R>* const* sc, ImportArgs a) {
     S.P.m[i] = (R)a.mass[i];
     S.P.rho[i] = (R)a.dens[i];
     S.P.mt[i] = mt;
+    if (S.any_conc) {  // walls carry none; reservoir phases start at their fixed value
+      double c = a.conc ? a.conc[i] : 0.0;
+      if (kind == KWALL) c = 0.0;
+      else if (!isnan(S.mat[mt].Cfix)) c = S.mat[mt].Cfix;
+      S.P.C[i] = (R)c;
+    }
     S.P.body[i] = kind == KRIGID ? a.body[i] : -1;
     S.P.slot[i] = a.slot[i];
     S.P.orig[i] = i;
@@ -179,6 +186,8 @@ __global__ void k_export(Scene<R>* const* sc, ExportArgs a) {
     }
     if (a.fi[SPH_F_CELL]) a.fi[SPH_F_CELL][o] = key_lin(S, S.key[i]);
     if (a.f[SPH_F_ENTH]) a.f[SPH_F_ENTH][o] = S.P.H[i];
+    if (a.f[SPH_F_CONC]) a.f[SPH_F_CONC][o] = S.any_conc ? (double)S.P.C[i] : 0.0;
+    if (a.f[SPH_F_DCONC]) a.f[SPH_F_DCONC][o] = (S.any_conc && kind != KWALL) ? (double)S.dC[i] : 0.0;
     if (a.f[SPH_F_BACC]) {
       bool b = S.tvf && kind == KFLUID;
       a.f[SPH_F_BACC][3 * o] = b ? (double)S.P.bx[i] : 0.0;

@@ -25,12 +25,15 @@ enum { KFLUID = 0, KRIGID = 1, KWALL = 2 };
 struct MatD {  // material constants, FP64
   int kind, to, enth, src;
   double rho0, c, eta, cp, kappa, Tt, L, w, p0;
+  int tby;              // transition driven by 0 temperature, 1 concentration
+  double D, Ct, Cfix;   // diffusivity, transition concentration, fixed concentration (NaN: free)
 };
 
 template <class R>
 struct MatR {  // material constants in the working precision (pair sums)
   int kind, enth;
   R rho0, c2, eta, cp, kappa, inv_p0;
+  R D;                  // diffusivity of the concentration
 };
 
 template <class R>
@@ -43,6 +46,7 @@ struct PBank {  // particle fields (one bank)
   // transport-velocity formulation (null when off): background acceleration a~ of the
   // last evaluation and u~ - u of the current half step
   R *bx, *by, *bz, *tx, *ty, *tz;
+  R* C;                 // concentration (null when no phase carries one)
 };
 
 template <class R>
@@ -63,6 +67,7 @@ struct Scene {
   double src_Q, src_r, src_v[3], src_x0[3], src_depth, src_ztop;
   int dt_mode, rebin_interval, has_transition, has_enthalpy, has_source, any_heat;
   int tvf;             // transport-velocity formulation on (p_background > 0)
+  int any_conc;        // some phase diffuses, holds or transitions on a concentration
   double pbg;          // background pressure p_b
   R pbgR;
   double dt_fixed, dt_cond;  // dt_cond: min of the velocity-independent conditions
@@ -72,6 +77,7 @@ struct Scene {
   // ---------------------------------------------------------------- particles
   PBank<R> P, Q;       // current and alternate bank
   R *prs, *dT;         // pressure, rate (not permuted: recomputed every evaluation)
+  R* dC;               // dC/dt of the last evaluation (when any_conc)
   R *vex, *vey, *vez;  // extrapolated velocity of wall and rigid particles
   R* vol;              // particle volume m / rho of the current evaluation
   // FP32 scenes: what a pair sweep gathers from a neighbour, packed per particle after the
@@ -79,7 +85,7 @@ struct Scene {
   // pa = (x, y, z, rho), pb = (u or extrapolated v_w, p or p_w), pc = (T, V, material |
   // kind << 16, body)
   float4 *pa, *pb, *pc;
-  float4* pd;          // (u~ - u, 0) when the transport-velocity formulation is on
+  float4* pd;          // (u~ - u, C): transport-velocity formulation and concentration
   int* nbl;            // neighbour lists: entry k of particle i at nbl[k * n + i] = j << 5 | cell code
   int* nbc;            // neighbour count of each particle (may exceed maxnb: then cells are scanned)
   R *xr, *yr, *zr;     // positions at the last list rebuild (same frame as the bank)

@@ -100,6 +100,7 @@ inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
   S.nmat = p->n_materials;
   S.has_transition = S.has_enthalpy = 0;
   S.any_heat = 0;
+  S.any_conc = 0;
   S.cmax = 0.0;
   double numax = 0.0, cond = INFINITY;
   for (int q = 0; q < p->n_materials; q++) {
@@ -118,8 +119,11 @@ inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
     D.kind = m.kind; D.to = m.transitions_to; D.enth = m.latent_heat > 0; D.src = m.transitions_to >= 0;
     D.rho0 = m.rho0; D.c = m.c; D.eta = m.eta; D.cp = m.cp; D.kappa = m.kappa; D.Tt = m.T_transition;
     D.L = m.latent_heat; D.w = m.mushy_width; D.p0 = m.rho0 * m.c * m.c;
+    D.tby = m.transition_by; D.D = m.diffusivity; D.Ct = m.C_transition; D.Cfix = m.C_fixed;
+    if (m.diffusivity > 0.0 || m.transition_by == 1 || !std::isnan(m.C_fixed)) S.any_conc = 1;
     MatR<R>& A = S.matR[q];
     A.kind = m.kind; A.enth = D.enth;
+    A.D = (R)m.diffusivity;
     A.rho0 = (R)m.rho0; A.c2 = (R)(m.c * m.c); A.eta = (R)m.eta; A.cp = (R)m.cp; A.kappa = (R)m.kappa;
     A.inv_p0 = D.p0 > 0 ? (R)(1.0 / D.p0) : R(0);
     if (D.enth) S.has_enthalpy = 1;
@@ -544,6 +548,7 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     for (R** f : rf) SPH_TRY(A(f, (size_t)n));
     int** ifs[] = {&B->mt, &B->body, &B->slot, &B->orig};
     for (int** f : ifs) SPH_TRY(A(f, (size_t)n));
+    if (S.any_conc) SPH_TRY(A(&B->C, (size_t)n));
     if (S.tvf) {
       R** tf[] = {&B->bx, &B->by, &B->bz, &B->tx, &B->ty, &B->tz};
       for (R** f : tf) {
@@ -556,7 +561,11 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   for (R** f : rx) SPH_TRY(A(f, (size_t)n));
   if (sizeof(R) == 4)
     for (float4** f : {&S.pa, &S.pb, &S.pc}) SPH_TRY(A(f, (size_t)n));
-  if (sizeof(R) == 4 && S.tvf) SPH_TRY(A(&S.pd, (size_t)n));
+  if (sizeof(R) == 4 && (S.tvf || S.any_conc)) SPH_TRY(A(&S.pd, (size_t)n));
+  if (S.any_conc) {
+    SPH_TRY(A(&S.dC, (size_t)n));
+    SPH_CU(cudaMemsetAsync(S.dC, 0, sizeof(R) * n, stream));
+  }
   S.maxnb = list_capacity(DIM, (S.rc + S.skin) / S.dx);
   SPH_TRY(A(&S.nbl, (size_t)S.maxnb * n));
   SPH_TRY(A(&S.nbc, (size_t)n));
@@ -653,7 +662,7 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   // raw inputs -> staging -> k_import
   {
     size_t nd = (size_t)n;
-    size_t doubles = nd * (3 + 3 + 1 + 1 + 1 + 3 + 1);
+    size_t doubles = nd * (3 + 3 + 1 + 1 + 1 + 3 + 1 + 1);
     size_t ints = nd * 3;
     char* stg = nullptr;
     SPH_CU(cudaMallocAsync((void**)&stg, doubles * 8 + ints * 4 + 64, stream));
@@ -664,7 +673,8 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     double* dtemp = ddens + nd;
     double* dwv = dtemp + nd;
     double* dwt = dwv + 3 * nd;
-    int* dmat = (int*)(dwt + nd);
+    double* dconc = dwt + nd;
+    int* dmat = (int*)(dconc + nd);
     int* dbody = dmat + nd;
     int* dslot = dbody + nd;
     cudaMemcpyAsync(dpos, in->pos, 24 * nd, cudaMemcpyHostToDevice, stream);
@@ -674,12 +684,13 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     cudaMemcpyAsync(dtemp, in->temperature, 8 * nd, cudaMemcpyHostToDevice, stream);
     if (in->wall_velocity) cudaMemcpyAsync(dwv, in->wall_velocity, 24 * nd, cudaMemcpyHostToDevice, stream);
     if (in->wall_temperature) cudaMemcpyAsync(dwt, in->wall_temperature, 8 * nd, cudaMemcpyHostToDevice, stream);
+    if (in->concentration) cudaMemcpyAsync(dconc, in->concentration, 8 * nd, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(dmat, in->material, 4 * nd, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(dbody, in->body, 4 * nd, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(dslot, slot.data(), 4 * nd, cudaMemcpyHostToDevice, stream);
     SPH_CU(cudaMemcpyAsync(dself, &S, sizeof(S), cudaMemcpyHostToDevice, stream));
     ImportArgs ia{dpos, dvel, dmass, ddens, dtemp, in->wall_velocity ? dwv : nullptr,
-                  in->wall_temperature ? dwt : nullptr, dmat, dbody, dslot};
+                  in->wall_temperature ? dwt : nullptr, dmat, dbody, dslot, in->concentration ? dconc : nullptr};
     k_import<R><<<grid_for(n, 256, sms * 8), 256, 0, stream>>>(S.self, ia);
     SPH_CU(cudaGetLastError());
     SPH_CU(cudaFreeAsync(stg, stream));
@@ -719,7 +730,7 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   int gsw = grid_for(n, sweep_block, grid_sweep);
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   k_extrap<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
-  if (S.tvf) k_force<R, DIM, true><<<gsw, sweep_block, 0, stream>>>(B);
+  if (S.tvf || S.any_conc) k_force<R, DIM, true><<<gsw, sweep_block, 0, stream>>>(B);
   else k_force<R, DIM, false><<<gsw, sweep_block, 0, stream>>>(B);
   if (meta[idx].K0 > 0) k_body_reduce<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
@@ -755,7 +766,7 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   bool any_dt = false, any_body = false;
   bool any_transition = false, any_tvf = false;
   for (int a : act) {
-    any_tvf |= hs[a].tvf != 0;
+    any_tvf |= hs[a].tvf != 0 || hs[a].any_conc != 0;
     any_dt |= hs[a].dt_mode == 1;
     any_body |= meta[a].K0 > 0 || hs[a].has_transition != 0;
     any_transition |= hs[a].has_transition != 0;
@@ -918,8 +929,8 @@ sph_status Engine<R, DIM>::read_fields(int idx, uint32_t mask, void* const* dst,
   if (!dst) { set_error("null destination array"); return SPH_ERR_INVALID; }
   const Scene<R>& S = hs[idx];
   size_t n = (size_t)S.n;
-  static const int comps[SPH_F_COUNT] = {3, 3, 3, 1, 1, 1, 1, 1, 1, 3, 3, 1, 1, 3};
-  static const int isint[SPH_F_COUNT] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 0, 0, 1, 0, 0};
+  static const int comps[SPH_F_COUNT] = {3, 3, 3, 1, 1, 1, 1, 1, 1, 3, 3, 1, 1, 3, 1, 1};
+  static const int isint[SPH_F_COUNT] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 0, 0, 1, 0, 0, 0, 0};
   size_t bytes = 0;
   for (int f = 0; f < SPH_F_COUNT; f++)
     if (mask & (1u << f)) {

@@ -576,6 +576,7 @@ __global__ void k_permute(BatchView<R> B, int force) {
     Q.ax[j] = P.ax[i]; Q.ay[j] = P.ay[i]; Q.az[j] = P.az[i];
     Q.rho[j] = P.rho[i]; Q.T[j] = P.T[i]; Q.H[j] = P.H[i]; Q.m[j] = P.m[i];
     Q.mt[j] = P.mt[i];
+    if (S.any_conc) Q.C[j] = P.C[i];
     if (S.tvf) {
       Q.bx[j] = P.bx[i]; Q.by[j] = P.by[i]; Q.bz[j] = P.bz[i];
       Q.tx[j] = P.tx[i]; Q.ty[j] = P.ty[i]; Q.tz[j] = P.tz[i];
@@ -832,6 +833,10 @@ __global__ void k_final(BatchView<R> B) {
       S.P.T[i] = (R)T;
     } else {
       S.P.T[i] = S.P.T[i] + dt * S.dT[i];
+    }
+    if (S.any_conc) {  // concentration; reservoir phases keep their fixed value
+      double cf = S.mat[S.P.mt[i]].Cfix;
+      S.P.C[i] = isnan(cf) ? S.P.C[i] + dt * S.dC[i] : (R)cf;
     }
     if (A.kind == KFLUID) {
       R half = R(0.5) * dt;

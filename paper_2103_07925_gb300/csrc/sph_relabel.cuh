@@ -54,10 +54,11 @@ __global__ void k_rl_flag(BatchView<R> B) {
     int i = g - __ldg(B.pfx_part + s);
     const MatD& M = S.mat[S.P.mt[i]];
     int f = 0;
-    if (M.to >= 0) {
-      double T = (double)S.P.T[i];
-      if (M.kind == KRIGID && T > M.Tt) f = 1;
-      else if (M.kind == KFLUID && T < M.Tt) f = 2;
+    if (M.to >= 0) {  // temperature, or the concentration for phases that transition on it
+      double v = M.tby == 1 ? (double)S.P.C[i] : (double)S.P.T[i];
+      double vt = M.tby == 1 ? M.Ct : M.Tt;
+      if (M.kind == KRIGID && v > vt) f = 1;
+      else if (M.kind == KFLUID && v < vt) f = 2;
     }
     S.tloc[i] = f;
     if (f) atomicAdd(&S.status[1], 1);

@@ -45,7 +45,9 @@ __device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p,
       S.pa[i].w = rho;
     S.pb[i] = make_float4(S.P.vx[i], S.P.vy[i], S.P.vz[i], p);
     S.pc[i] = make_float4(S.P.T[i], vol, __int_as_float(mt | (S.matR[mt].kind << 16)), __int_as_float(S.P.body[i]));
-    if (S.tvf) S.pd[i] = make_float4(S.P.tx[i], S.P.ty[i], S.P.tz[i], 0.f);
+    if (S.tvf || S.any_conc)
+      S.pd[i] = make_float4(S.tvf ? S.P.tx[i] : 0.f, S.tvf ? S.P.ty[i] : 0.f, S.tvf ? S.P.tz[i] : 0.f,
+                            S.any_conc ? S.P.C[i] : 0.f);
   }
 }
 
@@ -347,6 +349,8 @@ struct Target {
   R u[3], ve[3];
   R tv[3];   // u~ - u (transport-velocity formulation)
   R bs[3];   // sum_j (V_i^2 + V_j^2) dW/dr e_ij of the background acceleration
+  R C, D;    // concentration and diffusivity
+  R cs;      // sum_j V_j D_ij (C_i - C_j) / r dW/dr
 };
 
 template <class R, int DIM, bool TVF>
@@ -368,6 +372,11 @@ __device__ __forceinline__ void force_pair(const Scene<R>& S, Target<R>& t, int 
       R kab = ks > R(0) ? qdiv<R>(R(4) * t.kap * kb, ks) : R(0);
       heat += Vj * kab * (t.T - Tb) * inv_r * dW;
     }
+  }
+  if (TVF && S.any_conc && bk != KWALL) {  // concentration: the heat form with the diffusivity
+    R Db = Bm.D, Ds = t.D + Db;
+    R Dab = Ds > R(0) ? qdiv<R>(R(4) * t.D * Db, Ds) : R(0);
+    t.cs += Vj * Dab * (t.C - S.P.C[j]) * inv_r * dW;
   }
   if (t.kind == KFLUID) {
     R rhoj, pj, etaj, uj[3];
@@ -444,6 +453,11 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, Target<
       heat += Vj * kab * (t.T - Tb) * inv_r * dW;
     }
   }
+  if (TVF && S.any_conc && bk != KWALL) {  // concentration: the heat form with the diffusivity
+    float Db = Bm.D, Ds = t.D + Db;
+    float Dab = Ds > 0.f ? qdiv<float>(4.f * t.D * Db, Ds) : 0.f;
+    t.cs += Vj * Dab * (t.C - S.pd[j].w) * inv_r * dW;
+  }
   if (t.kind == KFLUID) {
     float rhoj, pj = b.w, etaj;
     if (bk == KFLUID) {
@@ -509,8 +523,8 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, Target<
 #define SPH_FORCE_MIN_BLOCKS 4
 #endif
 
-// TVF: instantiation with the transport-velocity terms (launched when a resident scene
-// uses them; the plain instantiation keeps its register budget)
+// TVF: instantiation with the transport-velocity and concentration terms (launched when
+// a resident scene uses either; the plain instantiation keeps its register budget)
 template <class R, int DIM, bool TVF>
 __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
@@ -541,6 +555,8 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
       t.tv[0] = t.tv[1] = t.tv[2] = R(0);
       t.bs[0] = t.bs[1] = t.bs[2] = R(0);
       if (TVF && S.tvf && kind == KFLUID) { t.tv[0] = S.P.tx[i]; t.tv[1] = S.P.ty[i]; t.tv[2] = S.P.tz[i]; }
+      t.C = t.D = t.cs = R(0);
+      if (TVF && S.any_conc) { t.C = S.P.C[i]; t.D = t.M->D; }
       R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
       R acc[3] = {R(0), R(0), R(0)}, heat = R(0);
       auto visit = [&](int j, int code) {
@@ -615,6 +631,7 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
         S.fr[3 * sl + 1] = acc[1];
         S.fr[3 * sl + 2] = acc[2];
       }
+      if (TVF && S.any_conc) S.dC[i] = t.cs / t.rho;
       R rate = heat / t.rho;  // c_p dT/dt = dH/dt
       if (S.has_source && S.mat[tm].src) {
         double x[3];
