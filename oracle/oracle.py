@@ -53,6 +53,8 @@ def lib():
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [C.POINTER(_Params), C.c_int64, dp, dp, dp, dp, dp, ip, ip, dp, dp,
                                  C.c_int32, dp, dp, dp, dp]
+        L.orc_interpolate.argtypes = [C.c_void_p, C.c_int64, dp, C.c_int32, C.c_uint32, dp]
+        L.orc_interpolate.restype = C.c_int
         L.orc_error.restype = C.c_char_p
         L.orc_step.argtypes = [C.c_void_p, C.c_int32]
         L.orc_step.restype = C.c_int
@@ -183,6 +185,16 @@ class OracleScene:
         lst = np.empty(max(tot, 1), dtype=np.int32)
         lib().orc_neighbors(self.h, counts.ctypes.data_as(C.POINTER(C.c_int64)), _ip(lst), tot)
         return counts, lst[:tot]
+
+    def interpolate(self, query, field, material_mask=0xFFFFFFFF):
+        """Shepard-filtered field (Eq. postprocessing) at query points (nq x 3)."""
+        q = np.ascontiguousarray(query, dtype=np.float64).reshape(-1, 3)
+        comps = 3 if field == "vel" else 1
+        out = np.empty((len(q), comps))
+        rc = lib().orc_interpolate(self.h, len(q), _dp(q), FIELDS[field], C.c_uint32(material_mask), _dp(out))
+        if rc:
+            raise ValueError("field %s cannot be interpolated" % field)
+        return out if comps == 3 else out[:, 0]
 
     def diagnostics(self):
         out = np.empty(16)

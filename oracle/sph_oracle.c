@@ -1333,6 +1333,44 @@ void orc_diagnostics(orc_scene* s, double out[16]) {
   out[15] = s->pairs_force;
 }
 
+/* ------------------------------------------------------------------ post-processing (Eq. postprocessing) */
+
+int orc_interpolate(orc_scene* s, int64_t nq, const double* query, int32_t field, uint32_t material_mask,
+                    double* out) {
+  int comps = field == ORC_F_VEL ? 3 : 1;
+  if (field != ORC_F_VEL && field != ORC_F_RHO && field != ORC_F_PRES && field != ORC_F_TEMP &&
+      field != ORC_F_CONC)
+    return -1;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t q = 0; q < nq; q++) {
+    double xq[3] = {query[3 * q], query[3 * q + 1], s->P.dim == 3 ? query[3 * q + 2] : 0.0};
+    wrap(s, xq);
+    double num[3] = {0, 0, 0}, den = 0.0;
+    for (int64_t j = 0; j < s->n; j++) {
+      if (!((material_mask >> s->mat[j]) & 1u)) continue;
+      double d[3];
+      min_image(s, xq, &s->x[3 * j], d);
+      double r2 = norm2(s, d);
+      if (!(r2 < s->rc2)) continue;
+      double w = wij(s, sqrt(r2)) * s->m[j] / s->rho[j];
+      den += w;
+      double f[3] = {0, 0, 0};
+      switch (field) {
+        case ORC_F_VEL:
+          for (int k = 0; k < 3; k++) f[k] = is_kind(s, j, ORC_WALL) ? s->wu[3 * j + k] : s->u[3 * j + k];
+          break;
+        case ORC_F_RHO: f[0] = s->rho[j]; break;
+        case ORC_F_PRES: f[0] = s->p[j]; break;
+        case ORC_F_TEMP: f[0] = is_kind(s, j, ORC_WALL) ? s->wT[j] : s->T[j]; break;
+        default: f[0] = s->C[j]; break;
+      }
+      for (int k = 0; k < comps; k++) num[k] += w * f[k];
+    }
+    for (int k = 0; k < comps; k++) out[comps * q + k] = den > 0.0 ? num[k] / den : NAN;
+  }
+  return 0;
+}
+
 void orc_destroy(orc_scene* s) {
   if (!s) return;
   double* arrs[] = {s->x, s->u, s->a, s->rho, s->p, s->T, s->dT, s->m, s->H, s->vext, s->f, s->rb,

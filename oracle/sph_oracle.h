@@ -77,6 +77,13 @@ void orc_get_bodies(orc_scene* s, double* com, double* quat, double* vel, double
                     double* mass, double* inertia, double* force, double* torque, int32_t* alive);
 int64_t orc_neighbors(orc_scene* s, int64_t* counts, int32_t* list, int64_t cap);
 void orc_diagnostics(orc_scene* s, double out[16]);
+/* Shepard-filtered field at nq query points (Eq. postprocessing): field one of ORC_F_VEL,
+ * ORC_F_RHO, ORC_F_PRES, ORC_F_TEMP, ORC_F_CONC; particles whose material bit is set in
+ * material_mask contribute; out gets 3 (VEL) or 1 value per query, NaN without any
+ * contributing particle within r_c.  Brute force over all particles.  Returns 0, or -1 for
+ * an unsupported field. */
+int orc_interpolate(orc_scene* s, int64_t nq, const double* query, int32_t field, uint32_t material_mask,
+                    double* out);
 void orc_destroy(orc_scene* s);
 
 /* pieces exposed for pinning */

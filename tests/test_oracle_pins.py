@@ -663,3 +663,43 @@ def test_reservoir_bounds_and_concentration_driven_transition():
     assert np.all(o.get("conc")[chyme] > 0.0)
     assert np.sum(mat == 2) == n_bolus - int(chyme.sum())
     assert np.all(o.get("body")[chyme] == -1)
+
+
+# --------------------------------------------------------------------------- post-processing (Eq. postprocessing)
+
+def test_shepard_filter_reproduces_constants_everywhere():
+    """The Shepard normalisation makes the filtered field of a constant exactly that constant,
+    next to walls and bodies too."""
+    sc = S.tank2d_disc(dx=0.025)
+    sc["particles"]["temperature"][:] = 123.25
+    sc["particles"]["wall_temperature"] = np.full(len(sc["particles"]["mass"]), 123.25)
+    o = O.OracleScene(sc)
+    rng = np.random.default_rng(0)
+    q = np.zeros((500, 3))
+    q[:, :2] = rng.uniform(-0.05, 1.05, (500, 2))
+    T = o.interpolate(q, "temp")
+    ok = ~np.isnan(T)
+    assert ok.sum() > 400
+    assert np.abs(T[ok] - 123.25).max() < 1e-12
+
+
+def test_shepard_filter_converges_at_second_order():
+    errs = []
+    for n, dx in ((24, 0.1), (48, 0.05), (96, 0.025)):
+        sc = S.periodic_box(dim=2, n=n, dx=dx, vel_amp=0.0, jitter=0.0)
+        x, L = sc["particles"]["pos"], n * dx
+        f = lambda y: 300 + np.sin(2 * np.pi * y[:, 0] / L) * np.cos(2 * np.pi * y[:, 1] / L)
+        sc["particles"]["temperature"] = f(x)
+        o = O.OracleScene(sc)
+        q = np.zeros((400, 3))
+        q[:, :2] = np.random.default_rng(0).uniform(0, L, (400, 2))
+        errs.append(np.abs(o.interpolate(q, "temp") - f(q)).max())
+    assert errs[1] < errs[0] / 3.5 and errs[2] < errs[1] / 3.5, errs
+
+
+def test_shepard_filter_without_contributing_particles_is_nan():
+    sc = S.tank2d_disc(dx=0.025)
+    o = O.OracleScene(sc)
+    q = np.array([[0.5, 0.4, 0.0], [0.1, 0.9, 0.0]])  # disc centre; far from the disc
+    v = o.interpolate(q, "vel", material_mask=1 << 2)  # the disc's material only
+    assert np.isfinite(v[0]).all() and np.isnan(v[1]).all()
