@@ -192,6 +192,17 @@ enum {
 sph_status sph_read_fields(sph_scene* scene, uint32_t field_mask, void* const* host_dst,
                            int32_t original_order);
 
+/* Post-processing (Eq. postprocessing): the Shepard-filtered field
+ *   f^(r) = sum_j V_j f_j W(|r - r_j|) / sum_j V_j W(|r - r_j|)
+ * at nq query points (host, nq*3 doubles; z ignored in 2D; wrapped on periodic axes) over
+ * the particles whose material index i has bit i set in material_mask, closer than r_c.
+ * field: SPH_F_VEL (3 values per query; walls contribute their prescribed velocity),
+ * SPH_F_RHO, SPH_F_PRES, SPH_F_TEMP (walls: prescribed temperature) or SPH_F_CONC (1 value).
+ * out: host, nq*3 or nq doubles, NaN where no particle contributes.  FP64 accumulation on
+ * both paths.  Synchronises the scene's stream.  SPH_ERR_INVALID for other fields. */
+sph_status sph_interpolate(sph_scene* scene, int64_t nq, const double* query, int32_t field,
+                           uint32_t material_mask, double* out);
+
 /* Overwrite POS, VEL and TEMP of fluid particles from host arrays in input order (FP64,
  * n rows of 3 or 1; rows of other particles are ignored).  Ownership stays with the
  * caller; the copy is enqueued on the scene's stream.  The next step starts from the

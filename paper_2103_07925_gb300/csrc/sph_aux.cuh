@@ -332,3 +332,79 @@ static __global__ void k_sort_segments(const int64_t* offs, int n, int32_t* list
 }
 
 }  // namespace sph
+
+namespace sph {
+
+// ------------------------------------------------------------------ post-processing
+// Shepard-filtered field at query points (Eq. postprocessing): sum_j V_j f_j W / sum_j V_j W
+// over particles of the selected materials closer than r_c, one thread per query, FP64
+// accumulation on both paths.  The 3^d cells around the query's cell hold every such
+// particle: cells have edge >= r_c + skin and no particle has moved more than skin / 2
+// since it was binned.
+template <class R, int DIM>
+__global__ void k_interpolate(Scene<R>* const* sc, int nq, const double* q, int field, unsigned mask,
+                              double* out) {
+  const Scene<R>& S = **sc;
+  const double sig = DIM == 2 ? 7.0 / (478.0 * M_PI * S.h * S.h) : 1.0 / (120.0 * M_PI * S.h * S.h * S.h);
+  const int comps = field == SPH_F_VEL ? 3 : 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += gridDim.x * blockDim.x) {
+    double xq[3] = {q[3 * t], q[3 * t + 1], DIM == 3 ? q[3 * t + 2] : 0.0};
+    int c[3] = {0, 0, 0};
+    for (int k = 0; k < DIM; k++) {
+      if (S.per[k]) {
+        if (xq[k] >= S.hi[k]) xq[k] -= S.L[k];
+        else if (xq[k] < S.lo[k]) xq[k] += S.L[k];
+      }
+      double v = floor((xq[k] - S.lo[k]) / S.ell[k]);
+      c[k] = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
+    }
+    double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
+    const int zl = DIM == 3 ? -1 : 0, zh = DIM == 3 ? 1 : 0;
+    for (int dz = zl; dz <= zh; dz++)
+      for (int dy = -1; dy <= 1; dy++)
+        for (int dx = -1; dx <= 1; dx++) {
+          int cc[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+          bool skip = false;
+          for (int k = 0; k < DIM; k++)
+            if (cc[k] < 0 || cc[k] >= S.ncell[k]) {
+              if (!S.per[k] || S.ncell[k] < 3) { skip = true; break; }
+              cc[k] = (cc[k] + S.ncell[k]) % S.ncell[k];
+            }
+          if (skip) continue;
+          int key = cell_key(S, cc[0] + S.ncell[0] * (cc[1] + S.ncell[1] * cc[2]));
+          int a = max(S.cstart[key], 0), e = min(S.cstart[key + 1], S.n);
+          for (int j = a; j < e; j++) {
+            int mt = S.P.mt[j];
+            if (!((mask >> mt) & 1u)) continue;
+            double xj[3];
+            abs_pos<R>(S, j, xj);
+            double r2 = 0.0;
+            for (int k = 0; k < DIM; k++) {
+              double d = xq[k] - xj[k];
+              if (S.per[k]) {
+                if (d > 0.5 * S.L[k]) d -= S.L[k];
+                else if (d < -0.5 * S.L[k]) d += S.L[k];
+              }
+              r2 += d * d;
+            }
+            if (!(r2 < S.rc2)) continue;
+            double w = sig * quintic_w<double>(sqrt(r2) / S.h) * (double)S.P.m[j] / (double)S.P.rho[j];
+            den += w;
+            if (field == SPH_F_VEL) {
+              num[0] += w * (double)S.P.vx[j];
+              num[1] += w * (double)S.P.vy[j];
+              num[2] += w * (double)S.P.vz[j];
+            } else {
+              double f = field == SPH_F_RHO ? (double)S.P.rho[j]
+                       : field == SPH_F_PRES ? (double)S.prs[j]
+                       : field == SPH_F_TEMP ? (double)S.P.T[j]
+                       : (S.any_conc ? (double)S.P.C[j] : 0.0);
+              num[0] += w * f;
+            }
+          }
+        }
+    for (int k = 0; k < comps; k++) out[comps * t + k] = den > 0.0 ? num[k] / den : (double)NAN;
+  }
+}
+
+}  // namespace sph

@@ -98,6 +98,12 @@ sph_status sph_write_fields(sph_scene* s, uint32_t mask, const void* const* src)
   return s->e->write_fields(0, mask, src);
 }
 
+sph_status sph_interpolate(sph_scene* s, int64_t nq, const double* query, int32_t field, uint32_t material_mask,
+                           double* out) {
+  if (!s) { set_error("null scene"); return SPH_ERR_INVALID; }
+  return s->e->interpolate(0, nq, query, field, material_mask, out);
+}
+
 sph_status sph_read_bodies(sph_scene* s, const sph_bodies_out* out, int32_t* k_out) {
   if (!s) { set_error("null scene"); return SPH_ERR_INVALID; }
   return s->e->read_bodies(0, out, k_out);

@@ -394,6 +394,7 @@ class Engine {
   sph_status evaluate_initial(int idx);
   sph_status read_fields(int idx, uint32_t mask, void* const* dst, int original_order);
   sph_status write_fields(int idx, uint32_t mask, const void* const* src);
+  sph_status interpolate(int idx, int64_t nq, const double* query, int32_t field, uint32_t mask, double* out);
   sph_status read_bodies(int idx, const sph_bodies_out* out, int32_t* kout);
   sph_status diagnostics(int idx, double out[16]);
   sph_status neighbors(int idx, int64_t* counts, int32_t* list, int64_t cap_list, int64_t* total);
@@ -957,6 +958,29 @@ sph_status Engine<R, DIM>::read_fields(int idx, uint32_t mask, void* const* dst,
       SPH_CU(cudaMemcpyAsync(dst[f], p, b, cudaMemcpyDeviceToHost, stream));
       p += b;
     }
+  SPH_CU(cudaStreamSynchronize(stream));
+  return SPH_OK;
+}
+
+template <class R, int DIM>
+sph_status Engine<R, DIM>::interpolate(int idx, int64_t nq, const double* query, int32_t field, uint32_t mask,
+                                       double* out) {
+  if (field != SPH_F_VEL && field != SPH_F_RHO && field != SPH_F_PRES && field != SPH_F_TEMP && field != SPH_F_CONC) {
+    set_error("field %d cannot be interpolated (VEL, RHO, PRES, TEMP or CONC)", field);
+    return SPH_ERR_INVALID;
+  }
+  if (nq < 0 || (nq > 0 && (!query || !out))) { set_error("bad query arguments"); return SPH_ERR_INVALID; }
+  if (nq == 0) return SPH_OK;
+  if (nq > (1LL << 30)) { set_error("at most 2^30 query points per call"); return SPH_ERR_INVALID; }
+  const Scene<R>& S = hs[idx];
+  int comps = field == SPH_F_VEL ? 3 : 1;
+  SPH_TRY(ensure_stage(sizeof(double) * (size_t)nq * (3 + comps)));
+  double* dq = (double*)d_stage;
+  double* dout = dq + 3 * nq;
+  SPH_CU(cudaMemcpyAsync(dq, query, sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, stream));
+  k_interpolate<R, DIM><<<grid_for(nq, 128, grid_part), 128, 0, stream>>>(S.self, (int)nq, dq, field, mask, dout);
+  SPH_CU(cudaGetLastError());
+  SPH_CU(cudaMemcpyAsync(out, dout, sizeof(double) * comps * nq, cudaMemcpyDeviceToHost, stream));
   SPH_CU(cudaStreamSynchronize(stream));
   return SPH_OK;
 }

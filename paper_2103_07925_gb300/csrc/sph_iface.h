@@ -18,6 +18,7 @@ struct EngineIface {
   virtual sph_status advance(int32_t n) = 0;
   virtual sph_status read_fields(int idx, uint32_t mask, void* const* dst, int original) = 0;
   virtual sph_status write_fields(int idx, uint32_t mask, const void* const* src) = 0;
+  virtual sph_status interpolate(int idx, int64_t nq, const double* q, int32_t field, uint32_t mask, double* out) = 0;
   virtual sph_status read_bodies(int idx, const sph_bodies_out* o, int32_t* k) = 0;
   virtual sph_status diagnostics(int idx, double* out) = 0;
   virtual sph_status neighbors(int idx, int64_t* counts, int32_t* list, int64_t cap, int64_t* total) = 0;

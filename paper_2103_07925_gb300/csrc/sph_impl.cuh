@@ -19,6 +19,9 @@ struct EngineImpl final : EngineIface {
   sph_status advance(int32_t n) override { return e.advance_jobs(n); }
   sph_status read_fields(int idx, uint32_t m, void* const* d, int o) override { return e.read_fields(idx, m, d, o); }
   sph_status write_fields(int idx, uint32_t m, const void* const* s) override { return e.write_fields(idx, m, s); }
+  sph_status interpolate(int idx, int64_t nq, const double* q, int32_t f, uint32_t m, double* out) override {
+    return e.interpolate(idx, nq, q, f, m, out);
+  }
   sph_status read_bodies(int idx, const sph_bodies_out* o, int32_t* k) override { return e.read_bodies(idx, o, k); }
   sph_status diagnostics(int idx, double* out) override { return e.diagnostics(idx, out); }
   sph_status neighbors(int idx, int64_t* c, int32_t* l, int64_t cap, int64_t* t) override {

@@ -28,7 +28,7 @@ EXPORTS = ["sph_create_scene", "sph_step", "sph_step_async", "sph_read_fields", 
            "sph_batch_step", "sph_batch_poll", "sph_batch_read_fields", "sph_batch_job_diagnostics",
            "sph_batch_release", "sph_batch_info", "sph_batch_destroy", "sph_profile",
            "sph_profile_stage_name", "sph_density_static", "sph_set_launch", "sph_time_steps",
-           "sph_batch_set_launch", "sph_batch_time_steps", "sph_batch_job_state"]
+           "sph_batch_set_launch", "sph_batch_time_steps", "sph_batch_job_state", "sph_interpolate"]
 PROFILE_STAGES = 21
 
 
@@ -115,6 +115,7 @@ def lib():
             "sph_batch_set_launch": [vp, i32, C.POINTER(i32), i32],
             "sph_batch_time_steps": [vp, i32, C.POINTER(C.c_double)],
             "sph_batch_job_state": [vp, i64, C.POINTER(i32)],
+            "sph_interpolate": [vp, i64, vp, i32, C.c_uint32, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -255,6 +256,17 @@ class Scene:
                 src[FIELDS[nm]] = a.ctypes.data
                 mask |= 1 << FIELDS[nm]
         _check(lib().sph_write_fields(self.h, mask, src))
+
+    def interpolate(self, query, field, material_mask=0xFFFFFFFF):
+        """Shepard-filtered field (Eq. postprocessing) at query points (nq x 3 or nq x 2)."""
+        q = np.zeros((len(query), 3))
+        qa = np.asarray(query, dtype=np.float64)
+        q[:, : qa.shape[1]] = qa
+        comps = 3 if field == "vel" else 1
+        out = np.empty((len(q), comps))
+        _check(lib().sph_interpolate(self.h, len(q), q.ctypes.data, FIELDS[field], C.c_uint32(material_mask),
+                                     out.ctypes.data))
+        return out if comps == 3 else out[:, 0]
 
     def bodies(self):
         k = C.c_int32()
