@@ -74,3 +74,28 @@ def test_powder_bed_full_size_fp32():
         e = rel_err(g.read(f), o.get(f), mask=~edge if f in ("pres", "vext") else None, scale=sca.get(f, 0.0))
         assert e < 1e-5, (f, e)
     g.close()
+
+
+def test_batched_mix_full_size_sampled_scenes():
+    """The 256-scene batched mix (27M particles) for one step in one batch, FP32, with the
+    row-major layout and skin the tuner picks for it; 8 sampled scenes against the oracle."""
+    from oracle.oracle import OracleScene
+    from paper_2103_07925_gb300.errors import edge_only_boundary
+    from paper_2103_07925_gb300.sph import Batch
+    mix = S.batch_mix(count=256, seed=2103)
+    B = Batch(capacity=256, precision=32)
+    ids = [B.admit(sc, 1, key_order=1, skin=0.3 * sc["params"]["h"]) for sc, _ in mix]
+    assert all(i is not None for i in ids)
+    B.step(1)
+    assert len(B.poll()) == 256
+    for q in [int(v) for v in np.linspace(0, 255, 8)]:
+        sc = mix[q][0]
+        o = OracleScene(sc)
+        o.step(1)
+        edge = edge_only_boundary(sc, o.get("pos"), sc["particles"]["material"])
+        sca = field_scales(sc)
+        for f in ("pos", "vel", "rho", "pres", "temp"):
+            e = rel_err(B.read(ids[q], f), o.get(f), mask=~edge if f == "pres" else None, scale=sca.get(f, 0.0))
+            assert e < 1e-5, (q, f, e)
+        assert np.array_equal(B.read(ids[q], "mat"), o.get("mat"))
+    B.close()
