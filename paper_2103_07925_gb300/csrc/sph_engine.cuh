@@ -765,9 +765,10 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   int64_t np = h_pfx[ns], nc = h_pfx[(cap + 1) + ns], ng = h_pfx[2 * (cap + 1) + ns];
   int64_t nb = h_pfx[3 * (cap + 1) + ns], ncb = h_pfx[4 * (cap + 1) + ns];
   bool any_dt = false, any_body = false;
-  bool any_transition = false, any_tvf = false;
+  bool any_transition = false, any_tvf = false, any_plain = false;
   for (int a : act) {
     any_tvf |= hs[a].tvf != 0 || hs[a].any_conc != 0;
+    any_plain |= hs[a].tvf == 0 && hs[a].any_conc == 0;
     any_dt |= hs[a].dt_mode == 1;
     any_body |= meta[a].K0 > 0 || hs[a].has_transition != 0;
     any_transition |= hs[a].has_transition != 0;
@@ -815,8 +816,9 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_extrap<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
   rec();
-  if (any_tvf) k_force<R, DIM, true><<<gsw, sweep_block, 0, stream>>>(B);
-  else k_force<R, DIM, false><<<gsw, sweep_block, 0, stream>>>(B);
+  if (any_tvf) { k_force<R, DIM, true><<<gsw, sweep_block, 0, stream>>>(B); kcount++; }
+  if (any_plain) { k_force<R, DIM, false><<<gsw, sweep_block, 0, stream>>>(B); kcount++; }
+  kcount--;  // one force launch is counted with the fixed stages
   rec();
   if (any_body) { k_body_reduce<R><<<gb, 128, 0, stream>>>(B, 1); kcount++; }
   rec();

@@ -538,7 +538,10 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
     int i = g - __ldg(B.pfx_part + s);
     int tm = g < total ? S.P.mt[i] : 0;
     int kind = S.matR[tm].kind;
-    if (g < total && kind != KWALL) {
+    // each instantiation takes the scenes of its own kind, so a scene's arithmetic does not
+    // depend on the other scenes of a batch
+    bool mine = TVF == (S.tvf != 0 || S.any_conc != 0);
+    if (g < total && kind != KWALL && mine) {
       Target<R> t;
       t.kind = kind;
       t.body = S.P.body[i];

@@ -8,7 +8,7 @@ import pytest
 from paper_2103_07925_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
-FIELDS = ("pos", "vel", "rho", "pres", "temp", "dtemp", "mat", "body")
+FIELDS = ("pos", "vel", "rho", "pres", "temp", "dtemp", "mat", "body", "conc", "bacc")
 
 
 def _mix():
@@ -23,7 +23,15 @@ def _mix():
         ("box2d", S.periodic_box(dim=2, n=30, bodies=4, body_radius=0.2), 6),
         ("cycle2d", _cycle(), 8),
         ("hydro2d", S.hydrostatic_tank2d(), 4),
+        ("tvf2d", _tvf(S.periodic_box(dim=2, n=24, bodies=2, body_radius=0.2, vel_amp=0.1, jitter=0.1)), 5),
+        ("gastric", S.gastric2d(dx=0.1, n_boluses=3), 6),
     ]
+
+
+def _tvf(sc):
+    fl = sc["materials"][0]
+    sc["params"]["p_background"] = fl["rho0"] * fl["c"] ** 2
+    return sc
 
 
 def _alone(sc, steps, precision):
