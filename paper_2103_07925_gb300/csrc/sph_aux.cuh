@@ -271,6 +271,8 @@ __global__ void k_diag_fin(Scene<R>* const* sc, const double* part, int nblk, do
 template <class R, int DIM>
 struct NbPol {
   R *sx, *sy, *sz;
+  float *fx, *fy, *fz;
+  float tf[3];
   int* so;
   int cox, cdy, cdz;
   bool active;
@@ -281,6 +283,7 @@ struct NbPol {
   unsigned long long hits;
   __device__ void stage(const Scene<R>& S, int j, int lane) {
     sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
+    if (sizeof(R) == 8) { fx[lane] = (float)sx[lane]; fy[lane] = (float)sy[lane]; fz[lane] = (float)sz[lane]; }
     so[lane] = S.P.orig[j];
   }
   __device__ bool accept(int) const { return true; }
@@ -294,11 +297,13 @@ template <class R, int DIM>
 __global__ void __launch_bounds__(128) k_neighbors(Scene<R>* const* sc, int ngroups, int64_t* counts,
                                                    const int64_t* offs, int32_t* list) {
   __shared__ R sm[4][3][32];
+  __shared__ float smf[4][3][32];
   __shared__ int smo[4][32];
   const Scene<R>& S = **sc;
   int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   NbPol<R, DIM> pol;
   pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2]; pol.so = smo[wib];
+  pol.fx = smf[wib][0]; pol.fy = smf[wib][1]; pol.fz = smf[wib][2];
   pol.list = list;
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int g = gw; g < ngroups; g += nw) {
@@ -310,10 +315,11 @@ __global__ void __launch_bounds__(128) k_neighbors(Scene<R>* const* sc, int ngro
       if (!__any_sync(FULL, pol.active)) continue;
       pol.idx = valid ? i : -1;
       if (valid) target_pos(S, i, G.cx0, pol.tp);
+      pol.tf[0] = (float)pol.tp[0]; pol.tf[1] = (float)pol.tp[1]; pol.tf[2] = (float)pol.tp[2];
       pol.cnt = 0;
       pol.off = (valid && offs) ? offs[S.P.orig[i]] : 0;
       pol.hits = 0;
-      traverse<R, DIM>(S, G, pol, lane, S.rc2R);
+      traverse<R, DIM>(S, G, pol, lane, S.rc2R, S.rc2f);
       if (valid && !offs) counts[S.P.orig[i]] = pol.cnt;
     }
   }

@@ -62,6 +62,7 @@ struct Scene {
   double h, rc, rc2, dx, skin;
   R rc2R, rl2R, inv_h, sig_w, sig_dw, w0;  // W = sig_w w(q), dW/dr = sig_dw w'(q); rl: list radius
   R half_skin2;
+  float rc2f, rl2f;    // FP64 scenes: FP32 pre-test radii (squared) with the rounding margin
   double kc, dc;
   R kcR, dcR, dxR;
   double src_Q, src_r, src_v[3], src_x0[3], src_depth, src_ztop;
@@ -74,6 +75,10 @@ struct Scene {
   double cmax;
   MatD mat[MAXMAT];
   MatR<R> matR[MAXMAT];
+  // FP64 scenes: pair means of the material constants, from the per-pair formulas
+  // 2 eta_a eta_b / (eta_a + eta_b) and 4 kappa_a kappa_b / (kappa_a + kappa_b) (0 when the
+  // denominator is 0), evaluated once on the host
+  double eta_ab[MAXMAT][MAXMAT], kap_ab[MAXMAT][MAXMAT];
   // ---------------------------------------------------------------- particles
   PBank<R> P, Q;       // current and alternate bank
   R *prs, *dT;         // pressure, rate (not permuted: recomputed every evaluation)

@@ -91,6 +91,15 @@ inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
   S.skin = p->skin > 0.0 ? p->skin : 0.0;
   S.rc2R = (R)S.rc2;
   S.rl2R = (R)((S.rc + S.skin) * (S.rc + S.skin));
+  {  // FP32 copies of coordinates up to X in magnitude are off by 2^-24 X each; the pre-test
+     // distance (two subtractions and a shift) by at most about 1.5e-6 X
+    double X = 0.0;
+    for (int d = 0; d < 3; d++) X = std::fmax(X, std::fmax(std::fabs(p->box_min[d]), std::fabs(p->box_max[d])));
+    X += std::fmax(std::fmax(S.L[0], S.L[1]), S.L[2]);
+    double m = 2e-6 * X + 1e-30;
+    S.rc2f = (float)((S.rc + m) * (S.rc + m) * (1.0 + 1e-5));
+    S.rl2f = (float)((S.rc + S.skin + m) * (S.rc + S.skin + m) * (1.0 + 1e-5));
+  }
   S.half_skin2 = (R)(0.25 * S.skin * S.skin);
   S.inv_h = (R)(1.0 / S.h);
   double sig = p->dim == 2 ? 7.0 / (478.0 * M_PI * S.h * S.h) : 1.0 / (120.0 * M_PI * S.h * S.h * S.h);
@@ -137,6 +146,13 @@ inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
       if (c5 < cond) cond = c5;
     }
   }
+  for (int a = 0; a < p->n_materials; a++)
+    for (int b = 0; b < p->n_materials; b++) {
+      double ea = p->materials[a].eta, eb = p->materials[b].eta;
+      double ka = p->materials[a].kappa, kb = p->materials[b].kappa;
+      S.eta_ab[a][b] = (ea + eb > 0.0) ? 2.0 * ea * eb / (ea + eb) : 0.0;
+      S.kap_ab[a][b] = (ka + kb > 0.0) ? 4.0 * ka * kb / (ka + kb) : 0.0;
+    }
   S.has_source = p->src_power > 0 ? 1 : 0;
   S.pbg = p->p_background > 0.0 ? p->p_background : 0.0;
   S.pbgR = (R)S.pbg;

@@ -26,7 +26,7 @@ namespace sph {
 constexpr unsigned FULL = 0xffffffffu;
 
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
-template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return 1.0 / sqrt(x); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 
 // quintic spline (Morris 1997), polynomial part: w(q) and dw/dq, valid for q < 3
@@ -695,9 +695,12 @@ __device__ __forceinline__ R dsub(R a, R b) {
 }
 
 // generic traversal.  Pol provides: stage(S, j, lane), active, tp[3], idx,
-// bool accept(k) (candidate filter for the hit mask), pair(S, k, j, dx, dy, dz, r2).
+// bool accept(k) (candidate filter for the hit mask), pair(S, k, j, dx, dy, dz, r2), and for
+// FP64 scenes FP32 copies fx/fy/fz of the staged positions and tf of the target (rc2f: the
+// FP32 pre-test radius, squared, with the margin of the rounding of those copies).
 template <class R, int DIM, class Pol>
-__device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>& G, Pol& pol, int lane, R rc2) {
+__device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>& G, Pol& pol, int lane, R rc2,
+                                         float rc2f) {
   const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
   for (int dz = zlo; dz <= zhi; dz++)
     for (int dy = -1; dy <= 1; dy++)
@@ -716,12 +719,25 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
           __syncwarp();
           unsigned mask = 0u;
           if (pol.active) {
-            for (int k = 0; k < cnt; k++) {
-              R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sh[0]);
-              R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
-              R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
-              R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
-              if (r2 < rc2 && cb + k != pol.idx && pol.accept(k)) mask |= 1u << k;
+            if constexpr (sizeof(R) == 8) {
+              // FP64 scenes: an FP32 test with a margin keeps a superset of the pairs, the
+              // exact FP64 test below decides each of them (the result is the exact set)
+              float shf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
+              for (int k = 0; k < cnt; k++) {
+                float dx = (pol.tf[0] - pol.fx[k]) - shf[0];
+                float dy2 = (pol.tf[1] - pol.fy[k]) - shf[1];
+                float dz2 = DIM == 3 ? (pol.tf[2] - pol.fz[k]) - shf[2] : 0.f;
+                float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+                if (r2 < rc2f && cb + k != pol.idx && pol.accept(k)) mask |= 1u << k;
+              }
+            } else {
+              for (int k = 0; k < cnt; k++) {
+                R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sh[0]);
+                R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
+                R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
+                R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
+                if (r2 < rc2 && cb + k != pol.idx && pol.accept(k)) mask |= 1u << k;
+              }
             }
           }
           pol.hits += __popc(mask);
@@ -732,6 +748,7 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
             R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
             R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
             R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
+            if (sizeof(R) == 8 && !(r2 < rc2)) continue;
             pol.pair(S, k, cb + k, dx, dy2, dz2, r2);
           }
         }

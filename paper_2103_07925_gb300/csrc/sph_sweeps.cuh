@@ -55,6 +55,8 @@ __device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p,
 template <class R, int DIM>
 struct SearchPol {
   R *sx, *sy, *sz;
+  float *fx, *fy, *fz;  // FP32 copies of the staged positions (FP64 scenes)
+  float tf[3];
   int* sk;             // kind of every staged candidate
   bool active, fluid, wall;
   int idx, tx, n, maxnb, cnt;
@@ -65,6 +67,7 @@ struct SearchPol {
   unsigned long long hits;
   __device__ void stage(const Scene<R>& S, int j, int lane) {
     sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
+    if (sizeof(R) == 8) { fx[lane] = (float)sx[lane]; fy[lane] = (float)sy[lane]; fz[lane] = (float)sz[lane]; }
     sk[lane] = S.matR[S.P.mt[j]].kind;
   }
   // a wall particle only ever reads its fluid neighbours (extrapolation of Sec. 3.3.4)
@@ -80,10 +83,13 @@ struct SearchPol {
 template <class R, int DIM>
 __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
   __shared__ R sm[4][3][32];
+  __shared__ float smf[sizeof(R) == 8 ? 4 : 1][3][32];
   __shared__ int smk[4][32];
   int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   SearchPol<R, DIM> pol;
   pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
+  int wf = sizeof(R) == 8 ? wib : 0;
+  pol.fx = smf[wf][0]; pol.fy = smf[wf][1]; pol.fz = smf[wf][2];
   pol.sk = smk[wib];
   int total = __ldg(B.pfx_grp + B.nsc);
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -109,10 +115,11 @@ __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
         target_pos(S, i, G.cx0, pol.tp);
         if (G.ncx > 1) pol.tx = key_lin(S, S.key[i]) % S.ncell[0] - G.cx0;
       }
+      pol.tf[0] = (float)pol.tp[0]; pol.tf[1] = (float)pol.tp[1]; pol.tf[2] = (float)pol.tp[2];
       pol.acc = R(0);
       pol.cnt = 0;
       pol.hits = 0;
-      traverse<R, DIM>(S, G, pol, lane, S.rl2R);
+      traverse<R, DIM>(S, G, pol, lane, S.rl2R, S.rl2f);
       if (valid) {
         S.nbc[i] = pol.cnt;
         R rho = S.P.rho[i], p = R(0);
@@ -343,7 +350,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
 // ---------------------------------------------------------------- forces and heat
 template <class R>
 struct Target {
-  int kind, body;
+  int kind, body, mi;  // kind, body id, material index
   const MatR<R>* M;
   R rho, p, V2, eta, kap, T;
   R u[3], ve[3];
@@ -356,20 +363,20 @@ struct Target {
 template <class R, int DIM, bool TVF>
 __device__ __forceinline__ void force_pair(const Scene<R>& S, Target<R>& t, int j, const R* d, R r2,
                                            R* acc, R& heat) {
-  const MatR<R>& Bm = S.matR[S.P.mt[j]];
+  int mj = S.P.mt[j];
+  const MatR<R>& Bm = S.matR[mj];
   int bk = Bm.kind;
   R inv_r = rsqrt_<R>(r2);
   R r = r2 * inv_r;
   R dW = S.sig_dw * quintic_dw<R>(r * S.inv_h);
   R ex = d[0] * inv_r, ey = d[1] * inv_r, ez = d[2] * inv_r;
   R Vj = S.vol[j];
-  // heat conduction (Cleary & Monaghan), walls Dirichlet (kappa_b = kappa_a) or adiabatic
+  // heat conduction (Cleary & Monaghan), walls Dirichlet (kappa_b = kappa_a) or adiabatic;
+  // the pair mean 4 kappa_a kappa_b / (kappa_a + kappa_b) from the material-pair table
   if (S.any_heat) {
     R Tb = S.P.T[j];
     if (!(bk == KWALL && isnan(Tb))) {
-      R kb = bk == KWALL ? t.kap : Bm.kappa;
-      R ks = t.kap + kb;
-      R kab = ks > R(0) ? qdiv<R>(R(4) * t.kap * kb, ks) : R(0);
+      R kab = (R)S.kap_ab[t.mi][bk == KWALL ? t.mi : mj];
       heat += Vj * kab * (t.T - Tb) * inv_r * dW;
     }
   }
@@ -391,8 +398,8 @@ __device__ __forceinline__ void force_pair(const Scene<R>& S, Target<R>& t, int 
       uj[0] = S.vex[j]; uj[1] = S.vey[j]; uj[2] = S.vez[j];
     }
     R pt = qdiv<R>(rhoj * t.p + t.rho * pj, t.rho + rhoj);
-    R es = t.eta + etaj;
-    R et = es > R(0) ? qdiv<R>(R(2) * t.eta * etaj, es) : R(0);
+    (void)etaj;  // eta_j = eta_i for boundaries: the table's diagonal
+    R et = (R)S.eta_ab[t.mi][bk == KFLUID ? mj : t.mi];
     R coef = (t.V2 + Vj * Vj) * dW;
     R vis = et * inv_r;
     acc[0] += coef * (-pt * ex + vis * (t.u[0] - uj[0]));
@@ -544,6 +551,7 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
     if (g < total && kind != KWALL && mine) {
       Target<R> t;
       t.kind = kind;
+      t.mi = tm;
       t.body = S.P.body[i];
       t.M = &S.matR[tm];
       t.rho = S.P.rho[i];
