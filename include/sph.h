@@ -87,7 +87,9 @@ typedef struct {
  *  rebin_interval   with skin > 0: also rebuild at least every rebin_interval steps (0: no
  *                   forced rebuild)
  *  key_order        0: Morton order of cells;  1: row-major order (x fastest)
- *  cells_per_group  cells along x handled by one warp (0 = automatic; row-major only)
+ *  cells_per_group  cells along x handled by one warp (0 = automatic; row-major only);
+ *                   -1: the search takes windows of 32 consecutive (sorted) particles,
+ *                   split where they cross into the next row of cells
  *  body_capacity    maximum number of bodies including those created by solidification
  *                   (0: initial count + 1024)
  *  src_*            optional moving Gaussian surface heat source (not in the paper; a heat

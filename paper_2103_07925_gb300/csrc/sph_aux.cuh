@@ -307,7 +307,9 @@ __global__ void __launch_bounds__(128) k_neighbors(Scene<R>* const* sc, int ngro
   pol.list = list;
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int g = gw; g < ngroups; g += nw) {
-    Group<R, DIM> G = group_of<R, DIM>(S, g);
+    GroupIter<R, DIM> it(S, g);
+    Group<R, DIM> G;
+    while (it.next(S, g, lane, G))
     for (int tb = G.ts; tb < G.te; tb += 32) {
       int i = tb + lane;
       bool valid = i < G.te;

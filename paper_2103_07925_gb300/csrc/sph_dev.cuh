@@ -53,6 +53,7 @@ template <class R>
 struct Scene {
   // ---------------------------------------------------------------- constants
   int dim, n, nmat, key_order, G;
+  int win;             // row-major keys searched in windows of 32 consecutive particles
   int ncell[3], ncells, ngroups, ngx, ncblk;
   int per[3];
   double lo[3], hi[3], L[3], ell[3];

@@ -554,9 +554,10 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   bool morton = p->key_order == 0;
   S.key_order = morton ? 0 : 1;
   S.G = 1;
-  if (!morton) S.G = p->cells_per_group > 0 ? p->cells_per_group : (DIM == 2 ? 3 : 1);
+  S.win = !morton && p->cells_per_group < 0;
+  if (!morton && !S.win) S.G = p->cells_per_group > 0 ? p->cells_per_group : (DIM == 2 ? 3 : 1);
   S.ngx = (S.ncell[0] + S.G - 1) / S.G;
-  S.ngroups = morton ? S.ncells : S.ngx * S.ncell[1] * S.ncell[2];
+  S.ngroups = morton ? S.ncells : (S.win ? (n + 31) / 32 : S.ngx * S.ncell[1] * S.ncell[2]);
   S.ncblk = (S.ncells + 1023) / 1024;
   // ------------------------------------------------------------------ allocations
   auto A = [&](auto** ptr, size_t cnt) { return dalloc(M, ptr, cnt); };

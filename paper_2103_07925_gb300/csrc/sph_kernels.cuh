@@ -633,12 +633,52 @@ __device__ __forceinline__ Group<R, DIM> group_of(const Scene<R>& S, int grp) {
   return G;
 }
 
+// Target ranges of search group g, one per call of next(): a cell (Morton keys) or a run of
+// cells along x (row-major keys) gives one range; in window mode (row-major keys) group g is
+// the 32 consecutive sorted particles [32 g, 32 g + 32), split where they cross from one row
+// of cells (cy, cz) to the next, each part with the x range of cells it spans.  All lanes of
+// the warp call next() together.
+template <class R, int DIM>
+struct GroupIter {
+  int ts, te;
+  bool done;
+  __device__ GroupIter(const Scene<R>& S, int g) {
+    done = false;
+    ts = S.win ? 32 * g : 0;
+    te = S.win ? min(ts + 32, S.n) : 0;
+  }
+  __device__ bool next(const Scene<R>& S, int g, int lane, Group<R, DIM>& G) {
+    if (!S.win) {
+      if (done) return false;
+      done = true;
+      G = group_of<R, DIM>(S, g);
+      return true;
+    }
+    if (ts >= te) return false;
+    int i = ts + lane;
+    int cx = 0, cy = 0, cz = 0;
+    if (i < te) lin_xyz(S, key_lin(S, S.key[i]), cx, cy, cz);
+    int row = cy + S.ncell[1] * cz;
+    int row0 = __shfl_sync(FULL, row, 0);
+    unsigned same = __ballot_sync(FULL, i < te && row == row0);
+    int cnt = __popc(same);  // sorted keys: the lanes of the first row form a prefix
+    G.cx0 = __shfl_sync(FULL, cx, 0);
+    G.ncx = __shfl_sync(FULL, cx, cnt - 1) - G.cx0 + 1;
+    G.cy = __shfl_sync(FULL, cy, 0);
+    G.cz = __shfl_sync(FULL, cz, 0);
+    G.ts = ts;
+    G.te = ts + cnt;
+    ts += cnt;
+    return true;
+  }
+};
+
 // target position in the frame of the group: FP64 absolute; FP32 relative to the origin
 // of the group's first cell
 template <class R>
 __device__ __forceinline__ void target_pos(const Scene<R>& S, int i, int cx0, R* p) {
   p[0] = S.P.px[i]; p[1] = S.P.py[i]; p[2] = S.P.pz[i];
-  if (sizeof(R) == 4 && S.G > 1 && !S.key2lin) {
+  if (sizeof(R) == 4 && !S.key2lin) {
     int lin = S.key[i];
     int cx = lin % S.ncell[0];
     p[0] += (R)(cx - cx0) * S.ellR[0];

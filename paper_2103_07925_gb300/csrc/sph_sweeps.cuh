@@ -97,10 +97,13 @@ __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
     int s = find_scene(B.pfx_grp, B.nsc, g);
     const Scene<R>& S = *B.sc[s];
     if (!rebin_now(S)) continue;  // lists of the last rebuild still hold (skin)
-    Group<R, DIM> G = group_of<R, DIM>(S, g - __ldg(B.pfx_grp + s));
+    int gl = g - __ldg(B.pfx_grp + s);
+    GroupIter<R, DIM> it(S, gl);
+    Group<R, DIM> G;
     pol.list = S.nbl;
     pol.n = S.n;
     pol.maxnb = S.maxnb;
+    while (it.next(S, gl, lane, G))
     for (int tb = G.ts; tb < G.te; tb += 32) {
       int i = tb + lane;
       bool valid = i < G.te;

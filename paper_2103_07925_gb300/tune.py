@@ -22,7 +22,8 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass, field
 
-LAYOUTS = [dict(key_order=0, cells_per_group=0)] + [dict(key_order=1, cells_per_group=g) for g in (1, 2, 3)]
+# cells_per_group = -1: row-major keys searched in windows of 32 consecutive particles
+LAYOUTS = [dict(key_order=0, cells_per_group=0)] + [dict(key_order=1, cells_per_group=g) for g in (1, 2, 3, -1)]
 SKINS_H = (0.0, 0.1, 0.15, 0.2, 0.3, 0.5)
 SWEEP_BLOCKS = (64, 128, 256)
 WAVES = (0, 1, 2, 4)

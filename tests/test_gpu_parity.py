@@ -38,10 +38,11 @@ SCENES = small_scenes()
 
 
 @pytest.mark.parametrize("name", list(SCENES))
-@pytest.mark.parametrize("key_order", [0, 1])
-def test_binning_and_neighbours_bit_exact(name, key_order):
+@pytest.mark.parametrize("key_order,cpg", [(0, 0), (1, 0), (1, -1)])
+def test_binning_and_neighbours_bit_exact(name, key_order, cpg):
+    """cpg = -1: row-major keys searched in windows of 32 consecutive particles."""
     sc = SCENES[name]
-    g = _gpu(sc, precision=64, key_order=key_order)
+    g = _gpu(sc, precision=64, key_order=key_order, cells_per_group=cpg)
     o = OracleScene(sc)
     assert np.array_equal(g.read("cell"), o.get("cell"))
     gc, gl = g.neighbors()
@@ -125,11 +126,15 @@ def test_skin_lists_give_the_same_step(name):
 
 
 @pytest.mark.parametrize("name", ["tank2d_full", "tank3d_small", "periodic3d_heat", "cloud3d"])
-def test_fp32_fields_from_shared_state(name):
+@pytest.mark.parametrize("layout", [dict(), dict(key_order=1, cells_per_group=-1, skin=0.3)])
+def test_fp32_fields_from_shared_state(name, layout):
     """FP32 pair sums with cell-relative positions: every per-step field within 1e-5 of
     the FP64 oracle, relative to max(|y|, RMS(y), the field's term scale)."""
     sc = SCENES[name]
-    g = _gpu(sc, precision=32)
+    lay = dict(layout)
+    if "skin" in lay:
+        lay["skin"] *= sc["params"]["h"]
+    g = _gpu(sc, precision=32, **lay)
     o = OracleScene(sc)
     g.step(1)
     o.step(1)
