@@ -49,7 +49,7 @@ __global__ void k_import(Scene<R>* const* sc, ImportArgs a) {
       c[k] = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
     }
     int lin = c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]);
-    S.key[i] = cell_key(S, lin);
+    S.key[i] = part_key(S, kind, lin);
     if (sizeof(R) == 8) {
       S.P.px[i] = (R)x[0]; S.P.py[i] = (R)x[1]; S.P.pz[i] = (R)x[2];
     } else {
@@ -124,7 +124,7 @@ __global__ void k_import_fluid(Scene<R>* const* sc, const double* pos, const dou
             c[k] = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
             o[k] = x[k] - (S.lo[k] + c[k] * S.ell[k]);
           }
-          S.key[i] = cell_key(S, c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]));
+          S.key[i] = part_key(S, S.matR[S.P.mt[i]].kind, c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]));
           S.status[10] = 1;
         }
         S.P.px[i] = (R)o[0];
@@ -274,6 +274,7 @@ struct NbPol {
   float *fx, *fy, *fz;
   float tf[3];
   int* so;
+  unsigned cmask;
   int cox, cdy, cdz;
   bool active;
   int idx;
@@ -286,7 +287,6 @@ struct NbPol {
     if (sizeof(R) == 8) { fx[lane] = (float)sx[lane]; fy[lane] = (float)sy[lane]; fz[lane] = (float)sz[lane]; }
     so[lane] = S.P.orig[j];
   }
-  __device__ bool accept(int) const { return true; }
   __device__ void pair(const Scene<R>&, int k, int, R, R, R, R) {
     if (list) list[off + cnt] = so[k];
     cnt++;
@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(128) k_neighbors(Scene<R>* const* sc, int ngro
   pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2]; pol.so = smo[wib];
   pol.fx = smf[wib][0]; pol.fy = smf[wib][1]; pol.fz = smf[wib][2];
   pol.list = list;
+  pol.cmask = (1u << NCLS) - 1u;  // every neighbour, whatever its kind
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int g = gw; g < ngroups; g += nw) {
     GroupIter<R, DIM> it(S, g);
@@ -380,34 +381,36 @@ __global__ void k_interpolate(Scene<R>* const* sc, int nq, const double* q, int 
             }
           if (skip) continue;
           int key = cell_key(S, cc[0] + S.ncell[0] * (cc[1] + S.ncell[1] * cc[2]));
-          int a = max(S.cstart[key], 0), e = min(S.cstart[key + 1], S.n);
-          for (int j = a; j < e; j++) {
-            int mt = S.P.mt[j];
-            if (!((mask >> mt) & 1u)) continue;
-            double xj[3];
-            abs_pos<R>(S, j, xj);
-            double r2 = 0.0;
-            for (int k = 0; k < DIM; k++) {
-              double d = xq[k] - xj[k];
-              if (S.per[k]) {
-                if (d > 0.5 * S.L[k]) d -= S.L[k];
-                else if (d < -0.5 * S.L[k]) d += S.L[k];
+          for (int kc = 0; kc < NCLS; kc++) {
+            int a = max(S.cstart[kc * S.ncells + key], 0), e = min(S.cstart[kc * S.ncells + key + 1], S.n);
+            for (int j = a; j < e; j++) {
+              int mt = S.P.mt[j];
+              if (!((mask >> mt) & 1u)) continue;
+              double xj[3];
+              abs_pos<R>(S, j, xj);
+              double r2 = 0.0;
+              for (int k = 0; k < DIM; k++) {
+                double d = xq[k] - xj[k];
+                if (S.per[k]) {
+                  if (d > 0.5 * S.L[k]) d -= S.L[k];
+                  else if (d < -0.5 * S.L[k]) d += S.L[k];
+                }
+                r2 += d * d;
               }
-              r2 += d * d;
-            }
-            if (!(r2 < S.rc2)) continue;
-            double w = sig * quintic_w<double>(sqrt(r2) / S.h) * (double)S.P.m[j] / (double)S.P.rho[j];
-            den += w;
-            if (field == SPH_F_VEL) {
-              num[0] += w * (double)S.P.vx[j];
-              num[1] += w * (double)S.P.vy[j];
-              num[2] += w * (double)S.P.vz[j];
-            } else {
-              double f = field == SPH_F_RHO ? (double)S.P.rho[j]
-                       : field == SPH_F_PRES ? (double)S.prs[j]
-                       : field == SPH_F_TEMP ? (double)S.P.T[j]
-                       : (S.any_conc ? (double)S.P.C[j] : 0.0);
-              num[0] += w * f;
+              if (!(r2 < S.rc2)) continue;
+              double w = sig * quintic_w<double>(sqrt(r2) / S.h) * (double)S.P.m[j] / (double)S.P.rho[j];
+              den += w;
+              if (field == SPH_F_VEL) {
+                num[0] += w * (double)S.P.vx[j];
+                num[1] += w * (double)S.P.vy[j];
+                num[2] += w * (double)S.P.vz[j];
+              } else {
+                double f = field == SPH_F_RHO ? (double)S.P.rho[j]
+                         : field == SPH_F_PRES ? (double)S.prs[j]
+                         : field == SPH_F_TEMP ? (double)S.P.T[j]
+                         : (S.any_conc ? (double)S.P.C[j] : 0.0);
+                num[0] += w * f;
+              }
             }
           }
         }

@@ -21,6 +21,7 @@ namespace sph {
 
 constexpr int MAXMAT = 16;
 enum { KFLUID = 0, KRIGID = 1, KWALL = 2 };
+constexpr int NCLS = 3;  // key classes: the particle kinds, in this order
 
 struct MatD {  // material constants, FP64
   int kind, to, enth, src;
@@ -55,6 +56,7 @@ struct Scene {
   int dim, n, nmat, key_order, G;
   int win;             // row-major keys searched in windows of 32 consecutive particles
   int ncell[3], ncells, ngroups, ngx, ncblk;
+  int nkey;             // key space: NCLS classes (particle kinds) x ncells cells
   int per[3];
   double lo[3], hi[3], L[3], ell[3];
   R ellR[3], LR[3];
@@ -97,13 +99,16 @@ struct Scene {
   R *xr, *yr, *zr;     // positions at the last list rebuild (same frame as the bank)
   unsigned long long* disp;  // bits of the largest squared displacement since the rebuild
   int maxnb;           // list capacity per particle
-  int* key;            // cell key of each (sorted) particle
+  int* key;            // sort key of each (sorted) particle: kind * ncells + cell key, so the
+                       // fluid, rigid and wall particles form three runs in cell order (a
+                       // particle changes kind only in the relabelling, which forces a
+                       // rebuild before the next pair sweep: key class == kind in every sweep)
   int* where;          // input index -> current sorted index
   // rebin scratch
   int *tkey, *tloc, *bucket, *perm, *tshift;
   // ---------------------------------------------------------------- cells
-  int *cstart;         // ncells + 1 entries, by key
-  int *ccount;         // ncells, kept at zero between rebins
+  int *cstart;         // nkey + 1 entries, by key
+  int *ccount;         // nkey, kept at zero between rebins
   int *cblk;           // block sums of the counting scan
   const int *lin2key;  // Morton rank of a row-major cell (null for row-major keys)
   const int *key2lin;

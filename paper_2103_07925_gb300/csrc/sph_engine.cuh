@@ -85,7 +85,7 @@ inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
     }
     S.ellR[d] = (R)S.ell[d];
     S.LR[d] = (R)S.L[d];
-    if ((double)S.ncells * S.ncell[d] > 2.0e9) { set_error("cell lattice too large"); return SPH_ERR_INVALID; }
+    if ((double)S.ncells * S.ncell[d] * NCLS > 2.0e9) { set_error("cell lattice too large"); return SPH_ERR_INVALID; }
     S.ncells *= S.ncell[d];
   }
   S.skin = p->skin > 0.0 ? p->skin : 0.0;
@@ -348,7 +348,7 @@ class Engine {
       const Scene<R>& S = hs[act[s]];
       h_ptrs.push_back(d_self[act[s]]);
       h_pfx[0 * c1 + s + 1] = h_pfx[0 * c1 + s] + S.n;
-      h_pfx[1 * c1 + s + 1] = h_pfx[1 * c1 + s] + S.ncells;
+      h_pfx[1 * c1 + s + 1] = h_pfx[1 * c1 + s] + S.nkey;
       h_pfx[2 * c1 + s + 1] = h_pfx[2 * c1 + s] + S.ngroups;
       h_pfx[3 * c1 + s + 1] = h_pfx[3 * c1 + s] + S.Kcap;
       h_pfx[4 * c1 + s + 1] = h_pfx[4 * c1 + s] + S.ncblk;
@@ -377,7 +377,8 @@ class Engine {
   static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans, bool tvf) {
     size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 9 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
                  (DIM == 3 ? 192 : 64) * sizeof(int) + (sizeof(R) == 4 ? 3 * sizeof(float4) : 0);
-    size_t cells = (size_t)(ncells + 1) * 4 * sizeof(int) + (size_t)(ncells / 1024 + 2) * sizeof(int);
+    size_t cells = (size_t)(NCLS * ncells + 1) * 2 * sizeof(int) + (size_t)ncells * 2 * sizeof(int) +
+                   (size_t)(NCLS * ncells / 1024 + 2) * sizeof(int);
     size_t bodies = (size_t)kcap * (60 * sizeof(double) + 3 * sizeof(int));
     size_t slots = (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R) + sizeof(int));
     // relabel scratch: offsets and forces in the new slot order, one root mark per particle
@@ -558,7 +559,8 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   if (!morton && !S.win) S.G = p->cells_per_group > 0 ? p->cells_per_group : (DIM == 2 ? 3 : 1);
   S.ngx = (S.ncell[0] + S.G - 1) / S.G;
   S.ngroups = morton ? S.ncells : (S.win ? (n + 31) / 32 : S.ngx * S.ncell[1] * S.ncell[2]);
-  S.ncblk = (S.ncells + 1023) / 1024;
+  S.nkey = NCLS * S.ncells;
+  S.ncblk = (S.nkey + 1023) / 1024;
   // ------------------------------------------------------------------ allocations
   auto A = [&](auto** ptr, size_t cnt) { return dalloc(M, ptr, cnt); };
   for (PBank<R>* B : {&S.P, &S.Q}) {
@@ -594,8 +596,8 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   SPH_CU(cudaMemsetAsync(S.disp, 0, sizeof(unsigned long long), stream));
   int** ix[] = {&S.key, &S.where, &S.tkey, &S.tloc, &S.bucket, &S.perm, &S.tshift};
   for (int** f : ix) SPH_TRY(A(f, (size_t)n));
-  SPH_TRY(A(&S.cstart, (size_t)S.ncells + 1));
-  SPH_TRY(A(&S.ccount, (size_t)S.ncells));
+  SPH_TRY(A(&S.cstart, (size_t)S.nkey + 1));
+  SPH_TRY(A(&S.ccount, (size_t)S.nkey));
   SPH_TRY(A(&S.cblk, (size_t)S.ncblk + 1));
   std::vector<int> l2k, k2l;
   if (morton) {
@@ -639,7 +641,7 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   Scene<R>* dself;
   SPH_TRY(A(&dself, 1));
   // ------------------------------------------------------------------ uploads
-  SPH_CU(cudaMemsetAsync(S.ccount, 0, sizeof(int) * S.ncells, stream));
+  SPH_CU(cudaMemsetAsync(S.ccount, 0, sizeof(int) * S.nkey, stream));
   SPH_CU(cudaMemsetAsync(S.st, 0, sizeof(double) * 8, stream));
   SPH_CU(cudaMemsetAsync(S.umax, 0, sizeof(unsigned long long), stream));
   {
@@ -658,7 +660,7 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     std::vector<double> st(8, 0.0);
     st[0] = p->dt_mode == 0 ? p->dt_fixed : 0.0;
     SPH_CU(cudaMemcpyAsync(S.st, st.data(), sizeof(double) * 8, cudaMemcpyHostToDevice, stream));
-    int pf[12] = {0, n, 0, S.ncells, 0, S.ngroups, 0, S.Kcap, 0, S.ncblk, 0, S.nslot};
+    int pf[12] = {0, n, 0, S.nkey, 0, S.ngroups, 0, S.Kcap, 0, S.ncblk, 0, S.nslot};
     SPH_CU(cudaMemcpyAsync(S.pfx1, pf, sizeof(pf), cudaMemcpyHostToDevice, stream));
     SPH_CU(cudaMemcpyAsync(S.self, &dself, sizeof(dself), cudaMemcpyHostToDevice, stream));
     SPH_CU(cudaMemcpyAsync(S.K, &K, sizeof(int), cudaMemcpyHostToDevice, stream));
@@ -739,7 +741,7 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   k_scan_top<R><<<1, 1024, 0, stream>>>(B, 1);
   k_scan_cells<R><<<grid_for(S.ncblk, 1, grid_blk), 1024, 0, stream>>>(B, 1);
   k_scatter<R><<<gp, 256, 0, stream>>>(B, 1);
-  k_rank<R><<<grid_for((int64_t)S.ncells * 32, 256, grid_part), 256, 0, stream>>>(B, 1);
+  k_rank<R><<<grid_for((int64_t)S.nkey * 32, 256, grid_part), 256, 0, stream>>>(B, 1);
   k_permute<R><<<gp, 256, 0, stream>>>(B, 1);
   k_flip<R><<<1, 32, 0, stream>>>(B, 1);
   if (meta[idx].K0 > 0) k_body_mass<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
@@ -918,6 +920,10 @@ sph_status Engine<R, DIM>::check_status(int idx, bool* nonfinite) {
   SPH_CU(cudaMemcpyAsync(st, hs[idx].status, sizeof(st), cudaMemcpyDeviceToHost, stream));
   SPH_CU(cudaStreamSynchronize(stream));
   *nonfinite = st[0] != 0;
+  if (st[3] != 0) {
+    set_error("inconsistent cell table or particle kinds (scene %d)", idx);
+    return SPH_ERR_INVALID;
+  }
   if (st[2] != 0) {
     set_error("body capacity exceeded by new bodies from solidification (scene %d)", idx);
     return SPH_ERR_CAPACITY;

@@ -84,9 +84,16 @@ template <class R>
 __device__ __forceinline__ int cell_key(const Scene<R>& S, int lin) {
   return S.lin2key ? __ldg(S.lin2key + lin) : lin;
 }
+// row-major cell index of a sort key (kind * ncells + cell key)
 template <class R>
 __device__ __forceinline__ int key_lin(const Scene<R>& S, int key) {
-  return S.key2lin ? __ldg(S.key2lin + key) : key;
+  int k = key % S.ncells;
+  return S.key2lin ? __ldg(S.key2lin + k) : k;
+}
+// sort key of a particle of kind `kind` in row-major cell `lin`
+template <class R>
+__device__ __forceinline__ int part_key(const Scene<R>& S, int kind, int lin) {
+  return kind * S.ncells + cell_key(S, lin);
 }
 template <class R>
 __device__ __forceinline__ void lin_xyz(const Scene<R>& S, int lin, int& cx, int& cy, int& cz) {
@@ -395,7 +402,7 @@ __global__ void k_bin(BatchView<R> B, int force) {
       }
     }
     int lin = c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]);
-    int key = cell_key(S, lin);
+    int key = part_key(S, S.matR[S.P.mt[i]].kind, lin);
     S.tkey[i] = key;
     S.tshift[i] = shift;
     S.tloc[i] = atomicAdd(&S.ccount[key], 1);
@@ -413,7 +420,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(BatchView<R> B, int force)
     if (!force && !rebin_now(S)) continue;
     int b = blk - __ldg(B.pfx_cblk + s);
     int c = b * 1024 + threadIdx.x;
-    int v = c < S.ncells ? S.ccount[c] : 0;
+    int v = c < S.nkey ? S.ccount[c] : 0;
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
@@ -475,7 +482,7 @@ __global__ void __launch_bounds__(1024) k_scan_cells(BatchView<R> B, int force) 
     if (!force && !rebin_now(S)) continue;
     int b = blk - __ldg(B.pfx_cblk + s);
     int c = b * 1024 + threadIdx.x;
-    int v = c < S.ncells ? S.ccount[c] : 0;
+    int v = c < S.nkey ? S.ccount[c] : 0;
     int x = v;
     for (int o = 1; o < 32; o <<= 1) {
       int y = __shfl_up_sync(FULL, x, o);
@@ -492,11 +499,11 @@ __global__ void __launch_bounds__(1024) k_scan_cells(BatchView<R> B, int force) 
       wsum[threadIdx.x] = u - t;
     }
     __syncthreads();
-    if (c < S.ncells) {
+    if (c < S.nkey) {
       S.cstart[c] = S.cblk[b] + wsum[threadIdx.x >> 5] + x - v;
       S.ccount[c] = 0;
     }
-    if (c == S.ncells - 1) S.cstart[S.ncells] = S.n;
+    if (c == S.nkey - 1) S.cstart[S.nkey] = S.n;
     __syncthreads();
   }
 }
@@ -609,17 +616,22 @@ __global__ void k_flip(BatchView<R> B, int force) {
 template <class R, int DIM>
 struct Group {
   int cx0, cy, cz, ncx, ts, te;
+  int cls;  // kind of every target of the range
 };
 
+// the targets of kind `cls` in search group grp (a cell for Morton keys, a run of G cells
+// along x for row-major keys)
 template <class R, int DIM>
-__device__ __forceinline__ Group<R, DIM> group_of(const Scene<R>& S, int grp) {
+__device__ __forceinline__ Group<R, DIM> group_of(const Scene<R>& S, int grp, int cls) {
   Group<R, DIM> G;
+  G.cls = cls;
+  int base = cls * S.ncells;
   if (S.key2lin) {  // Morton keys: one cell per group
     int lin = __ldg(S.key2lin + grp);
     lin_xyz(S, lin, G.cx0, G.cy, G.cz);
     G.ncx = 1;
-    G.ts = max(S.cstart[grp], 0);
-    G.te = min(S.cstart[grp + 1], S.n);
+    G.ts = max(S.cstart[base + grp], 0);
+    G.te = min(S.cstart[base + grp + 1], S.n);
   } else {
     int gx = grp % S.ngx, r = grp / S.ngx;
     G.cy = r % S.ncell[1];
@@ -627,41 +639,44 @@ __device__ __forceinline__ Group<R, DIM> group_of(const Scene<R>& S, int grp) {
     G.cx0 = gx * S.G;
     G.ncx = min(S.G, S.ncell[0] - G.cx0);
     int lin0 = G.cx0 + S.ncell[0] * (G.cy + S.ncell[1] * G.cz);
-    G.ts = max(S.cstart[lin0], 0);
-    G.te = min(S.cstart[lin0 + G.ncx], S.n);
+    G.ts = max(S.cstart[base + lin0], 0);
+    G.te = min(S.cstart[base + lin0 + G.ncx], S.n);
   }
   return G;
 }
 
-// Target ranges of search group g, one per call of next(): a cell (Morton keys) or a run of
-// cells along x (row-major keys) gives one range; in window mode (row-major keys) group g is
-// the 32 consecutive sorted particles [32 g, 32 g + 32), split where they cross from one row
-// of cells (cy, cz) to the next, each part with the x range of cells it spans.  All lanes of
-// the warp call next() together.
+// Target ranges of search group g, one per call of next(), each of a single kind: the
+// fluid, rigid and wall runs of a cell (Morton keys) or of a run of cells along x (row-major
+// keys); in window mode (row-major keys) group g is the 32 consecutive sorted particles
+// [32 g, 32 g + 32), split where they cross from one row of cells (cy, cz) or one kind to
+// the next, each part with the x range of cells it spans.  All lanes of the warp call next()
+// together.
 template <class R, int DIM>
 struct GroupIter {
-  int ts, te;
-  bool done;
+  int ts, te, cls;
   __device__ GroupIter(const Scene<R>& S, int g) {
-    done = false;
+    cls = 0;
     ts = S.win ? 32 * g : 0;
     te = S.win ? min(ts + 32, S.n) : 0;
   }
   __device__ bool next(const Scene<R>& S, int g, int lane, Group<R, DIM>& G) {
     if (!S.win) {
-      if (done) return false;
-      done = true;
-      G = group_of<R, DIM>(S, g);
-      return true;
+      while (cls < NCLS) {
+        G = group_of<R, DIM>(S, g, cls++);
+        if (G.te > G.ts) return true;
+      }
+      return false;
     }
     if (ts >= te) return false;
     int i = ts + lane;
+    int key = i < te ? S.key[i] : 0;
     int cx = 0, cy = 0, cz = 0;
-    if (i < te) lin_xyz(S, key_lin(S, S.key[i]), cx, cy, cz);
-    int row = cy + S.ncell[1] * cz;
+    lin_xyz(S, key_lin(S, key), cx, cy, cz);
+    int row = key / S.ncell[0];  // (kind, cy, cz): ncells is a multiple of ncell[0]
     int row0 = __shfl_sync(FULL, row, 0);
     unsigned same = __ballot_sync(FULL, i < te && row == row0);
     int cnt = __popc(same);  // sorted keys: the lanes of the first row form a prefix
+    G.cls = __shfl_sync(FULL, key, 0) / S.ncells;
     G.cx0 = __shfl_sync(FULL, cx, 0);
     G.ncx = __shfl_sync(FULL, cx, cnt - 1) - G.cx0 + 1;
     G.cy = __shfl_sync(FULL, cy, 0);
@@ -679,8 +694,7 @@ template <class R>
 __device__ __forceinline__ void target_pos(const Scene<R>& S, int i, int cx0, R* p) {
   p[0] = S.P.px[i]; p[1] = S.P.py[i]; p[2] = S.P.pz[i];
   if (sizeof(R) == 4 && !S.key2lin) {
-    int lin = S.key[i];
-    int cx = lin % S.ncell[0];
+    int cx = S.key[i] % S.ncell[0];  // ncells is a multiple of ncell[0]
     p[0] += (R)(cx - cx0) * S.ellR[0];
   }
 }
@@ -734,10 +748,11 @@ __device__ __forceinline__ R dsub(R a, R b) {
   return a - b;
 }
 
-// generic traversal.  Pol provides: stage(S, j, lane), active, tp[3], idx,
-// bool accept(k) (candidate filter for the hit mask), pair(S, k, j, dx, dy, dz, r2), and for
-// FP64 scenes FP32 copies fx/fy/fz of the staged positions and tf of the target (rc2f: the
-// FP32 pre-test radius, squared, with the margin of the rounding of those copies).
+// generic traversal.  Pol provides: stage(S, j, lane), active, tp[3], idx, cmask (the
+// candidate kinds visited, a bit per kind, the same for the whole warp), pair(S, k, j, dx,
+// dy, dz, r2), and for FP64 scenes FP32 copies fx/fy/fz of the staged positions and tf of the
+// target (rc2f: the FP32 pre-test radius, squared, with the margin of the rounding of those
+// copies).  In every neighbour cell the candidates come kind by kind (fluid, rigid, wall).
 template <class R, int DIM, class Pol>
 __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>& G, Pol& pol, int lane, R rc2,
                                          float rc2f) {
@@ -751,45 +766,49 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
         pol.cox = ox;
         pol.cdy = dy;
         pol.cdz = dz;
-        int cs = max(S.cstart[key], 0), ce = min(S.cstart[key + 1], S.n);
-        for (int cb = cs; cb < ce; cb += 32) {
-          int cnt = min(32, ce - cb);
-          __syncwarp();
-          if (lane < cnt) pol.stage(S, cb + lane, lane);
-          __syncwarp();
-          unsigned mask = 0u;
-          if (pol.active) {
-            if constexpr (sizeof(R) == 8) {
-              // FP64 scenes: an FP32 test with a margin keeps a superset of the pairs, the
-              // exact FP64 test below decides each of them (the result is the exact set)
-              float shf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
-              for (int k = 0; k < cnt; k++) {
-                float dx = (pol.tf[0] - pol.fx[k]) - shf[0];
-                float dy2 = (pol.tf[1] - pol.fy[k]) - shf[1];
-                float dz2 = DIM == 3 ? (pol.tf[2] - pol.fz[k]) - shf[2] : 0.f;
-                float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-                if (r2 < rc2f && cb + k != pol.idx && pol.accept(k)) mask |= 1u << k;
-              }
-            } else {
-              for (int k = 0; k < cnt; k++) {
-                R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sh[0]);
-                R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
-                R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
-                R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
-                if (r2 < rc2 && cb + k != pol.idx && pol.accept(k)) mask |= 1u << k;
+        for (int cc = 0; cc < NCLS; cc++) {
+          if (!((pol.cmask >> cc) & 1u)) continue;
+          int kk = cc * S.ncells + key;
+          int cs = max(S.cstart[kk], 0), ce = min(S.cstart[kk + 1], S.n);
+          for (int cb = cs; cb < ce; cb += 32) {
+            int cnt = min(32, ce - cb);
+            __syncwarp();
+            if (lane < cnt) pol.stage(S, cb + lane, lane);
+            __syncwarp();
+            unsigned mask = 0u;
+            if (pol.active) {
+              if constexpr (sizeof(R) == 8) {
+                // FP64 scenes: an FP32 test with a margin keeps a superset of the pairs, the
+                // exact FP64 test below decides each of them (the result is the exact set)
+                float shf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
+                for (int k = 0; k < cnt; k++) {
+                  float dx = (pol.tf[0] - pol.fx[k]) - shf[0];
+                  float dy2 = (pol.tf[1] - pol.fy[k]) - shf[1];
+                  float dz2 = DIM == 3 ? (pol.tf[2] - pol.fz[k]) - shf[2] : 0.f;
+                  float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+                  if (r2 < rc2f && cb + k != pol.idx) mask |= 1u << k;
+                }
+              } else {
+                for (int k = 0; k < cnt; k++) {
+                  R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sh[0]);
+                  R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
+                  R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
+                  R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
+                  if (r2 < rc2 && cb + k != pol.idx) mask |= 1u << k;
+                }
               }
             }
-          }
-          pol.hits += __popc(mask);
-          while (mask) {
-            int k = __ffs(mask) - 1;
-            mask &= mask - 1;
-            R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sh[0]);
-            R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
-            R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
-            R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
-            if (sizeof(R) == 8 && !(r2 < rc2)) continue;
-            pol.pair(S, k, cb + k, dx, dy2, dz2, r2);
+            pol.hits += __popc(mask);
+            while (mask) {
+              int k = __ffs(mask) - 1;
+              mask &= mask - 1;
+              R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sh[0]);
+              R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
+              R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
+              R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
+              if (sizeof(R) == 8 && !(r2 < rc2)) continue;
+              pol.pair(S, k, cb + k, dx, dy2, dz2, r2);
+            }
           }
         }
       }

@@ -57,8 +57,9 @@ struct SearchPol {
   R *sx, *sy, *sz;
   float *fx, *fy, *fz;  // FP32 copies of the staged positions (FP64 scenes)
   float tf[3];
-  int* sk;             // kind of every staged candidate
-  bool active, fluid, wall;
+  unsigned cmask;      // candidate kinds: a wall particle only ever reads its fluid neighbours
+                       // (extrapolation of Sec. 3.3.4), the others read all
+  bool active, fluid;
   int idx, tx, n, maxnb, cnt;
   int cox, cdy, cdz;
   int* list;
@@ -68,10 +69,7 @@ struct SearchPol {
   __device__ void stage(const Scene<R>& S, int j, int lane) {
     sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
     if (sizeof(R) == 8) { fx[lane] = (float)sx[lane]; fy[lane] = (float)sy[lane]; fz[lane] = (float)sz[lane]; }
-    sk[lane] = S.matR[S.P.mt[j]].kind;
   }
-  // a wall particle only ever reads its fluid neighbours (extrapolation of Sec. 3.3.4)
-  __device__ bool accept(int k) const { return !wall || sk[k] == KFLUID; }
   __device__ void pair(const Scene<R>& S, int, int j, R, R, R, R r2) {
     int code = (cox - tx + 1) + 3 * (cdy + 1) + 9 * (cdz + 1);
     if (cnt < maxnb) list[(size_t)cnt * n + idx] = (j << 5) | code;
@@ -84,13 +82,11 @@ template <class R, int DIM>
 __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
   __shared__ R sm[4][3][32];
   __shared__ float smf[sizeof(R) == 8 ? 4 : 1][3][32];
-  __shared__ int smk[4][32];
   int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   SearchPol<R, DIM> pol;
   pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
   int wf = sizeof(R) == 8 ? wib : 0;
   pol.fx = smf[wf][0]; pol.fy = smf[wf][1]; pol.fz = smf[wf][2];
-  pol.sk = smk[wib];
   int total = __ldg(B.pfx_grp + B.nsc);
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int g = gw; g < total; g += nw) {
@@ -110,9 +106,10 @@ __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
       pol.active = valid;
       if (!__any_sync(FULL, valid)) continue;
       pol.idx = valid ? i : -1;
-      int tkind = valid ? S.matR[S.P.mt[i]].kind : KFLUID;
+      int tkind = valid ? S.matR[S.P.mt[i]].kind : G.cls;
+      if (tkind != G.cls) S.status[3] = 1;  // a kind changed without a rebuild (never expected)
       pol.fluid = valid && tkind == KFLUID;
-      pol.wall = tkind == KWALL;
+      pol.cmask = G.cls == KWALL ? 1u << KFLUID : (1u << NCLS) - 1u;
       pol.tx = 0;
       if (valid) {
         target_pos(S, i, G.cx0, pol.tp);
@@ -174,11 +171,13 @@ __device__ __forceinline__ void pack_delta(const Scene<float>& S, const float* t
 }
 
 // scan of the 3^d cells around target i (targets whose list overflowed); calls
-// f(j, code) for every candidate j != i in the traversal order of k_search
+// f(j, code) for every candidate j != i of the kinds its list holds, in the traversal order
+// of k_search
 template <class R, int DIM, class F>
 __device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
   int cx, cy, cz;
   lin_xyz(S, key_lin(S, S.key[i]), cx, cy, cz);
+  unsigned cm = S.key[i] / S.ncells == KWALL ? 1u << KFLUID : (1u << NCLS) - 1u;
   const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
   for (int dz = zlo; dz <= zhi; dz++)
     for (int dy = -1; dy <= 1; dy++)
@@ -193,10 +192,13 @@ __device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
         if (skip) continue;
         if (DIM == 2) c[2] = 0;
         int key = cell_key(S, c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]));
-        int a = max(S.cstart[key], 0), e = min(S.cstart[key + 1], S.n);
         int code = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-        for (int j = a; j < e; j++)
-          if (j != i) f(j, code);
+        for (int cc = 0; cc < NCLS; cc++) {
+          if (!((cm >> cc) & 1u)) continue;
+          int a = max(S.cstart[cc * S.ncells + key], 0), e = min(S.cstart[cc * S.ncells + key + 1], S.n);
+          for (int j = a; j < e; j++)
+            if (j != i) f(j, code);
+        }
       }
 }
 
@@ -264,12 +266,14 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
     int i = g - __ldg(B.pfx_part + s);
     int kind = S.matR[S.P.mt[i]].kind;
     if (kind == KFLUID) continue;
+    // a wall particle's list (and its cell scan) holds fluid neighbours only; a rigid
+    // particle's holds all kinds and reads the fluid ones
+    bool wall = kind == KWALL;
     R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
     R S0 = R(0), P0 = R(0), Rv[3] = {R(0), R(0), R(0)}, U[3] = {R(0), R(0), R(0)};
     auto visit = [&](int j, int code) {
       if constexpr (sizeof(R) == 4) {
-        float4 c = S.pc[j];
-        if ((__float_as_int(c.z) >> 16) != KFLUID) return;
+        if (!wall && (__float_as_int(S.pc[j].z) >> 16) != KFLUID) return;
         float4 a = S.pa[j];
         R d[3];
         pack_delta<DIM>(S, ti, a, code, d);
@@ -283,7 +287,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
         Rv[0] += rw * d[0]; Rv[1] += rw * d[1]; Rv[2] += rw * d[2];
         U[0] += b.x * W; U[1] += b.y * W; U[2] += b.z * W;
       } else {
-        if (S.matR[S.P.mt[j]].kind != KFLUID) return;
+        if (!wall && S.matR[S.P.mt[j]].kind != KFLUID) return;
         R d[3];
         list_delta<R, DIM>(S, ti, j, code, d);
         R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
@@ -306,8 +310,8 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
         for (; k < cnt; k++) {
           int en = k + 1 < cnt ? __ldg(L + (size_t)(k + 1) * S.n) : 0;
           int j = e >> 5;
-          float4 c = S.pc[j], a = S.pa[j], b = S.pb[j];
-          if ((__float_as_int(c.z) >> 16) == KFLUID) {
+          float4 a = S.pa[j], b = S.pb[j];
+          if (wall || (__float_as_int(S.pc[j].z) >> 16) == KFLUID) {
             R d[3];
             pack_delta<DIM>(S, ti, a, e & 31, d);
             R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
