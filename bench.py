@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--key-order", type=int, default=0)
+    ap.add_argument("--cells-per-group", type=int, default=0,
+                    help="row-major keys: cells along x per search warp (0 automatic, -1 windows of 32 particles)")
     ap.add_argument("--dx", type=float, default=None, help="lattice spacing (default 0.01 tank, 0.005 powder)")
     ap.add_argument("--skin", type=float, default=0.3, help="Verlet skin in units of h")
     ap.add_argument("--workload", default="tank3d", choices=["tank3d", "powder", "batch", "serve"],
@@ -366,7 +368,7 @@ def main():
     # cell layout and launch shape: the autotuner's pick on this workload (steps 30-60 from
     # the initial state), or the command-line layout with --no-tune
     if args.no_tune:
-        layout = dict(key_order=args.key_order, skin=args.skin * sc["params"]["h"])
+        layout = dict(key_order=args.key_order, cells_per_group=args.cells_per_group, skin=args.skin * sc["params"]["h"])
         launch = dict(sweep_block=256, sweep_waves=0, search_waves=0)
         tuned = None
     else:

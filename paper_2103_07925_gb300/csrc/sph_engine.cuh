@@ -192,7 +192,8 @@ class Engine {
   // launch shape of the pair sweeps (density, extrapolation, force) and of the search:
   // threads per block of the sweeps, and resident waves of blocks per SM for both
   int sweep_block = 256, sweep_waves = 0, search_waves = 0;
-  int grid_sweep = 0;
+  int grid_sweep = 0;                    // force sweep (plain instantiation)
+  int grid_tvf = 0, grid_dens = 0, grid_extrap = 0;  // the other sweeps, each by its own occupancy
   int kernels_per_step = 0;
   int sms = 0;
   int64_t steps_taken = 0;
@@ -233,13 +234,19 @@ class Engine {
 
   // grids of the sweeps and the search from the launch shape (0 waves: the occupancy limit)
   sph_status apply_launch() {
-    int bs = 0, bw = 0;
+    int bs = 0, bw = 0, bt = 0, bd = 0, be = 0;
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_force<R, DIM, false>, sweep_block, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, k_force<R, DIM, true>, sweep_block, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_density<R, DIM>, sweep_block, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_extrap<R, DIM>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, k_search<R, DIM>, 128, 0));
-    bs = std::max(1, bs);
-    bw = std::max(1, bw);
-    grid_sweep = sms * (sweep_waves > 0 ? std::min(sweep_waves, bs) : bs);
-    grid_warp = sms * (search_waves > 0 ? std::min(search_waves, bw) : bw);
+    // resident blocks per SM: the kernel's occupancy, capped by the requested waves
+    auto waves = [&](int occ, int req) { occ = std::max(1, occ); return sms * (req > 0 ? std::min(req, occ) : occ); };
+    grid_sweep = waves(bs, sweep_waves);
+    grid_tvf = waves(bt, sweep_waves);
+    grid_dens = waves(bd, sweep_waves);
+    grid_extrap = waves(be, sweep_waves);
+    grid_warp = waves(bw, search_waves);
     graph_dirty = true;
     return SPH_OK;
   }
@@ -747,11 +754,10 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   if (meta[idx].K0 > 0) k_body_mass<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
   int gw = grid_for((int64_t)S.ngroups * 32, 128, grid_warp);
-  int gsw = grid_for(n, sweep_block, grid_sweep);
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
-  k_extrap<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
-  if (S.tvf || S.any_conc) k_force<R, DIM, true><<<gsw, sweep_block, 0, stream>>>(B);
-  else k_force<R, DIM, false><<<gsw, sweep_block, 0, stream>>>(B);
+  k_extrap<R, DIM><<<grid_for(n, sweep_block, grid_extrap), sweep_block, 0, stream>>>(B);
+  if (S.tvf || S.any_conc) k_force<R, DIM, true><<<grid_for(n, sweep_block, grid_tvf), sweep_block, 0, stream>>>(B);
+  else k_force<R, DIM, false><<<grid_for(n, sweep_block, grid_sweep), sweep_block, 0, stream>>>(B);
   if (meta[idx].K0 > 0) k_body_reduce<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
   SPH_CU(cudaGetLastError());
@@ -796,6 +802,9 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   int gs = grid_for(ns, 128, 1 << 20);
   int gw = grid_for(ng * 32, 128, grid_warp);
   int gsw = grid_for(np, sweep_block, grid_sweep);
+  int gst = grid_for(np, sweep_block, grid_tvf);
+  int gsd = grid_for(np, sweep_block, grid_dens);
+  int gse = grid_for(np, sweep_block, grid_extrap);
   int gb = grid_for(nb, 1, grid_blk);
   int gcb = grid_for(ncb, 1, grid_blk);
   int kcount = 0, stage = 0;
@@ -831,11 +840,11 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   rec();
-  k_density<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
+  k_density<R, DIM><<<gsd, sweep_block, 0, stream>>>(B);
   rec();
-  k_extrap<R, DIM><<<gsw, sweep_block, 0, stream>>>(B);
+  k_extrap<R, DIM><<<gse, sweep_block, 0, stream>>>(B);
   rec();
-  if (any_tvf) { k_force<R, DIM, true><<<gsw, sweep_block, 0, stream>>>(B); kcount++; }
+  if (any_tvf) { k_force<R, DIM, true><<<gst, sweep_block, 0, stream>>>(B); kcount++; }
   if (any_plain) { k_force<R, DIM, false><<<gsw, sweep_block, 0, stream>>>(B); kcount++; }
   kcount--;  // one force launch is counted with the fixed stages
   rec();

@@ -263,7 +263,10 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     int s = find_scene(B.pfx_part, B.nsc, g);
     const Scene<R>& S = *B.sc[s];
-    int i = g - __ldg(B.pfx_part + s);
+    // kind-major keys: the wall and rigid particles follow the fluid ones, from the start of
+    // the rigid key range on
+    int i = S.cstart[S.ncells] + (g - __ldg(B.pfx_part + s));
+    if (i >= S.n) continue;
     int kind = S.matR[S.P.mt[i]].kind;
     if (kind == KFLUID) continue;
     // a wall particle's list (and its cell scan) holds fluid neighbours only; a rigid
@@ -529,9 +532,11 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, Target<
 
 // resident blocks per SM the force sweep is compiled for (register budget)
 // 1: the velocity and material records of a list entry are loaded with its position
-// (speculatively, before the distance test); 0: only for pairs inside the support
+// (speculatively, before the distance test); 0: only for pairs inside the support (about
+// two thirds of the entries at a skin of 0.3 h), which measured faster once every warp's
+// targets are of one kind
 #ifndef SPH_FORCE_SPECULATE
-#define SPH_FORCE_SPECULATE 1
+#define SPH_FORCE_SPECULATE 0
 #endif
 #ifndef SPH_FORCE_MIN_BLOCKS
 #define SPH_FORCE_MIN_BLOCKS 4
