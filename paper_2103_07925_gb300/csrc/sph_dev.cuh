@@ -50,6 +50,20 @@ struct PBank {  // particle fields (one bank)
   R* C;                 // concentration (null when no phase carries one)
 };
 
+// What the FP32 pair sweeps read for every list entry, besides the neighbour records: a
+// copy lives in the scene descriptor, and launches over a single scene also take it by value
+// (kernel parameters are read from the constant bank: no cache traffic and no registers to
+// hold them across the list walk).  Nothing in it changes after the scene is created.
+struct SweepK {
+  const float4 *pa, *pb, *pc, *pd;  // packed neighbour records (pd: TVF / concentration)
+  const int* nbl;                   // neighbour lists, entry k of particle i at nbl[k * n + i]
+  int n;
+  float ell[3];                     // cell edges (positions are relative to the cell origin)
+  float rc2, sig_dw, inv_h;         // r_c^2, dW/dr = sig_dw w'(r / h)
+  float dx, kc, dc;                 // contact: cut-off distance, spring and damper
+  int any_heat, any_conc, tvf;
+};
+
 template <class R>
 struct Scene {
   // ---------------------------------------------------------------- constants
@@ -93,6 +107,7 @@ struct Scene {
   // pa = (x, y, z, rho), pb = (u or extrapolated v_w, p or p_w), pc = (T, V, material |
   // kind << 16, body)
   float4 *pa, *pb, *pc;
+  SweepK k;            // FP32 scenes: the per-entry constants of the pair sweeps
   float4* pd;          // (u~ - u, C): transport-velocity formulation and concentration
   int* nbl;            // neighbour lists: entry k of particle i at nbl[k * n + i] = j << 5 | cell code
   int* nbc;            // neighbour count of each particle (may exceed maxnb: then cells are scanned)

@@ -194,6 +194,7 @@ class Engine {
   int sweep_block = 256, sweep_waves = 0, search_waves = 0;
   int grid_sweep = 0;                    // force sweep (plain instantiation)
   int grid_tvf = 0, grid_dens = 0, grid_extrap = 0;  // the other sweeps, each by its own occupancy
+  int grid_sweep1 = 0, grid_tvf1 = 0;   // force sweeps of launches over a single scene
   int kernels_per_step = 0;
   int sms = 0;
   int64_t steps_taken = 0;
@@ -234,9 +235,11 @@ class Engine {
 
   // grids of the sweeps and the search from the launch shape (0 waves: the occupancy limit)
   sph_status apply_launch() {
-    int bs = 0, bw = 0, bt = 0, bd = 0, be = 0;
-    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_force<R, DIM, false>, sweep_block, 0));
-    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, k_force<R, DIM, true>, sweep_block, 0));
+    int bs = 0, bw = 0, bt = 0, bd = 0, be = 0, bs1 = 0, bt1 = 0;
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_force<R, DIM, false, false>, sweep_block, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, k_force<R, DIM, true, false>, sweep_block, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs1, k_force<R, DIM, false, true>, sweep_block, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt1, k_force<R, DIM, true, true>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_density<R, DIM>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_extrap<R, DIM>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, k_search<R, DIM>, 128, 0));
@@ -244,6 +247,8 @@ class Engine {
     auto waves = [&](int occ, int req) { occ = std::max(1, occ); return sms * (req > 0 ? std::min(req, occ) : occ); };
     grid_sweep = waves(bs, sweep_waves);
     grid_tvf = waves(bt, sweep_waves);
+    grid_sweep1 = waves(bs1, sweep_waves);
+    grid_tvf1 = waves(bt1, sweep_waves);
     grid_dens = waves(bd, sweep_waves);
     grid_extrap = waves(be, sweep_waves);
     grid_warp = waves(bw, search_waves);
@@ -715,6 +720,16 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     cudaMemcpyAsync(dmat, in->material, 4 * nd, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(dbody, in->body, 4 * nd, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(dslot, slot.data(), 4 * nd, cudaMemcpyHostToDevice, stream);
+    S.k = SweepK{};
+    if (sizeof(R) == 4) {
+      S.k.pa = S.pa; S.k.pb = S.pb; S.k.pc = S.pc; S.k.pd = S.pd;
+      S.k.nbl = S.nbl;
+      S.k.n = n;
+      for (int d = 0; d < 3; d++) S.k.ell[d] = (float)S.ellR[d];
+      S.k.rc2 = (float)S.rc2R; S.k.sig_dw = (float)S.sig_dw; S.k.inv_h = (float)S.inv_h;
+      S.k.dx = (float)S.dxR; S.k.kc = (float)S.kcR; S.k.dc = (float)S.dcR;
+      S.k.any_heat = S.any_heat; S.k.any_conc = S.any_conc; S.k.tvf = S.tvf;
+    }
     SPH_CU(cudaMemcpyAsync(dself, &S, sizeof(S), cudaMemcpyHostToDevice, stream));
     ImportArgs ia{dpos, dvel, dmass, ddens, dtemp, in->wall_velocity ? dwv : nullptr,
                   in->wall_temperature ? dwt : nullptr, dmat, dbody, dslot, in->concentration ? dconc : nullptr};
@@ -756,8 +771,10 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   int gw = grid_for((int64_t)S.ngroups * 32, 128, grid_warp);
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   k_extrap<R, DIM><<<grid_for(n, sweep_block, grid_extrap), sweep_block, 0, stream>>>(B);
-  if (S.tvf || S.any_conc) k_force<R, DIM, true><<<grid_for(n, sweep_block, grid_tvf), sweep_block, 0, stream>>>(B);
-  else k_force<R, DIM, false><<<grid_for(n, sweep_block, grid_sweep), sweep_block, 0, stream>>>(B);
+  if (S.tvf || S.any_conc)
+    k_force<R, DIM, true, true><<<grid_for(n, sweep_block, grid_tvf1), sweep_block, 0, stream>>>(B, S.k);
+  else
+    k_force<R, DIM, false, true><<<grid_for(n, sweep_block, grid_sweep1), sweep_block, 0, stream>>>(B, S.k);
   if (meta[idx].K0 > 0) k_body_reduce<R><<<grid_for(S.Kcap, 1, grid_blk), 128, 0, stream>>>(B, 0);
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
   SPH_CU(cudaGetLastError());
@@ -844,8 +861,16 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_extrap<R, DIM><<<gse, sweep_block, 0, stream>>>(B);
   rec();
-  if (any_tvf) { k_force<R, DIM, true><<<gst, sweep_block, 0, stream>>>(B); kcount++; }
-  if (any_plain) { k_force<R, DIM, false><<<gsw, sweep_block, 0, stream>>>(B); kcount++; }
+  if (ns == 1) {  // one scene: its sweep constants by value
+    const SweepK& k1 = hs[act[0]].k;
+    if (any_tvf) k_force<R, DIM, true, true><<<grid_for(np, sweep_block, grid_tvf1), sweep_block, 0, stream>>>(B, k1);
+    else k_force<R, DIM, false, true><<<grid_for(np, sweep_block, grid_sweep1), sweep_block, 0, stream>>>(B, k1);
+    kcount++;
+  } else {
+    SweepK k0{};
+    if (any_tvf) { k_force<R, DIM, true, false><<<gst, sweep_block, 0, stream>>>(B, k0); kcount++; }
+    if (any_plain) { k_force<R, DIM, false, false><<<gsw, sweep_block, 0, stream>>>(B, k0); kcount++; }
+  }
   kcount--;  // one force launch is counted with the fixed stages
   rec();
   if (any_body) { k_body_reduce<R><<<gb, 128, 0, stream>>>(B, 1); kcount++; }

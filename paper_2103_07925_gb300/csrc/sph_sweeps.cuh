@@ -163,11 +163,23 @@ __device__ __forceinline__ void list_delta(const Scene<R>& S, const R* ti, int j
 
 // the same offset from a packed FP32 neighbour record
 template <int DIM>
-__device__ __forceinline__ void pack_delta(const Scene<float>& S, const float* ti, float4 a, int code, float* d) {
+__device__ __forceinline__ void pack_delta(const SweepK& K, const float* ti, float4 a, int code, float* d) {
   int ox = code % 3 - 1, oy = (code / 3) % 3 - 1, oz = code / 9 - 1;
-  d[0] = (ti[0] - a.x) - (float)ox * S.ellR[0];
-  d[1] = (ti[1] - a.y) - (float)oy * S.ellR[1];
-  d[2] = DIM == 3 ? (ti[2] - a.z) - (float)oz * S.ellR[2] : 0.f;
+  d[0] = (ti[0] - a.x) - (float)ox * K.ell[0];
+  d[1] = (ti[1] - a.y) - (float)oy * K.ell[1];
+  d[2] = DIM == 3 ? (ti[2] - a.z) - (float)oz * K.ell[2] : 0.f;
+}
+template <int DIM>
+__device__ __forceinline__ void pack_delta(const Scene<float>& S, const float* ti, float4 a, int code, float* d) {
+  pack_delta<DIM>(S.k, ti, a, code, d);
+}
+
+// the sweep constants of a launch: the kernel parameter (launches over one scene) or the
+// scene descriptor's copy
+template <bool ONE>
+__device__ __forceinline__ const SweepK& sweep_k(const SweepK& kp, const SweepK& ks) {
+  if constexpr (ONE) return kp;
+  else return ks;
 }
 
 // scan of the 3^d cells around target i (targets whose list overflowed); calls
@@ -360,7 +372,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
 // ---------------------------------------------------------------- forces and heat
 template <class R>
 struct Target {
-  int kind, body, mi;  // kind, body id, material index
+  int i, kind, body, mi;  // index, kind, body id, material index
   const MatR<R>* M;
   R rho, p, V2, eta, kap, T;
   R u[3], ve[3];
@@ -451,35 +463,37 @@ __device__ __forceinline__ void force_pair(const Scene<R>& S, Target<R>& t, int 
 
 // force_pair on packed FP32 neighbour records (same arithmetic in the same order)
 template <int DIM, bool TVF>
-__device__ __forceinline__ void force_pair_packed(const Scene<float>& S, Target<float>& t, int j, const float* d,
-                                                  float r2, float4 a, float4 b, float4 c, float* acc, float& heat) {
+__device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const SweepK& K, Target<float>& t, int j,
+                                                  const float* d, float r2, float4 a, float4 b, float4 c, float* acc,
+                                                  float& heat) {
   int mk = __float_as_int(c.z);
   int bk = mk >> 16;
-  const MatR<float>& Bm = S.matR[mk & 0xffff];
+  int mj = mk & 0xffff;
+  bool same = mj == t.mi;  // the material constants of a pair of one material are the target's
   float inv_r = rsqrt_<float>(r2);
   float r = r2 * inv_r;
-  float dW = S.sig_dw * quintic_dw<float>(r * S.inv_h);
+  float dW = K.sig_dw * quintic_dw<float>(r * K.inv_h);
   float ex = d[0] * inv_r, ey = d[1] * inv_r, ez = d[2] * inv_r;
   float Vj = c.y;
-  if (S.any_heat) {
+  if (K.any_heat) {
     float Tb = c.x;
     if (!(bk == KWALL && isnan(Tb))) {
-      float kb = bk == KWALL ? t.kap : Bm.kappa;
+      float kb = bk == KWALL || same ? t.kap : S.matR[mj].kappa;
       float ks = t.kap + kb;
       float kab = ks > 0.f ? qdiv<float>(4.f * t.kap * kb, ks) : 0.f;
       heat += Vj * kab * (t.T - Tb) * inv_r * dW;
     }
   }
-  if (TVF && S.any_conc && bk != KWALL) {  // concentration: the heat form with the diffusivity
-    float Db = Bm.D, Ds = t.D + Db;
+  if (TVF && K.any_conc && bk != KWALL) {  // concentration: the heat form with the diffusivity
+    float Db = same ? t.D : S.matR[mj].D, Ds = t.D + Db;
     float Dab = Ds > 0.f ? qdiv<float>(4.f * t.D * Db, Ds) : 0.f;
-    t.cs += Vj * Dab * (t.C - S.pd[j].w) * inv_r * dW;
+    t.cs += Vj * Dab * (t.C - K.pd[j].w) * inv_r * dW;
   }
   if (t.kind == KFLUID) {
     float rhoj, pj = b.w, etaj;
     if (bk == KFLUID) {
       rhoj = a.w;
-      etaj = Bm.eta;
+      etaj = same ? t.eta : S.matR[mj].eta;
     } else {  // wall / rigid: inverse EOS of fluid i for the extrapolated pressure
       rhoj = t.M->rho0 * (pj * t.M->inv_p0 + 1.f);
       etaj = t.eta;
@@ -492,10 +506,10 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, Target<
     acc[0] += coef * (-pt * ex + vis * (t.u[0] - b.x));
     acc[1] += coef * (-pt * ey + vis * (t.u[1] - b.y));
     acc[2] += coef * (-pt * ez + vis * (t.u[2] - b.z));
-    if (TVF && S.tvf) {  // 1/2 (A_i + A_j) . e_ij with A = rho u (u~ - u), zero for boundaries
+    if (TVF && K.tvf) {  // 1/2 (A_i + A_j) . e_ij with A = rho u (u~ - u), zero for boundaries
       float si = t.tv[0] * ex + t.tv[1] * ey + t.tv[2] * ez, sj = 0.f, rj = 0.f;
       if (bk == KFLUID) {
-        float4 w = S.pd[j];
+        float4 w = K.pd[j];
         sj = w.x * ex + w.y * ey + w.z * ez;
         rj = rhoj;
       }
@@ -505,25 +519,27 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, Target<
       t.bs[0] += coef * ex; t.bs[1] += coef * ey; t.bs[2] += coef * ez;
     }
   } else if (bk == KFLUID) {  // rigid target: -m_j a_jr seen from fluid particle j
+    const MatR<float>& Bm = S.matR[mj];
     float rhoj = a.w, pj = b.w;
     float rs = Bm.rho0 * (t.p * Bm.inv_p0 + 1.f);
     float pt = qdiv<float>(rs * pj + rhoj * t.p, rhoj + rs);
     float coef = (Vj * Vj + t.V2) * dW;
     float vis = Bm.eta * inv_r;
-    acc[0] -= coef * (pt * ex + vis * (b.x - t.ve[0]));
-    acc[1] -= coef * (pt * ey + vis * (b.y - t.ve[1]));
-    acc[2] -= coef * (pt * ez + vis * (b.z - t.ve[2]));
-    if (TVF && S.tvf) {  // the A_j term of a_jr (A = 0 for the rigid particle)
-      float4 w = S.pd[j];
+    float ve[3] = {S.vex[t.i], S.vey[t.i], S.vez[t.i]};
+    acc[0] -= coef * (pt * ex + vis * (b.x - ve[0]));
+    acc[1] -= coef * (pt * ey + vis * (b.y - ve[1]));
+    acc[2] -= coef * (pt * ez + vis * (b.z - ve[2]));
+    if (TVF && K.tvf) {  // the A_j term of a_jr (A = 0 for the rigid particle)
+      float4 w = K.pd[j];
       float sj = w.x * ex + w.y * ey + w.z * ez;
       acc[0] += coef * 0.5f * rhoj * b.x * sj;
       acc[1] += coef * 0.5f * rhoj * b.y * sj;
       acc[2] += coef * 0.5f * rhoj * b.z * sj;
     }
   } else if (bk == KWALL || __float_as_int(c.w) != t.body) {
-    if (r < S.dxR) {  // Eq. contactforce with tension cut-off (particle velocities, not v_w)
+    if (r < K.dx) {  // Eq. contactforce with tension cut-off (particle velocities, not v_w)
       float ev = ex * (t.u[0] - S.P.vx[j]) + ey * (t.u[1] - S.P.vy[j]) + ez * (t.u[2] - S.P.vz[j]);
-      float fn = S.kcR * (r - S.dxR) + S.dcR * ev;
+      float fn = K.kc * (r - K.dx) + K.dc * ev;
       float mn = fn < 0.f ? fn : 0.f;
       acc[0] -= mn * ex; acc[1] -= mn * ey; acc[2] -= mn * ez;
     }
@@ -543,9 +559,10 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, Target<
 #endif
 
 // TVF: instantiation with the transport-velocity and concentration terms (launched when
-// a resident scene uses either; the plain instantiation keeps its register budget)
-template <class R, int DIM, bool TVF>
-__global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R> B) {
+// a resident scene uses either; the plain instantiation keeps its register budget).
+// ONE: a launch over a single scene, whose sweep constants kp come as a kernel parameter.
+template <class R, int DIM, bool TVF, bool ONE>
+__global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(BatchView<R> B, SweepK kp) {
   int total = __ldg(B.pfx_part + B.nsc);
   int nthr = gridDim.x * blockDim.x;
   // uniform trip count so that the warp-wide pair counter sees every lane
@@ -562,6 +579,7 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
     bool mine = TVF == (S.tvf != 0 || S.any_conc != 0);
     if (g < total && kind != KWALL && mine) {
       Target<R> t;
+      t.i = i;
       t.kind = kind;
       t.mi = tm;
       t.body = S.P.body[i];
@@ -574,7 +592,7 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
       t.kap = t.M->kappa;
       t.T = S.P.T[i];
       t.u[0] = S.P.vx[i]; t.u[1] = S.P.vy[i]; t.u[2] = S.P.vz[i];
-      t.ve[0] = S.vex[i]; t.ve[1] = S.vey[i]; t.ve[2] = S.vez[i];
+      if constexpr (sizeof(R) == 8) { t.ve[0] = S.vex[i]; t.ve[1] = S.vey[i]; t.ve[2] = S.vez[i]; }
       t.tv[0] = t.tv[1] = t.tv[2] = R(0);
       t.bs[0] = t.bs[1] = t.bs[2] = R(0);
       if (TVF && S.tvf && kind == KFLUID) { t.tv[0] = S.P.tx[i]; t.tv[1] = S.P.ty[i]; t.tv[2] = S.P.tz[i]; }
@@ -582,15 +600,16 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
       if (TVF && S.any_conc) { t.C = S.P.C[i]; t.D = t.M->D; }
       R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
       R acc[3] = {R(0), R(0), R(0)}, heat = R(0);
+      const SweepK& K = sweep_k<ONE>(kp, S.k);
       auto visit = [&](int j, int code) {
         if constexpr (sizeof(R) == 4) {
-          float4 a = S.pa[j];
+          float4 a = K.pa[j];
           R d[3];
-          pack_delta<DIM>(S, ti, a, code, d);
+          pack_delta<DIM>(K, ti, a, code, d);
           R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
-          if (r2 < S.rc2R) {
-            float4 b = S.pb[j], c = S.pc[j];
-            force_pair_packed<DIM, TVF>(S, t, j, d, r2, a, b, c, acc, heat);
+          if (r2 < K.rc2) {
+            float4 b = K.pb[j], c = K.pc[j];
+            force_pair_packed<DIM, TVF>(S, K, t, j, d, r2, a, b, c, acc, heat);
             npairs++;
           }
         } else {
@@ -605,33 +624,34 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
       };
       int cnt = S.nbc[i];
       if (cnt <= S.maxnb) {
-        const int* L = S.nbl + i;
         int k = 0;
         if constexpr (sizeof(R) == 4) {
           // software pipeline: the next list entry is loaded while this pair is evaluated,
           // and the three records of a neighbour are loaded together (one latency per entry)
-          int e = k < cnt ? __ldg(L + (size_t)k * S.n) : 0;
+          const int* L = K.nbl + i;
+          int e = k < cnt ? __ldg(L + (size_t)k * K.n) : 0;
           for (; k < cnt; k++) {
-            int en = k + 1 < cnt ? __ldg(L + (size_t)(k + 1) * S.n) : 0;
+            int en = k + 1 < cnt ? __ldg(L + (size_t)(k + 1) * K.n) : 0;
             int j = e >> 5;
 #if SPH_FORCE_SPECULATE
-            float4 a = S.pa[j], b = S.pb[j], c = S.pc[j];
+            float4 a = K.pa[j], b = K.pb[j], c = K.pc[j];
 #else
-            float4 a = S.pa[j];
+            float4 a = K.pa[j];
 #endif
             float d[3];
-            pack_delta<DIM>(S, ti, a, e & 31, d);
+            pack_delta<DIM>(K, ti, a, e & 31, d);
             float r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
-            if (r2 < S.rc2R) {
+            if (r2 < K.rc2) {
 #if !SPH_FORCE_SPECULATE
-              float4 b = S.pb[j], c = S.pc[j];
+              float4 b = K.pb[j], c = K.pc[j];
 #endif
-              force_pair_packed<DIM, TVF>(S, t, j, d, r2, a, b, c, acc, heat);
+              force_pair_packed<DIM, TVF>(S, K, t, j, d, r2, a, b, c, acc, heat);
               npairs++;
             }
             e = en;
           }
         }
+        const int* L = S.nbl + i;
         for (; k < cnt; k++) {
           int e = __ldg(L + (size_t)k * S.n);
           visit(e >> 5, e & 31);
