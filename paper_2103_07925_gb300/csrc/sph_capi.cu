@@ -142,7 +142,7 @@ sph_status sph_profile(sph_scene* s, int32_t reps, double* ms_per_stage) {
 const char* sph_profile_stage_name(int32_t i) {
   static const char* const names[] = {"umax", "dt", "body_kick_drift", "kick_drift", "decide", "bin",
                                       "scan_blocks", "scan_top", "scan_cells", "scatter", "rank", "permute",
-                                      "flip", "search_density", "density", "extrap", "force", "body_reduce",
+                                      "flip", "search", "density", "extrap", "force", "body_reduce",
                                       "final", "relabel", "end_step"};
   static_assert(sizeof(names) / sizeof(names[0]) == SPH_PROFILE_STAGES, "one name per profiled stage");
   if (i < 0 || i >= SPH_PROFILE_STAGES) return "";

@@ -770,6 +770,7 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
   int gw = grid_for((int64_t)S.ngroups * 32, 128, grid_warp);
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
+  k_density<R, DIM><<<grid_for(n, sweep_block, grid_dens), sweep_block, 0, stream>>>(B);
   k_extrap<R, DIM><<<grid_for(n, sweep_block, grid_extrap), sweep_block, 0, stream>>>(B);
   if (S.tvf || S.any_conc)
     k_force<R, DIM, true, true><<<grid_for(n, sweep_block, grid_tvf1), sweep_block, 0, stream>>>(B, S.k);

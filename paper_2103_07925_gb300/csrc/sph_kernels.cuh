@@ -29,6 +29,12 @@ template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 
+// pair distance from its square for the kernel sums, correctly rounded: the pressure of a
+// weakly compressible fluid, c^2 (rho - rho_0), carries a relative error of the density sum
+// amplified by rho / (rho - rho_0), so a root through the approximate reciprocal root costs
+// the FP32 pressure its 1e-5 bound
+template <class R> __device__ __forceinline__ R pair_dist(R r2) { return sqrt(r2); }
+
 // quintic spline (Morris 1997), polynomial part: w(q) and dw/dq, valid for q < 3
 template <class R>
 __device__ __forceinline__ void quintic(R q, R& w, R& dw) {
@@ -578,6 +584,8 @@ __global__ void k_permute(BatchView<R> B, int force) {
       pz = pz - (R)d2 * S.ellR[2];
     }
     Q.px[j] = px; Q.py[j] = py; Q.pz[j] = pz;
+    // FP32: the packed positions in the new order (the density sweep reads them)
+    if constexpr (sizeof(R) == 4) S.pa[j] = make_float4(px, py, pz, P.rho[i]);
     S.xr[j] = px; S.yr[j] = py; S.zr[j] = pz;
     Q.vx[j] = P.vx[i]; Q.vy[j] = P.vy[i]; Q.vz[j] = P.vz[i];
     Q.ax[j] = P.ax[i]; Q.ay[j] = P.ay[i]; Q.az[j] = P.az[i];
@@ -699,28 +707,6 @@ __device__ __forceinline__ void target_pos(const Scene<R>& S, int i, int cx0, R*
   }
 }
 
-// neighbour cell (ox, dy, dz) of the group: key and the shift subtracted from p_i - p_j
-template <class R, int DIM>
-__device__ __forceinline__ bool stencil_cell(const Scene<R>& S, const Group<R, DIM>& G, int ox, int dy,
-                                             int dz, int& key, R* shift) {
-  int c[3] = {G.cx0 + ox, G.cy + dy, G.cz + dz};
-  int off[3] = {ox, dy, dz};
-  for (int k = 0; k < DIM; k++) {
-    shift[k] = R(0);
-    if (c[k] < 0 || c[k] >= S.ncell[k]) {
-      if (!S.per[k]) return false;
-      int w = c[k] < 0 ? 1 : -1;  // image of the cell inside the box
-      c[k] += w * S.ncell[k];
-      if (sizeof(R) == 8) shift[k] = w > 0 ? -S.LR[k] : S.LR[k];
-    }
-    if (sizeof(R) == 4) shift[k] = (R)off[k] * S.ellR[k];
-  }
-  if (DIM == 2) { c[2] = 0; shift[2] = R(0); }
-  int lin = c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]);
-  key = cell_key(S, lin);
-  return true;
-}
-
 template <class R, int DIM>
 __device__ __forceinline__ R dist2(R dx, R dy, R dz) {
   if (DIM == 2) return dx * dx + dy * dy;
@@ -748,70 +734,161 @@ __device__ __forceinline__ R dsub(R a, R b) {
   return a - b;
 }
 
+// The candidate runs of the 3^d stencil of cells around the columns [cx0, cx0 + ncx) of row
+// (cy0, cz0), kind by kind (a bit per kind in cmask), in a fixed order: rows (dz, dy); in
+// each row the periodic image of the column left of the box, the columns inside the box,
+// the periodic image of the column right of it; each of these kind by kind, and for
+// row-major keys the columns inside the box as one run (consecutive keys).  f(cs, ce, oxf,
+// shx, shy, shz, dy, dz) gets the sorted index range [cs, ce), the column offset oxf of the
+// run's candidates relative to cx0 (kOxKey: each candidate's own column), and the shift
+// subtracted from p_i - p_j: FP64 the periodic image (+-L), FP32 the cell offset (dy ell_y,
+// dz ell_z; along x the column offset, taken per candidate).
+constexpr int kOxKey = -(1 << 30);
+
+template <class R, int DIM, class F>
+__device__ __forceinline__ void for_each_run(const Scene<R>& S, int cx0, int ncx, int cy0, int cz0, unsigned cmask,
+                                             F&& f) {
+  const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
+  for (int dz = zlo; dz <= zhi; dz++)
+    for (int dy = -1; dy <= 1; dy++) {
+      int cy = cy0 + dy, cz = DIM == 3 ? cz0 + dz : 0;
+      R shy = sizeof(R) == 4 ? (R)dy * S.ellR[1] : R(0);
+      R shz = sizeof(R) == 4 && DIM == 3 ? (R)dz * S.ellR[2] : R(0);
+      if (cy < 0 || cy >= S.ncell[1]) {
+        if (!S.per[1]) continue;
+        int w = cy < 0 ? 1 : -1;  // image of the row inside the box
+        cy += w * S.ncell[1];
+        if (sizeof(R) == 8) shy = w > 0 ? -S.LR[1] : S.LR[1];
+      }
+      if (DIM == 3 && (cz < 0 || cz >= S.ncell[2])) {
+        if (!S.per[2]) continue;
+        int w = cz < 0 ? 1 : -1;
+        cz += w * S.ncell[2];
+        if (sizeof(R) == 8) shz = w > 0 ? -S.LR[2] : S.LR[2];
+      }
+      int row = S.ncell[0] * (cy + S.ncell[1] * cz);
+      int nx = S.ncell[0];
+      int xa = cx0 - 1, xb = cx0 + ncx;  // stencil columns, inclusive
+      int x0 = max(xa, 0), x1 = min(xb, nx - 1);
+      // segments: -1 the left image, 0 .. nseg-1 inside the box (one run of consecutive keys,
+      // or one column per segment for Morton keys), nseg the right image; one call site of f
+      int nseg = S.key2lin ? x1 - x0 + 1 : 1;
+      for (int sg = -1; sg <= nseg; sg++) {
+        int ka, kb, oxf;  // cell keys [ka, kb] within a kind
+        R shx = R(0);
+        if (sg < 0) {
+          if (!(xa < 0 && S.per[0])) continue;
+          ka = kb = cell_key(S, row + nx - 1);
+          oxf = -1;
+          if (sizeof(R) == 8) shx = -S.LR[0];
+        } else if (sg == nseg) {
+          if (!(xb > nx - 1 && S.per[0])) continue;
+          ka = kb = cell_key(S, row);
+          oxf = ncx;
+          if (sizeof(R) == 8) shx = S.LR[0];
+        } else if (S.key2lin) {
+          ka = kb = cell_key(S, row + x0 + sg);
+          oxf = x0 + sg - cx0;
+        } else {
+          ka = row + x0;
+          kb = row + x1;
+          oxf = kOxKey;
+        }
+        // the bounds of every kind first (independent loads, one latency), then the runs
+        int rb[NCLS], re[NCLS];
+#pragma unroll
+        for (int cc = 0; cc < NCLS; cc++) {
+          rb[cc] = re[cc] = 0;
+          if ((cmask >> cc) & 1u) {
+            int base = cc * S.ncells;
+            rb[cc] = S.cstart[base + ka];
+            re[cc] = S.cstart[base + kb + 1];
+          }
+        }
+#pragma unroll
+        for (int cc = 0; cc < NCLS; cc++)
+          if (rb[cc] < re[cc]) f(rb[cc], re[cc], oxf, shx, shy, shz, dy, dz);
+      }
+    }
+}
+
 // generic traversal.  Pol provides: stage(S, j, lane), active, tp[3], idx, cmask (the
-// candidate kinds visited, a bit per kind, the same for the whole warp), pair(S, k, j, dx,
-// dy, dz, r2), and for FP64 scenes FP32 copies fx/fy/fz of the staged positions and tf of the
-// target (rc2f: the FP32 pre-test radius, squared, with the margin of the rounding of those
-// copies).  In every neighbour cell the candidates come kind by kind (fluid, rigid, wall).
+// candidate kinds visited, the same for the whole warp), shared arrays sox (column offset
+// of each staged candidate) and sxs (FP32: staged x plus that offset), pair(S, k, j, dx, dy,
+// dz, r2) with cox/cdy/cdz set to the candidate's cell offset, kExact (pair() sees exactly
+// the pairs with r^2 < rc2, with their offset; otherwise every pre-test hit, a superset,
+// without it), and for FP64 scenes FP32 copies fx/fy/fz of the staged positions and tf of
+// the target (rc2f: the FP32 pre-test radius, squared, with the margin of the rounding of
+// those copies).  Candidates come in the order of for_each_run.
 template <class R, int DIM, class Pol>
 __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>& G, Pol& pol, int lane, R rc2,
                                          float rc2f) {
-  const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
-  for (int dz = zlo; dz <= zhi; dz++)
-    for (int dy = -1; dy <= 1; dy++)
-      for (int ox = -1; ox <= G.ncx; ox++) {
-        int key;
-        R sh[3];
-        if (!stencil_cell<R, DIM>(S, G, ox, dy, dz, key, sh)) continue;
-        pol.cox = ox;
-        pol.cdy = dy;
-        pol.cdz = dz;
-        for (int cc = 0; cc < NCLS; cc++) {
-          if (!((pol.cmask >> cc) & 1u)) continue;
-          int kk = cc * S.ncells + key;
-          int cs = max(S.cstart[kk], 0), ce = min(S.cstart[kk + 1], S.n);
-          for (int cb = cs; cb < ce; cb += 32) {
-            int cnt = min(32, ce - cb);
-            __syncwarp();
-            if (lane < cnt) pol.stage(S, cb + lane, lane);
-            __syncwarp();
-            unsigned mask = 0u;
-            if (pol.active) {
-              if constexpr (sizeof(R) == 8) {
-                // FP64 scenes: an FP32 test with a margin keeps a superset of the pairs, the
-                // exact FP64 test below decides each of them (the result is the exact set)
-                float shf[3] = {(float)sh[0], (float)sh[1], (float)sh[2]};
-                for (int k = 0; k < cnt; k++) {
-                  float dx = (pol.tf[0] - pol.fx[k]) - shf[0];
-                  float dy2 = (pol.tf[1] - pol.fy[k]) - shf[1];
-                  float dz2 = DIM == 3 ? (pol.tf[2] - pol.fz[k]) - shf[2] : 0.f;
-                  float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-                  if (r2 < rc2f && cb + k != pol.idx) mask |= 1u << k;
-                }
-              } else {
-                for (int k = 0; k < cnt; k++) {
-                  R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sh[0]);
-                  R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
-                  R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
-                  R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
-                  if (r2 < rc2 && cb + k != pol.idx) mask |= 1u << k;
-                }
-              }
-            }
-            pol.hits += __popc(mask);
-            while (mask) {
-              int k = __ffs(mask) - 1;
-              mask &= mask - 1;
-              R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sh[0]);
-              R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), sh[1]);
-              R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), sh[2]) : R(0);
-              R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
-              if (sizeof(R) == 8 && !(r2 < rc2)) continue;
-              pol.pair(S, k, cb + k, dx, dy2, dz2, r2);
-            }
+  for_each_run<R, DIM>(S, G.cx0, G.ncx, G.cy, G.cz, pol.cmask,
+                       [&](int cs0, int ce0, int oxf, R shx, R shy, R shz, int dy, int dz) {
+    int cs = max(cs0, 0), ce = min(ce0, S.n);
+    pol.cdy = dy;
+    pol.cdz = dz;
+    for (int cb = cs; cb < ce; cb += 32) {
+      int cnt = min(32, ce - cb);
+      __syncwarp();
+      if (lane < cnt) {
+        int j = cb + lane;
+        pol.stage(S, j, lane);
+        // row-major keys: the column is the key modulo ncell[0] (ncells is a multiple of it)
+        int ox = oxf != kOxKey ? oxf : S.key[j] % S.ncell[0] - G.cx0;
+        pol.sox[lane] = ox;
+        if constexpr (sizeof(R) == 4) pol.sxs[lane] = pol.sx[lane] + (R)ox * S.ellR[0];
+      }
+      __syncwarp();
+      unsigned mask = 0u;
+      if (pol.active) {
+        if constexpr (sizeof(R) == 8) {
+          // FP64 scenes: an FP32 test with a margin keeps a superset of the pairs
+          float shf[3] = {(float)shx, (float)shy, (float)shz};
+          for (int k = 0; k < cnt; k++) {
+            float dx = (pol.tf[0] - pol.fx[k]) - shf[0];
+            float dy2 = (pol.tf[1] - pol.fy[k]) - shf[1];
+            float dz2 = DIM == 3 ? (pol.tf[2] - pol.fz[k]) - shf[2] : 0.f;
+            float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+            if (r2 < rc2f) mask |= 1u << k;
+          }
+        } else {
+          // FP32 scenes: a pre-test on the staged x shifted by its column and the target
+          // shifted by the row, its radius widened past the rounding of that reordering (a
+          // relative 1e-4 on r^2)
+          R qy = pol.tp[1] - shy, qz = pol.tp[2] - shz;
+          R rc2m = rc2 * R(1.0001);
+          for (int k = 0; k < cnt; k++) {
+            R dx = pol.tp[0] - pol.sxs[k];
+            R dy2 = qy - pol.sy[k];
+            R dz2 = DIM == 3 ? qz - pol.sz[k] : R(0);
+            R r2 = dist2<R, DIM>(dx, dy2, dz2);
+            if (r2 < rc2m) mask |= 1u << k;
           }
         }
+        unsigned self = (unsigned)(pol.idx - cb);  // a target is not its own neighbour
+        if (self < (unsigned)cnt) mask &= ~(1u << self);
       }
+      pol.hits += __popc(mask);
+      while (mask) {
+        int k = __ffs(mask) - 1;
+        mask &= mask - 1;
+        int ox = pol.sox[k];
+        pol.cox = ox;
+        if constexpr (Pol::kExact) {  // the exact set: each hit decided on the sweeps' offset
+          R sx0 = sizeof(R) == 4 ? (R)ox * S.ellR[0] : shx;
+          R dx = dsub(dsub(pol.tp[0], pol.sx[k]), sx0);
+          R dy2 = dsub(dsub(pol.tp[1], pol.sy[k]), shy);
+          R dz2 = DIM == 3 ? dsub(dsub(pol.tp[2], pol.sz[k]), shz) : R(0);
+          R r2 = pair_r2<R, DIM>(dx, dy2, dz2);
+          if (!(r2 < rc2)) continue;  // the pre-tests keep a superset
+          pol.pair(S, k, cb + k, dx, dy2, dz2, r2);
+        } else {
+          pol.pair(S, k, cb + k, R(0), R(0), R(0), R(0));
+        }
+      }
+    }
+  });
 }
 
 }  // namespace sph

@@ -1,11 +1,13 @@
-// The three pair sweeps of a step.
+// The neighbour search and the three pair sweeps of a step.
 //
-//  k_search   one warp per target group: cell-list candidate tests (staged in shared
-//             memory), the neighbour list of every particle (index and cell-offset code
-//             per entry, layout list[k * n + i] so that a warp of consecutive targets
-//             reads one line per k; a wall particle lists its fluid neighbours only, the
-//             only ones it reads), and the density summation + EOS of fluid targets
-//             (Eq. densum, Eq. eos).
+//  k_search   on rebuild steps, one warp per target group: cell-list candidate tests
+//             (staged in shared memory) and the neighbour list of every particle (index
+//             and cell-offset code per entry, layout list[k * n + i] so that a warp of
+//             consecutive targets reads one line per k; a wall particle lists its fluid
+//             neighbours only, the only ones it reads).  A list holds every pair within
+//             its radius r_c + skin and possibly a few just beyond it.
+//  k_density  one thread per particle over its list: density summation + EOS of fluid
+//             targets (Eq. densum, Eq. eos), and the packed records of every particle.
 //  k_extrap   one thread per wall / rigid target over its list: extrapolation of pressure
 //             and velocity from the fluid (Adami et al. 2012, cited in Sec. 3.3.4).
 //  k_force    one thread per fluid / rigid target over its list: Eq. momentum,
@@ -54,37 +56,54 @@ __device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p,
 // ---------------------------------------------------------------- search + density
 template <class R, int DIM>
 struct SearchPol {
-  R *sx, *sy, *sz;
-  float *fx, *fy, *fz;  // FP32 copies of the staged positions (FP64 scenes)
+  R *sx, *sy, *sz, *sxs;  // staged candidates (see traverse)
+  int* sox;
+  float *fx, *fy, *fz;    // FP32 copies of the staged positions (FP64 scenes)
   float tf[3];
   unsigned cmask;      // candidate kinds: a wall particle only ever reads its fluid neighbours
                        // (extrapolation of Sec. 3.3.4), the others read all
-  bool active, fluid;
+  bool active;
   int idx, tx, n, maxnb, cnt;
   int cox, cdy, cdz;
-  int* list;
+  int* list;           // where the target's next list entry goes (list + cnt * n)
   R tp[3];
-  R acc;
   unsigned long long hits;
+  // a list may hold a few pairs just beyond its radius (the pre-test's margin): every sweep
+  // decides r < r_c itself, so the exact per-pair test is skipped here
+  static constexpr bool kExact = false;
   __device__ void stage(const Scene<R>& S, int j, int lane) {
     sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
     if (sizeof(R) == 8) { fx[lane] = (float)sx[lane]; fy[lane] = (float)sy[lane]; fz[lane] = (float)sz[lane]; }
   }
-  __device__ void pair(const Scene<R>& S, int, int j, R, R, R, R r2) {
+  __device__ void pair(const Scene<R>&, int, int j, R, R, R, R) {
     int code = (cox - tx + 1) + 3 * (cdy + 1) + 9 * (cdz + 1);
-    if (cnt < maxnb) list[(size_t)cnt * n + idx] = (j << 5) | code;
+    if (cnt < maxnb) {
+      *list = (j << 5) | code;
+      list += n;
+    }
     cnt++;
-    if (fluid && r2 < S.rc2R) acc += quintic_w<R>(sqrt(r2) * S.inv_h);
   }
 };
 
+// resident blocks of 128 threads per SM the search is compiled for (register budget: the
+// largest count without spills, FP32 and FP64)
+#ifndef SPH_SEARCH_MIN_BLOCKS
+#define SPH_SEARCH_MIN_BLOCKS 8
+#endif
+#ifndef SPH_SEARCH_MIN_BLOCKS_64
+#define SPH_SEARCH_MIN_BLOCKS_64 6
+#endif
+
 template <class R, int DIM>
-__global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
-  __shared__ R sm[4][3][32];
+__global__ void __launch_bounds__(128, sizeof(R) == 8 ? SPH_SEARCH_MIN_BLOCKS_64 : SPH_SEARCH_MIN_BLOCKS)
+    k_search(BatchView<R> B) {
+  __shared__ R sm[4][4][32];
   __shared__ float smf[sizeof(R) == 8 ? 4 : 1][3][32];
+  __shared__ int smo[4][32];
   int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   SearchPol<R, DIM> pol;
-  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
+  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2]; pol.sxs = sm[wib][3];
+  pol.sox = smo[wib];
   int wf = sizeof(R) == 8 ? wib : 0;
   pol.fx = smf[wf][0]; pol.fy = smf[wf][1]; pol.fz = smf[wf][2];
   int total = __ldg(B.pfx_grp + B.nsc);
@@ -96,7 +115,6 @@ __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
     int gl = g - __ldg(B.pfx_grp + s);
     GroupIter<R, DIM> it(S, gl);
     Group<R, DIM> G;
-    pol.list = S.nbl;
     pol.n = S.n;
     pol.maxnb = S.maxnb;
     while (it.next(S, gl, lane, G))
@@ -108,7 +126,6 @@ __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
       pol.idx = valid ? i : -1;
       int tkind = valid ? S.matR[S.P.mt[i]].kind : G.cls;
       if (tkind != G.cls) S.status[3] = 1;  // a kind changed without a rebuild (never expected)
-      pol.fluid = valid && tkind == KFLUID;
       pol.cmask = G.cls == KWALL ? 1u << KFLUID : (1u << NCLS) - 1u;
       pol.tx = 0;
       if (valid) {
@@ -116,24 +133,11 @@ __global__ void __launch_bounds__(128) k_search(BatchView<R> B) {
         if (G.ncx > 1) pol.tx = key_lin(S, S.key[i]) % S.ncell[0] - G.cx0;
       }
       pol.tf[0] = (float)pol.tp[0]; pol.tf[1] = (float)pol.tp[1]; pol.tf[2] = (float)pol.tp[2];
-      pol.acc = R(0);
       pol.cnt = 0;
+      pol.list = S.nbl + (valid ? i : 0);
       pol.hits = 0;
       traverse<R, DIM>(S, G, pol, lane, S.rl2R, S.rl2f);
-      if (valid) {
-        S.nbc[i] = pol.cnt;
-        R rho = S.P.rho[i], p = R(0);
-        if (pol.fluid) {
-          const MatR<R>& A = S.matR[S.P.mt[i]];
-          rho = S.P.m[i] * (S.w0 + S.sig_w * pol.acc);
-          p = A.c2 * (rho - A.rho0);
-          S.P.rho[i] = rho;
-          S.prs[i] = p;
-        }
-        R vol = qdiv<R>(S.P.m[i], rho);
-        S.vol[i] = vol;
-        write_pack<R>(S, i, rho, p, vol);
-      }
+      if (valid) S.nbc[i] = pol.cnt;
     }
   }
 }
@@ -183,46 +187,31 @@ __device__ __forceinline__ const SweepK& sweep_k(const SweepK& kp, const SweepK&
 }
 
 // scan of the 3^d cells around target i (targets whose list overflowed); calls
-// f(j, code) for every candidate j != i of the kinds its list holds, in the traversal order
-// of k_search
+// f(j, code) for every candidate j != i of the kinds its list holds, in the order of the
+// search's traversal (for_each_run)
 template <class R, int DIM, class F>
 __device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
   int cx, cy, cz;
   lin_xyz(S, key_lin(S, S.key[i]), cx, cy, cz);
   unsigned cm = S.key[i] / S.ncells == KWALL ? 1u << KFLUID : (1u << NCLS) - 1u;
-  const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
-  for (int dz = zlo; dz <= zhi; dz++)
-    for (int dy = -1; dy <= 1; dy++)
-      for (int dx = -1; dx <= 1; dx++) {
-        int c[3] = {cx + dx, cy + dy, cz + dz};
-        bool skip = false;
-        for (int k = 0; k < DIM; k++)
-          if (c[k] < 0 || c[k] >= S.ncell[k]) {
-            if (!S.per[k]) skip = true;
-            else c[k] = c[k] < 0 ? c[k] + S.ncell[k] : c[k] - S.ncell[k];
-          }
-        if (skip) continue;
-        if (DIM == 2) c[2] = 0;
-        int key = cell_key(S, c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]));
-        int code = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-        for (int cc = 0; cc < NCLS; cc++) {
-          if (!((cm >> cc) & 1u)) continue;
-          int a = max(S.cstart[cc * S.ncells + key], 0), e = min(S.cstart[cc * S.ncells + key + 1], S.n);
-          for (int j = a; j < e; j++)
-            if (j != i) f(j, code);
-        }
-      }
+  for_each_run<R, DIM>(S, cx, 1, cy, cz, cm, [&](int cs, int ce, int oxf, R, R, R, int dy, int dz) {
+    int a = max(cs, 0), e = min(ce, S.n);
+    for (int j = a; j < e; j++) {
+      if (j == i) continue;
+      int ox = oxf != kOxKey ? oxf : S.key[j] % S.ncell[0] - cx;
+      f(j, (ox + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+    }
+  });
 }
 
 // ---------------------------------------------------------------- density on steps without rebuild
-// Eq. densum + Eq. eos over the list (same pairs in the same order as the search sweep)
+// Eq. densum + Eq. eos over the list, every step
 template <class R, int DIM>
 __global__ void __launch_bounds__(256) k_density(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     int s = find_scene(B.pfx_part, B.nsc, g);
     const Scene<R>& S = *B.sc[s];
-    if (rebin_now(S)) continue;  // the search sweep computed it
     int i = g - __ldg(B.pfx_part + s);
     const MatR<R>& A = S.matR[S.P.mt[i]];
     R rho = S.P.rho[i];
@@ -236,7 +225,7 @@ __global__ void __launch_bounds__(256) k_density(BatchView<R> B) {
         else
           list_delta<R, DIM>(S, ti, j, code, d);
         R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
-        if (r2 < S.rc2R) acc += quintic_w<R>(sqrt(r2) * S.inv_h);
+        if (r2 < S.rc2R) acc += quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
       };
       int cnt = S.nbc[i];
       if (cnt <= S.maxnb) {
@@ -263,7 +252,8 @@ __global__ void __launch_bounds__(256) k_density(BatchView<R> B) {
     }
     R vol = qdiv<R>(S.P.m[i], rho);
     S.vol[i] = vol;
-    // the positions of the packed records are read by this sweep: write only the density
+    // the positions of the packed records (written by the drift, or by the permutation on
+    // rebuild steps) are read by this sweep: write only the density
     write_pack<R>(S, i, rho, A.kind == KFLUID ? S.prs[i] : R(0), vol, false);
   }
 }
@@ -295,7 +285,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
         R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
         if (!(r2 < S.rc2R)) return;
         float4 b = S.pb[j];
-        R W = quintic_w<R>(sqrt(r2) * S.inv_h);
+        R W = quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
         S0 += W;
         P0 += b.w * W;
         R rw = a.w * W;
@@ -307,7 +297,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
         list_delta<R, DIM>(S, ti, j, code, d);
         R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
         if (!(r2 < S.rc2R)) return;
-        R W = quintic_w<R>(sqrt(r2) * S.inv_h);
+        R W = quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
         S0 += W;
         P0 += S.prs[j] * W;
         R rw = S.P.rho[j] * W;
@@ -331,7 +321,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
             pack_delta<DIM>(S, ti, a, e & 31, d);
             R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
             if (r2 < S.rc2R) {
-              R W = quintic_w<R>(sqrt(r2) * S.inv_h);
+              R W = quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
               S0 += W;
               P0 += b.w * W;
               R rw = a.w * W;
