@@ -206,8 +206,11 @@ __device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
 
 // ---------------------------------------------------------------- density on steps without rebuild
 // Eq. densum + Eq. eos over the list, every step
+#ifndef SPH_DENSITY_MIN_BLOCKS
+#define SPH_DENSITY_MIN_BLOCKS 4
+#endif
 template <class R, int DIM>
-__global__ void __launch_bounds__(256) k_density(BatchView<R> B) {
+__global__ void __launch_bounds__(256, SPH_DENSITY_MIN_BLOCKS) k_density(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     int s = find_scene(B.pfx_part, B.nsc, g);
@@ -232,11 +235,29 @@ __global__ void __launch_bounds__(256) k_density(BatchView<R> B) {
         const int* L = S.nbl + i;
         int k = 0;
         if constexpr (sizeof(R) == 4) {
-          int e = k < cnt ? __ldg(L + (size_t)k * S.n) : 0;
-          for (; k < cnt; k++) {
-            int en = k + 1 < cnt ? __ldg(L + (size_t)(k + 1) * S.n) : 0;
-            visit(e >> 5, e & 31);
-            e = en;
+          // entries four at a time: the four position gathers are in flight together (a
+          // latency-bound walk), the next four list entries while they are summed; the sum
+          // keeps the list order
+          size_t n = S.n;
+          const float4* pa = S.pa;
+          int e[4], en[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) e[q] = q < cnt ? __ldg(L + (size_t)q * n) : 0;
+          for (; k + 4 <= cnt; k += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) en[q] = k + 4 + q < cnt ? __ldg(L + (size_t)(k + 4 + q) * n) : 0;
+            float4 a[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) a[q] = pa[e[q] >> 5];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+              R d[3];
+              pack_delta<DIM>(S, ti, a[q], e[q] & 31, d);
+              R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+              if (r2 < S.rc2R) acc += quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) e[q] = en[q];
           }
         }
         for (; k < cnt; k++) {
