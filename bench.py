@@ -27,10 +27,10 @@ sys.path.insert(0, ROOT)
 METRIC = "SPH pair-interactions/s & steps/s at 1M particles; p50/p99 job latency vs plain"
 FLOP_PER_PAIR = 62      # FP32 pair arithmetic of the force/heat sweep, FMA = 2 (see the design notes)
 BYTES_PER_TARGET = 72   # algorithmic HBM bytes per target particle of the force sweep (FP32)
-# DRAM bytes (read + write) of one k_force launch on the default workload, from
-# `ncu --set full` of this kernel version (profiles/ncu_k_force_tank3d_fp32.md), per cell
-# layout (key order, skin in h) it was captured with; emptied whenever the kernel changes
-K_FORCE_TRAFFIC = {(1, 0.3): 792.1e6}
+# DRAM bytes (read + write) of one k_force launch on the default workload, from an
+# `ncu --set full` capture of this kernel version, per cell layout (key order, skin in h) it
+# was captured with; emptied whenever the kernel changes
+K_FORCE_TRAFFIC = {(1, 0.3): 735.7e6}
 FP32_LANES_PER_SM = 128
 N_SM = 152
 

@@ -510,8 +510,13 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const S
       etaj = t.eta;
     }
     float pt = qdiv<float>(rhoj * t.p + t.rho * pj, t.rho + rhoj);
-    float es = t.eta + etaj;
-    float et = es > 0.f ? qdiv<float>(2.f * t.eta * etaj, es) : 0.f;
+    float et;  // 2 eta_i eta_j / (eta_i + eta_j): eta itself for a pair of one material
+    if (same || bk != KFLUID) {
+      et = t.eta;
+    } else {
+      float es = t.eta + etaj;
+      et = es > 0.f ? qdiv<float>(2.f * t.eta * etaj, es) : 0.f;
+    }
     float coef = (t.V2 + Vj * Vj) * dW;
     float vis = et * inv_r;
     acc[0] += coef * (-pt * ex + vis * (t.u[0] - b.x));
