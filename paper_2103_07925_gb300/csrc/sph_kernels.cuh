@@ -739,10 +739,11 @@ __device__ __forceinline__ R dsub(R a, R b) {
 // each row the periodic image of the column left of the box, the columns inside the box,
 // the periodic image of the column right of it; each of these kind by kind, and for
 // row-major keys the columns inside the box as one run (consecutive keys).  f(cs, ce, oxf,
-// shx, shy, shz, dy, dz) gets the sorted index range [cs, ce), the column offset oxf of the
-// run's candidates relative to cx0 (kOxKey: each candidate's own column), and the shift
-// subtracted from p_i - p_j: FP64 the periodic image (+-L), FP32 the cell offset (dy ell_y,
-// dz ell_z; along x the column offset, taken per candidate).
+// shx, shy, shz, dy, dz, kfirst, ncols) gets the sorted index range [cs, ce), the column
+// offset oxf of the run's candidates relative to cx0 (kOxKey: each candidate's own column,
+// the run then spans the ncols cells of keys kfirst, kfirst + 1, ...), and the shift subtracted from p_i - p_j: FP64 the periodic
+// image (+-L), FP32 the cell offset (dy ell_y, dz ell_z; along x the column offset, taken
+// per candidate; ox0 = x0 - cx0 the offset of the first column).
 constexpr int kOxKey = -(1 << 30);
 
 template <class R, int DIM, class F>
@@ -807,7 +808,7 @@ __device__ __forceinline__ void for_each_run(const Scene<R>& S, int cx0, int ncx
         }
 #pragma unroll
         for (int cc = 0; cc < NCLS; cc++)
-          if (rb[cc] < re[cc]) f(rb[cc], re[cc], oxf, shx, shy, shz, dy, dz);
+          if (rb[cc] < re[cc]) f(rb[cc], re[cc], oxf, shx, shy, shz, dy, dz, cc * S.ncells + ka, kb - ka + 1, x0 - cx0);
       }
     }
 }
@@ -824,7 +825,8 @@ template <class R, int DIM, class Pol>
 __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>& G, Pol& pol, int lane, R rc2,
                                          float rc2f) {
   for_each_run<R, DIM>(S, G.cx0, G.ncx, G.cy, G.cz, pol.cmask,
-                       [&](int cs0, int ce0, int oxf, R shx, R shy, R shz, int dy, int dz) {
+                       [&](int cs0, int ce0, int oxf, R shx, R shy, R shz, int dy, int dz, int kfirst, int ncols,
+                           int ox0) {
     int cs = max(cs0, 0), ce = min(ce0, S.n);
     pol.cdy = dy;
     pol.cdz = dz;
@@ -834,23 +836,38 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
       if (lane < cnt) {
         int j = cb + lane;
         pol.stage(S, j, lane);
-        // row-major keys: the column is the key modulo ncell[0] (ncells is a multiple of it)
-        int ox = oxf != kOxKey ? oxf : S.key[j] % S.ncell[0] - G.cx0;
+        int ox = oxf;
+        if (oxf == kOxKey) {
+          if (ncols <= 5) {  // the column from the cell bounds of the run
+            ox = ox0;
+            for (int m = 1; m < ncols; m++) ox += j >= __ldg(S.cstart + kfirst + m) ? 1 : 0;
+          } else {  // row-major keys: the key modulo ncell[0] (ncells is a multiple of it)
+            ox = S.key[j] % S.ncell[0] - G.cx0;
+          }
+        }
         pol.sox[lane] = ox;
         if constexpr (sizeof(R) == 4) pol.sxs[lane] = pol.sx[lane] + (R)ox * S.ellR[0];
+      } else if (sizeof(R) == 4) {
+        pol.sxs[lane] = 1e30f;  // padding: fails every test
+      } else {
+        pol.fx[lane] = 1e30f;
       }
       __syncwarp();
       unsigned mask = 0u;
       if (pol.active) {
+        // the candidates four at a time over the padded batch
         if constexpr (sizeof(R) == 8) {
           // FP64 scenes: an FP32 test with a margin keeps a superset of the pairs
           float shf[3] = {(float)shx, (float)shy, (float)shz};
-          for (int k = 0; k < cnt; k++) {
-            float dx = (pol.tf[0] - pol.fx[k]) - shf[0];
-            float dy2 = (pol.tf[1] - pol.fy[k]) - shf[1];
-            float dz2 = DIM == 3 ? (pol.tf[2] - pol.fz[k]) - shf[2] : 0.f;
-            float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-            if (r2 < rc2f) mask |= 1u << k;
+          for (int k0 = 0; k0 < cnt; k0 += 4) {
+#pragma unroll
+            for (int k = k0; k < k0 + 4; k++) {
+              float dx = (pol.tf[0] - pol.fx[k]) - shf[0];
+              float dy2 = (pol.tf[1] - pol.fy[k]) - shf[1];
+              float dz2 = DIM == 3 ? (pol.tf[2] - pol.fz[k]) - shf[2] : 0.f;
+              float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+              if (r2 < rc2f) mask |= 1u << k;
+            }
           }
         } else {
           // FP32 scenes: a pre-test on the staged x shifted by its column and the target
@@ -858,12 +875,15 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
           // relative 1e-4 on r^2)
           R qy = pol.tp[1] - shy, qz = pol.tp[2] - shz;
           R rc2m = rc2 * R(1.0001);
-          for (int k = 0; k < cnt; k++) {
-            R dx = pol.tp[0] - pol.sxs[k];
-            R dy2 = qy - pol.sy[k];
-            R dz2 = DIM == 3 ? qz - pol.sz[k] : R(0);
-            R r2 = dist2<R, DIM>(dx, dy2, dz2);
-            if (r2 < rc2m) mask |= 1u << k;
+          for (int k0 = 0; k0 < cnt; k0 += 4) {
+#pragma unroll
+            for (int k = k0; k < k0 + 4; k++) {
+              R dx = pol.tp[0] - pol.sxs[k];
+              R dy2 = qy - pol.sy[k];
+              R dz2 = DIM == 3 ? qz - pol.sz[k] : R(0);
+              R r2 = dist2<R, DIM>(dx, dy2, dz2);
+              if (r2 < rc2m) mask |= 1u << k;
+            }
           }
         }
         unsigned self = (unsigned)(pol.idx - cb);  // a target is not its own neighbour

@@ -85,10 +85,10 @@ struct SearchPol {
   }
 };
 
-// resident blocks of 128 threads per SM the search is compiled for (register budget: the
-// largest count without spills, FP32 and FP64)
+// resident blocks of 128 threads per SM the search is compiled for (register budget; six
+// measured fastest for FP32, against eight and ten)
 #ifndef SPH_SEARCH_MIN_BLOCKS
-#define SPH_SEARCH_MIN_BLOCKS 8
+#define SPH_SEARCH_MIN_BLOCKS 6
 #endif
 #ifndef SPH_SEARCH_MIN_BLOCKS_64
 #define SPH_SEARCH_MIN_BLOCKS_64 6
@@ -194,7 +194,7 @@ __device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
   int cx, cy, cz;
   lin_xyz(S, key_lin(S, S.key[i]), cx, cy, cz);
   unsigned cm = S.key[i] / S.ncells == KWALL ? 1u << KFLUID : (1u << NCLS) - 1u;
-  for_each_run<R, DIM>(S, cx, 1, cy, cz, cm, [&](int cs, int ce, int oxf, R, R, R, int dy, int dz) {
+  for_each_run<R, DIM>(S, cx, 1, cy, cz, cm, [&](int cs, int ce, int oxf, R, R, R, int dy, int dz, int, int, int) {
     int a = max(cs, 0), e = min(ce, S.n);
     for (int j = a; j < e; j++) {
       if (j == i) continue;
