@@ -207,7 +207,10 @@ sph_status sph_interpolate(sph_scene* scene, int64_t nq, const double* query, in
 
 /* Overwrite POS, VEL and TEMP of fluid particles from host arrays in input order (FP64,
  * n rows of 3 or 1; rows of other particles are ignored).  Ownership stays with the
- * caller; the copy is enqueued on the scene's stream.  The next step starts from the
+ * caller; the copy is enqueued on the scene's stream: a source in page-locked host memory
+ * is read in place by the import kernel (keep it unchanged until the stream passes it, e.g.
+ * until the next synchronising call), any other is staged before the call returns.  The
+ * next step starts from the
  * written state with the accelerations of the last evaluation (its first half kick,
  * Sec. 3.7), as a staggered coupling with an outside solver does.  A written particle stays
  * in its cell frame: the Verlet-skin test of the next step decides whether the neighbour

@@ -752,6 +752,18 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
 }
 
 // forced binning, body mass quantities and one full evaluation at t = 0
+// the device address of a host buffer the device can address directly (page-locked
+// memory): the import kernel then reads it over the host link, with no staging copy; null
+// for any other pointer (those go through a staging buffer)
+inline void* device_view(const void* h) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 template <class R, int DIM>
 sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   const Scene<R>& S = hs[idx];
@@ -1003,6 +1015,9 @@ sph_status Engine<R, DIM>::read_fields(int idx, uint32_t mask, void* const* dst,
   ExportArgs ea;
   memset(&ea, 0, sizeof(ea));
   ea.original = original_order ? 1 : 0;
+  // staged, then copied by the copy engine: a kernel writing page-locked host memory in
+  // place measured 3.5x slower than the copy (reading it in place, for sph_write_fields,
+  // measured faster)
   char* p = (char*)d_stage;
   for (int f = 0; f < SPH_F_COUNT; f++)
     if (mask & (1u << f)) {
@@ -1055,9 +1070,14 @@ sph_status Engine<R, DIM>::write_fields(int idx, uint32_t mask, const void* cons
   double* pos = (double*)d_stage;
   double* vel = pos + 3 * n;
   double* tmp = vel + 3 * n;
-  if (mask & (1u << SPH_F_POS)) SPH_CU(cudaMemcpyAsync(pos, src[SPH_F_POS], 24 * n, cudaMemcpyHostToDevice, stream));
-  if (mask & (1u << SPH_F_VEL)) SPH_CU(cudaMemcpyAsync(vel, src[SPH_F_VEL], 24 * n, cudaMemcpyHostToDevice, stream));
-  if (mask & (1u << SPH_F_TEMP)) SPH_CU(cudaMemcpyAsync(tmp, src[SPH_F_TEMP], 8 * n, cudaMemcpyHostToDevice, stream));
+  // page-locked host buffers are read by the import kernel in place, others are staged
+  struct { int f; double** d; size_t b; } in[] = {{SPH_F_POS, &pos, 24 * n}, {SPH_F_VEL, &vel, 24 * n},
+                                                  {SPH_F_TEMP, &tmp, 8 * n}};
+  for (auto& x : in)
+    if (mask & (1u << x.f)) {
+      if (void* v = device_view(src[x.f])) *x.d = (double*)v;
+      else SPH_CU(cudaMemcpyAsync(*x.d, src[x.f], x.b, cudaMemcpyHostToDevice, stream));
+    }
   k_import_fluid<R><<<grid_for((int64_t)n, 256, grid_part), 256, 0, stream>>>(
       S.self, (mask & (1u << SPH_F_POS)) ? pos : nullptr, (mask & (1u << SPH_F_VEL)) ? vel : nullptr,
       (mask & (1u << SPH_F_TEMP)) ? tmp : nullptr);
