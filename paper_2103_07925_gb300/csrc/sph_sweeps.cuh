@@ -331,26 +331,42 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
       const int* L = S.nbl + i;
       int k = 0;
       if constexpr (sizeof(R) == 4) {
-        // software pipeline as in the force sweep: next entry and all records in flight
-        int e = k < cnt ? __ldg(L + (size_t)k * S.n) : 0;
-        for (; k < cnt; k++) {
-          int en = k + 1 < cnt ? __ldg(L + (size_t)(k + 1) * S.n) : 0;
-          int j = e >> 5;
-          float4 a = S.pa[j], b = S.pb[j];
-          if (wall || (__float_as_int(S.pc[j].z) >> 16) == KFLUID) {
+        // entries two at a time, both records of both in flight together (a latency-bound
+        // walk), the next two list entries while they are summed; the sums keep the list
+        // order
+        size_t n = S.n;
+        int e[2], en[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) e[q] = q < cnt ? __ldg(L + (size_t)q * n) : 0;
+        for (; k + 2 <= cnt; k += 2) {
+#pragma unroll
+          for (int q = 0; q < 2; q++) en[q] = k + 2 + q < cnt ? __ldg(L + (size_t)(k + 2 + q) * n) : 0;
+          float4 a[2], b[2];
+          bool fl[2];
+#pragma unroll
+          for (int q = 0; q < 2; q++) {
+            int j = e[q] >> 5;
+            a[q] = S.pa[j];
+            b[q] = S.pb[j];
+            fl[q] = wall || (__float_as_int(S.pc[j].z) >> 16) == KFLUID;
+          }
+#pragma unroll
+          for (int q = 0; q < 2; q++) {
+            if (!fl[q]) continue;
             R d[3];
-            pack_delta<DIM>(S, ti, a, e & 31, d);
+            pack_delta<DIM>(S, ti, a[q], e[q] & 31, d);
             R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
             if (r2 < S.rc2R) {
               R W = quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
               S0 += W;
-              P0 += b.w * W;
-              R rw = a.w * W;
+              P0 += b[q].w * W;
+              R rw = a[q].w * W;
               Rv[0] += rw * d[0]; Rv[1] += rw * d[1]; Rv[2] += rw * d[2];
-              U[0] += b.x * W; U[1] += b.y * W; U[2] += b.z * W;
+              U[0] += b[q].x * W; U[1] += b[q].y * W; U[2] += b[q].z * W;
             }
           }
-          e = en;
+#pragma unroll
+          for (int q = 0; q < 2; q++) e[q] = en[q];
         }
       }
       for (; k < cnt; k++) {
