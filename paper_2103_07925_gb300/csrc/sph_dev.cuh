@@ -143,7 +143,7 @@ struct Scene {
   R* fr;               // force on every slot (3 per slot)
   // ---------------------------------------------------------------- per-step state
   double* st;          // [0] dt [1] time [2] step [3] dt of last step
-  unsigned long long* umax;  // bits of max |u| over fluid particles (FP64, non-negative)
+  unsigned long long* umax;  // bits of max |u|^2 over fluid particles (FP64, non-negative)
   int* status;         // [0] non-finite flag [1] relabel count [2] capacity error [3] table error
                        // [4] rebuild in this step [5] steps since rebuild [6] rebuild count
                        // [7] solidifiers without a rigid neighbour [8] new bodies this step

@@ -152,9 +152,32 @@ __device__ __forceinline__ void store_pos<float>(const Scene<float>& S, int i, c
 }
 
 // ============================================================================ time step
+// maximum of v over the block (all threads call it), one atomic per block; max is exact, so
+// the result does not depend on the order
+__device__ __forceinline__ void block_max_atomic(unsigned long long v, unsigned long long* ptr) {
+  __shared__ unsigned long long red[32];
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(FULL, v, o);
+    v = w > v ? w : v;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
+    for (int o = 16; o; o >>= 1) {
+      unsigned long long w = __shfl_xor_sync(FULL, v, o);
+      v = w > v ? w : v;
+    }
+    if (threadIdx.x == 0 && v > 0ull) atomicMax(ptr, v);
+  }
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) k_umax(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
+  // one scene: a running maximum per thread and one atomic per block; several scenes: one
+  // atomic per scene present in a warp
+  unsigned long long run = 0ull;
   for (int g0 = blockIdx.x * blockDim.x; g0 < total; g0 += gridDim.x * blockDim.x) {
     int g = g0 + threadIdx.x;
     // the block's first item decides the scene slice handled in this round
@@ -164,12 +187,24 @@ __global__ void __launch_bounds__(256) k_umax(BatchView<R> B) {
     if (g < total && S.dt_mode == 1) {
       int i = g - __ldg(B.pfx_part + s);
       if (S.matR[S.P.mt[i]].kind == KFLUID) {
-        double ux = S.P.vx[i], uy = S.P.vy[i], uz = S.P.vz[i];
-        u = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz)));
+        // |u|^2: the root of the maximum equals the maximum of the roots (a correctly
+        // rounded root is monotone), so k_dt takes one root instead of one per particle;
+        // FP32 scenes square in FP32 (their velocities are FP32; FP64 arithmetic is scarce)
+        if constexpr (sizeof(R) == 4) {
+          float ux = S.P.vx[i], uy = S.P.vy[i], uz = S.P.vz[i];
+          u = (double)__fadd_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)), __fmul_rn(uz, uz));
+        } else {
+          double ux = S.P.vx[i], uy = S.P.vy[i], uz = S.P.vz[i];
+          u = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
+        }
       }
     }
     // warp maximum for each scene present in the warp, one atomic per scene (max is exact)
     unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    if (B.nsc == 1) {
+      run = b > run ? b : run;
+      continue;
+    }
     unsigned pending = FULL;
     while (pending) {
       int leader = __ffs(pending) - 1;
@@ -183,6 +218,7 @@ __global__ void __launch_bounds__(256) k_umax(BatchView<R> B) {
       pending &= ~__ballot_sync(FULL, s == cs);
     }
   }
+  if (B.nsc == 1) block_max_atomic(run, B.sc[0]->umax);
 }
 
 template <class R>
@@ -192,7 +228,7 @@ __global__ void k_dt(BatchView<R> B) {
   Scene<R>& S = *B.sc[s];
   double dt = S.dt_fixed;
   if (S.dt_mode == 1) {
-    double umax = __longlong_as_double((long long)*S.umax);
+    double umax = sqrt(__longlong_as_double((long long)*S.umax));
     dt = S.dt_cond;
     if (S.cmax + umax > 0.0) dt = fmin(dt, 0.25 * S.h / (S.cmax + umax));
     if (!(dt < 1e300)) dt = S.dt_fixed;
@@ -254,6 +290,7 @@ __device__ __forceinline__ unsigned long long disp_bits<float>(float d2) {
 template <class R>
 __global__ void __launch_bounds__(256) k_kick_drift(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
+  unsigned long long run = 0ull;  // one scene: running maximum displacement (see k_umax)
   for (int g0 = blockIdx.x * blockDim.x; g0 < total; g0 += gridDim.x * blockDim.x) {
     int g = g0 + threadIdx.x;
     int s = find_scene(B.pfx_part, B.nsc, min(g, total - 1));
@@ -329,6 +366,10 @@ __global__ void __launch_bounds__(256) k_kick_drift(BatchView<R> B) {
       d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     }
     unsigned long long b = disp_bits<R>(d2);
+    if (B.nsc == 1) {
+      run = b > run ? b : run;
+      continue;
+    }
     unsigned pending = FULL;
     while (pending) {
       int leader = __ffs(pending) - 1;
@@ -342,6 +383,7 @@ __global__ void __launch_bounds__(256) k_kick_drift(BatchView<R> B) {
       pending &= ~__ballot_sync(FULL, s == cs);
     }
   }
+  if (B.nsc == 1) block_max_atomic(run, B.sc[0]->disp);
 }
 
 // ============================================================================ binning
