@@ -131,6 +131,7 @@ struct Scene {
   int Kcap, nslot;
   int* K;              // device: bodies in use (ids 0..K-1)
   double *bm, *br, *bq, *bu, *bw, *ba, *bal, *bf, *bt, *bIb, *bIbinv, *bIw;
+  double* bRm;         // rotation matrix R(q) of each body after the drift of the step
   int *balive, *bstart, *bend;  // slot ranges of each body
   int *bchg, *bcur;    // relabel: 1 changed body, 2 new body; slot cursor
   double* bold;        // relabel: centre of mass before the change (3 per body)

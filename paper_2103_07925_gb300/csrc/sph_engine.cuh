@@ -391,7 +391,7 @@ class Engine {
                  (DIM == 3 ? 192 : 64) * sizeof(int) + (sizeof(R) == 4 ? 3 * sizeof(float4) : 0);
     size_t cells = (size_t)(NCLS * ncells + 1) * 2 * sizeof(int) + (size_t)ncells * 2 * sizeof(int) +
                    (size_t)(NCLS * ncells / 1024 + 2) * sizeof(int);
-    size_t bodies = (size_t)kcap * (60 * sizeof(double) + 3 * sizeof(int));
+    size_t bodies = (size_t)kcap * (69 * sizeof(double) + 3 * sizeof(int));
     size_t slots = (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R) + sizeof(int));
     // relabel scratch: offsets and forces in the new slot order, one root mark per particle
     size_t relabel = trans ? (size_t)nrigid * (3 * sizeof(double) + 3 * sizeof(R)) + (size_t)n * sizeof(int) +
@@ -623,9 +623,9 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     S.key2lin = a2;
   }
   int kc = S.Kcap;
-  double** bd[] = {&S.bm, &S.br, &S.bq, &S.bu, &S.bw, &S.ba, &S.bal, &S.bf, &S.bt, &S.bIb, &S.bIbinv, &S.bIw};
-  size_t bdn[] = {1, 3, 4, 3, 3, 3, 3, 3, 3, 9, 9, 9};
-  for (int q = 0; q < 12; q++) SPH_TRY(A(bd[q], bdn[q] * (size_t)kc));
+  double** bd[] = {&S.bm, &S.br, &S.bq, &S.bu, &S.bw, &S.ba, &S.bal, &S.bf, &S.bt, &S.bIb, &S.bIbinv, &S.bIw, &S.bRm};
+  size_t bdn[] = {1, 3, 4, 3, 3, 3, 3, 3, 3, 9, 9, 9, 9};
+  for (int q = 0; q < 13; q++) SPH_TRY(A(bd[q], bdn[q] * (size_t)kc));
   SPH_TRY(A(&S.balive, (size_t)kc));
   SPH_TRY(A(&S.bchg, (size_t)kc));
   SPH_TRY(A(&S.bcur, (size_t)kc));
@@ -661,7 +661,7 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     SPH_CU(cudaMemcpyAsync(S.status, st0, sizeof(st0), cudaMemcpyHostToDevice, stream));
   }
   SPH_CU(cudaMemsetAsync(S.pairs, 0, sizeof(unsigned long long) * 2, stream));
-  for (int q = 0; q < 12; q++) SPH_CU(cudaMemsetAsync(*bd[q], 0, sizeof(double) * bdn[q] * kc, stream));
+  for (int q = 0; q < 13; q++) SPH_CU(cudaMemsetAsync(*bd[q], 0, sizeof(double) * bdn[q] * kc, stream));
   SPH_CU(cudaMemsetAsync(S.balive, 0, sizeof(int) * kc, stream));
   SPH_CU(cudaMemsetAsync(S.bstart, 0, sizeof(int) * kc, stream));
   SPH_CU(cudaMemsetAsync(S.bend, 0, sizeof(int) * kc, stream));

@@ -271,6 +271,9 @@ __global__ void k_body_kick_drift(BatchView<R> B) {
     double z = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
     double nq = sqrt(w * w + x * x + y * y + z * z);
     b[0] = w / nq; b[1] = x / nq; b[2] = y / nq; b[3] = z / nq;
+    // R(q^{n+1}) once per body for the rigid particles of this step (the drift and the
+    // final kick), instead of once per particle
+    qrot(b, &S.bRm[9 * k]);
   }
 }
 
@@ -335,9 +338,8 @@ __global__ void __launch_bounds__(256) k_kick_drift(BatchView<R> B) {
       }
     } else if (kind == KRIGID) {
       int k = S.P.body[i], sl = S.P.slot[i];
-      double Rm[9], rr[3], t1[3], t2[3], t3[3], x[3];
-      qrot(&S.bq[4 * k], Rm);
-      mv(Rm, &S.rb[3 * sl], rr);
+      double rr[3], t1[3], t2[3], t3[3], x[3];
+      mv(&S.bRm[9 * k], &S.rb[3 * sl], rr);
       const double* w = &S.bw[3 * k];
       cross(w, rr, t2);
       for (int q = 0; q < 3; q++) x[q] = S.br[3 * k + q] + rr[q];
@@ -1062,9 +1064,8 @@ __global__ void k_final(BatchView<R> B) {
       if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) S.status[0] = 1;
     } else {
       int k = S.P.body[i], sl = S.P.slot[i];
-      double Rm[9], rr[3], c[3];
-      qrot(&S.bq[4 * k], Rm);
-      mv(Rm, &S.rb[3 * sl], rr);
+      double rr[3], c[3];
+      mv(&S.bRm[9 * k], &S.rb[3 * sl], rr);  // R(q^{n+1}) of the body's drift this step
       cross(&S.bw[3 * k], rr, c);
       S.P.vx[i] = (R)(S.bu[3 * k] + c[0]);
       S.P.vy[i] = (R)(S.bu[3 * k + 1] + c[1]);
