@@ -288,18 +288,19 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
     const Scene<R>& S = *B.sc[s];
     // kind-major keys: the wall and rigid particles follow the fluid ones, from the start of
     // the rigid key range on
-    int i = S.cstart[S.ncells] + (g - __ldg(B.pfx_part + s));
+    int nf = S.cstart[S.ncells];  // fluid particles: sorted indices [0, nf)
+    int i = nf + (g - __ldg(B.pfx_part + s));
     if (i >= S.n) continue;
     int kind = S.matR[S.P.mt[i]].kind;
     if (kind == KFLUID) continue;
     // a wall particle's list (and its cell scan) holds fluid neighbours only; a rigid
-    // particle's holds all kinds and reads the fluid ones
+    // particle's holds all kinds and reads the fluid ones, told apart by their index
     bool wall = kind == KWALL;
     R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
     R S0 = R(0), P0 = R(0), Rv[3] = {R(0), R(0), R(0)}, U[3] = {R(0), R(0), R(0)};
     auto visit = [&](int j, int code) {
       if constexpr (sizeof(R) == 4) {
-        if (!wall && (__float_as_int(S.pc[j].z) >> 16) != KFLUID) return;
+        if (!wall && j >= nf) return;
         float4 a = S.pa[j];
         R d[3];
         pack_delta<DIM>(S, ti, a, code, d);
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
         Rv[0] += rw * d[0]; Rv[1] += rw * d[1]; Rv[2] += rw * d[2];
         U[0] += b.x * W; U[1] += b.y * W; U[2] += b.z * W;
       } else {
-        if (!wall && S.matR[S.P.mt[j]].kind != KFLUID) return;
+        if (!wall && j >= nf) return;
         R d[3];
         list_delta<R, DIM>(S, ti, j, code, d);
         R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
@@ -346,9 +347,9 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
 #pragma unroll
           for (int q = 0; q < 2; q++) {
             int j = e[q] >> 5;
-            a[q] = S.pa[j];
+            a[q] = S.pa[j];  // loaded whatever the kind: both loads of both entries in flight
             b[q] = S.pb[j];
-            fl[q] = wall || (__float_as_int(S.pc[j].z) >> 16) == KFLUID;
+            fl[q] = wall || j < nf;
           }
 #pragma unroll
           for (int q = 0; q < 2; q++) {
