@@ -282,7 +282,6 @@ struct NbPol {
   R tp[3];
   int64_t cnt, off;
   int32_t* list;
-  unsigned long long hits;
   static constexpr bool kExact = true;
   __device__ void stage(const Scene<R>& S, int j, int lane) {
     sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
@@ -324,7 +323,6 @@ __global__ void __launch_bounds__(128) k_neighbors(Scene<R>* const* sc, int ngro
       pol.tf[0] = (float)pol.tp[0]; pol.tf[1] = (float)pol.tp[1]; pol.tf[2] = (float)pol.tp[2];
       pol.cnt = 0;
       pol.off = (valid && offs) ? offs[S.P.orig[i]] : 0;
-      pol.hits = 0;
       traverse<R, DIM>(S, G, pol, lane, S.rc2R, S.rc2f);
       if (valid && !offs) counts[S.P.orig[i]] = pol.cnt;
     }

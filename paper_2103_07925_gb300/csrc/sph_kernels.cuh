@@ -5,7 +5,9 @@
 //   k_umax, k_dt            time step, Eq. timestepcond (or fixed)
 //   k_body_kick_drift       u_k, w_k half kick; r_k drift; q_k <- q_inc o q_k
 //   k_kick_drift            fluid half kick + drift; rigid particles follow their body
-//   k_bin .. k_flip         cell binning: counting sort by cell key, stable (Sec. 3.2)
+//   k_bin .. k_flip         cell binning: counting sort by (kind, cell) key, stable
+//                           (Sec. 3.2)
+//   k_search                neighbour lists (rebuild steps)
 //   k_density               Eq. densum + Eq. eos                       (pair sweep 1)
 //   k_extrap                wall / rigid extrapolation (Adami 2012)     (pair sweep 2)
 //   k_force                 Eq. momentum, couplingforce, contactforce,
@@ -659,11 +661,12 @@ __global__ void k_flip(BatchView<R> B, int force) {
   S.Q = t;
 }
 
-// ============================================================================ pair sweeps
-// One warp per target group (G consecutive cells along x, or one cell).  For each chunk of
-// <= 32 targets the warp visits the neighbour cells; each chunk of <= 32 candidates is
-// staged in shared memory, every lane tests all candidates against its target (hit mask,
-// r^2 < r_c^2), then processes its own hits.
+// ============================================================================ cell traversal
+// One warp per target group (a cell, G consecutive cells along x, or a window of 32
+// consecutive particles), split into ranges of one kind.  For each chunk of <= 32 targets
+// the warp visits the stencil rows kind by kind; each chunk of <= 32 candidates is staged
+// in shared memory, every lane tests all candidates against its target (hit mask), then
+// processes its own hits.
 
 template <class R, int DIM>
 struct Group {
@@ -933,7 +936,6 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
         unsigned self = (unsigned)(pol.idx - cb);  // a target is not its own neighbour
         if (self < (unsigned)cnt) mask &= ~(1u << self);
       }
-      pol.hits += __popc(mask);
       while (mask) {
         int k = __ffs(mask) - 1;
         mask &= mask - 1;

@@ -67,7 +67,6 @@ struct SearchPol {
   int cox, cdy, cdz;
   int* list;           // where the target's next list entry goes (list + cnt * n)
   R tp[3];
-  unsigned long long hits;
   // a list may hold a few pairs just beyond its radius (the pre-test's margin): every sweep
   // decides r < r_c itself, so the exact per-pair test is skipped here
   static constexpr bool kExact = false;
@@ -135,7 +134,6 @@ __global__ void __launch_bounds__(128, sizeof(R) == 8 ? SPH_SEARCH_MIN_BLOCKS_64
       pol.tf[0] = (float)pol.tp[0]; pol.tf[1] = (float)pol.tp[1]; pol.tf[2] = (float)pol.tp[2];
       pol.cnt = 0;
       pol.list = S.nbl + (valid ? i : 0);
-      pol.hits = 0;
       traverse<R, DIM>(S, G, pol, lane, S.rl2R, S.rl2f);
       if (valid) S.nbc[i] = pol.cnt;
     }
