@@ -53,7 +53,7 @@ __device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p,
   }
 }
 
-// ---------------------------------------------------------------- search + density
+// ---------------------------------------------------------------- neighbour search
 template <class R, int DIM>
 struct SearchPol {
   R *sx, *sy, *sz, *sxs;  // staged candidates (see traverse)
