@@ -82,8 +82,9 @@ def tune_scene(scene, precision=32, steps=12, warmup=3, skins_h=SKINS_H, layouts
         g.step(warmup)
         cur = g.time_steps(steps) / steps
         for knob, values in (("sweep_block", blocks), ("sweep_waves", waves), ("search_waves", waves)):
+            start = launch[knob]  # timed already
             for v in values:
-                if v == launch[knob]:
+                if v == start:
                     continue
                 trial = dict(launch, **{knob: v})
                 g.set_launch(**trial)
@@ -120,8 +121,9 @@ def tune_batch(batch, scenes, precision=32, steps=6, warmup=2, **kw):
             batch.step(1)
             cur = batch.time_steps(steps) / steps
             for knob, values in (("sweep_block", SWEEP_BLOCKS), ("sweep_waves", WAVES), ("search_waves", WAVES)):
+                start = launch[knob]  # timed already
                 for v in values:
-                    if v == launch[knob]:
+                    if v == start:
                         continue
                     trial = dict(launch, **{knob: v})
                     batch.set_launch(dim, **trial)
