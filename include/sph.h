@@ -215,7 +215,7 @@ sph_status sph_interpolate(sph_scene* scene, int64_t nq, const double* query, in
  * Sec. 3.7), as a staggered coupling with an outside solver does.  A written particle stays
  * in its cell frame: the Verlet-skin test of the next step decides whether the neighbour
  * lists are rebuilt; a particle written more than 64 cells away forces a rebuild.
- * SPH_ERR_INVALID for other fields. */
+ * SPH_ERR_INVALID for other fields or a null source of a requested field. */
 sph_status sph_write_fields(sph_scene* scene, uint32_t field_mask, const void* const* host_src);
 
 /* Body state (k rows; each pointer nullable): com k*3, quat k*4, vel k*3, omega k*3,

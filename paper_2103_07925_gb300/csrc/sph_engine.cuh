@@ -1066,6 +1066,8 @@ sph_status Engine<R, DIM>::write_fields(int idx, uint32_t mask, const void* cons
   size_t n = (size_t)S.n;
   uint32_t ok = (1u << SPH_F_POS) | (1u << SPH_F_VEL) | (1u << SPH_F_TEMP);
   if (!src || (mask & ~ok)) { set_error("write_fields supports POS, VEL and TEMP"); return SPH_ERR_INVALID; }
+  for (int f = 0; f < SPH_F_COUNT; f++)
+    if ((mask & (1u << f)) && !src[f]) { set_error("field %d written from a null source", f); return SPH_ERR_INVALID; }
   SPH_TRY(ensure_stage(n * 7 * 8));
   double* pos = (double*)d_stage;
   double* vel = pos + 3 * n;
