@@ -42,3 +42,54 @@ def test_tank3d_spheres_sizes_and_seed():
     assert per.min() >= 200 and per.max() <= 2300
     sc2 = S.tank3d_spheres()
     assert np.array_equal(sc2["particles"]["pos"], p["pos"])
+
+
+def _kinds(sc):
+    return np.array([m["kind"] for m in sc["materials"]])[sc["particles"]["material"]]
+
+
+def test_dx_for_count_gives_the_requested_size():
+    for dim, n in ((2, 2e4), (2, 3e5), (3, 2e4), (3, 4e5)):
+        dx = S.dx_for_count(dim, n)
+        sc = S.tank2d_discs(dx=dx, n_discs=0) if dim == 2 else S.tank3d_spheres(dx=dx, n_spheres=0)
+        m = len(sc["particles"]["mass"])
+        assert 0.8 * n < m < 1.25 * n, (dim, n, m)
+    assert S.dx_for_count(3, 1e5) > S.dx_for_count(3, 4e5)
+
+
+def test_batch_mix_spread_dims_bodies_and_seed():
+    mix = S.batch_mix(count=12, seed=7, n_lo=1e4, n_hi=6e4, max_bodies=5)
+    specs = [s for _, s in mix]
+    assert [s["index"] for s in specs] == list(range(12))
+    assert {s["dim"] for s in specs} == {2, 3}
+    for sc, s in mix:
+        assert sc["params"]["dim"] == s["dim"]
+        assert 1e4 <= s["target"] <= 6e4
+        assert 0.7 * s["target"] < s["n"] < 1.4 * s["target"]
+        assert len(sc["bodies"]["quat"]) == s["bodies"] <= 5
+        assert sc["params"]["precision"] == 32
+    again = S.batch_mix(count=12, seed=7, n_lo=1e4, n_hi=6e4, max_bodies=5)
+    for (a, _), (b, _) in zip(mix, again):
+        assert np.array_equal(a["particles"]["pos"], b["particles"]["pos"])
+
+
+def test_powder_bed_structure():
+    sc = S.powder_bed(dx=0.02, n_grains=40)
+    k = _kinds(sc)
+    p = sc["particles"]
+    mats = sc["materials"]
+    assert set(np.unique(k)) == {S.FLUID, S.RIGID, S.WALL}
+    # gas (density 1) and solid metal (density 1000) present; solid melts into liquid metal
+    rho0 = np.array([m["rho0"] for m in mats])[p["material"]]
+    assert np.any((k == S.FLUID) & (rho0 == 1.0)) and np.any((k == S.RIGID) & (rho0 == 1000.0))
+    solid = [i for i, m in enumerate(mats) if m["kind"] == S.RIGID]
+    assert all(mats[i]["transitions_to"] >= 0 and mats[mats[i]["transitions_to"]]["kind"] == S.FLUID
+               for i in solid)
+    # one body per grain, every rigid particle belongs to one, periodic in x and y
+    nb = len(sc["bodies"]["quat"])
+    assert 0 < nb <= 40
+    assert np.all(p["body"][k == S.RIGID] >= 0) and np.all(p["body"][k != S.RIGID] < 0)
+    assert list(sc["params"]["periodic"][:2]) == [1, 1]
+    # the substrate lies below z = 0, the grains above it
+    z = p["pos"][:, 2]
+    assert z[k == S.WALL].min() < 0.0 < z[k == S.RIGID].min()
