@@ -35,3 +35,19 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
         assert "not built" in str(e)
     else:
         raise AssertionError("expected SphError")
+
+
+def test_no_cpu_fallback_without_a_device():
+    """Without a GPU every entry point that needs the device reports a CUDA error: there is
+    no host path that would compute the sweep instead."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2103_07925_gb300 import scenes as S
+    sc = S.periodic_box(dim=3, n=6, dx=0.1)
+    for make in (lambda: sph.Scene(sc, precision=32), lambda: sph.Scene(sc, precision=64),
+                 lambda: sph.Batch(capacity=4)):
+        with pytest.raises(sph.SphError) as e:
+            make()
+        assert e.value.status == -3  # SPH_ERR_CUDA
