@@ -51,3 +51,21 @@ def test_no_cpu_fallback_without_a_device():
         with pytest.raises(sph.SphError) as e:
             make()
         assert e.value.status == -3  # SPH_ERR_CUDA
+
+
+def test_binding_tables_match_the_header():
+    """Field bits, their widths and types, status codes and the profile stage count of the
+    binding are the header's."""
+    txt = open(os.path.join(ROOT, "include", "sph.h")).read()
+    fields = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"SPH_F_([A-Z]+) = (\d+),", txt)}
+    assert fields == sph.FIELDS
+    assert int(re.search(r"SPH_F_COUNT = (\d+)", txt).group(1)) == len(sph.FIELDS)
+    typed = list(re.finditer(r"SPH_F_([A-Z]+) = \d+,\s*/\*\s*n(\*3)?\s+(double|int32)", txt))
+    assert len(typed) == len(sph.FIELDS)
+    for m in typed:
+        nm = m.group(1).lower()
+        assert (nm in sph._VEC) == (m.group(2) is not None), nm
+        assert (nm in sph._INT) == (m.group(3) == "int32"), nm
+    status = {int(v): "SPH_" + k for k, v in re.findall(r"SPH_(OK|ERR_[A-Z]+) = (-?\d+)", txt)}
+    assert status == sph.STATUS
+    assert int(re.search(r"#define SPH_PROFILE_STAGES (\d+)", txt).group(1)) == sph.PROFILE_STAGES
