@@ -534,6 +534,19 @@ static void rigid_arm(const orc_scene* s, int64_t i, double* rr) {
   matvec(R, &s->rb[3 * i], rr);
 }
 
+/* acceleration of the material point of rigid particle i in its body's motion:
+ * a_k + alpha_k x r_rk + w_k x (w_k x r_rk), with the body accelerations of the last
+ * evaluation (R4, R10) */
+static void rigid_point_acc(const orc_scene* s, int64_t i, double* a) {
+  int32_t b = s->body[i];
+  double rr[3], t1[3], t2[3], t3[3];
+  rigid_arm(s, i, rr);
+  cross3(&s->bal[3 * b], rr, t1);
+  cross3(&s->bw[3 * b], rr, t2);
+  cross3(&s->bw[3 * b], t2, t3);
+  for (int k = 0; k < 3; k++) a[k] = s->ba[3 * b + k] + t1[k] + t3[k];
+}
+
 /* boundary / rigid extrapolation (R4) */
 static void extrapolate(orc_scene* s) {
 #pragma omp parallel for schedule(dynamic, 256)
@@ -544,16 +557,8 @@ static void extrapolate(orc_scene* s) {
     if (kind == ORC_WALL) {
       for (int k = 0; k < 3; k++) uw[k] = s->wu[3 * w + k];
     } else {
-      int32_t b = s->body[w];
-      double rr[3], t1[3], t2[3], t3[3];
-      rigid_arm(s, w, rr);
-      cross3(&s->bal[3 * b], rr, t1);
-      cross3(&s->bw[3 * b], rr, t2);
-      cross3(&s->bw[3 * b], t2, t3);
-      for (int k = 0; k < 3; k++) {
-        uw[k] = s->u[3 * w + k];
-        aw[k] = s->ba[3 * b + k] + t1[k] + t3[k];
-      }
+      rigid_point_acc(s, w, aw);
+      for (int k = 0; k < 3; k++) uw[k] = s->u[3 * w + k];
     }
     double S = 0.0, P = 0.0, Rv[3] = {0, 0, 0}, U[3] = {0, 0, 0};
     for (int64_t q = s->nstart[w]; q < s->nstart[w + 1]; q++) {
@@ -932,13 +937,8 @@ static int relabel(orc_scene* s) {
   for (int64_t i = 0; i < n; i++) {
     if (flag[i] != 1) continue;
     int32_t k = s->body[i];
-    double rr[3], t1[3], t2[3], t3[3];
-    rigid_arm(s, i, rr);
-    cross3(&s->bal[3 * k], rr, t1);
-    cross3(&s->bw[3 * k], rr, t2);
-    cross3(&s->bw[3 * k], t2, t3);
+    rigid_point_acc(s, i, &s->a[3 * i]);
     for (int q = 0; q < 3; q++) {
-      s->a[3 * i + q] = s->ba[3 * k + q] + t1[q] + t3[q];
       s->ab[3 * i + q] = 0.0; /* R15 */
       s->tv[3 * i + q] = 0.0;
     }

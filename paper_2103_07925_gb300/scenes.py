@@ -747,3 +747,115 @@ def conc_slab(dim=2, n=(48, 8), dx=1.0 / 48, C0=0.5, A=0.2, D=1.0, rho0=1.0, c=1
     p = default_params(dim, dx, [0.0] * dim, L, periodic=[1] * dim + [0] * (3 - dim), dt_mode=0, dt_fixed=dt,
                        precision=precision)
     return b.finish(p, [material(FLUID, rho0, c=c, diffusivity=D)])
+
+
+# --------------------------------------------------------------------------- closed-form harnesses
+
+def dirichlet_slab(dim=2, nx=40, ny=6, dx=0.025, T_left=300.0, T_right=400.0, T0=300.0, kappa=1.0,
+                   cp=1.0, rho0=1.0, wall_kappa=0.0, wall_density=None, linear=False, c=1e-3, dt=None,
+                   precision=64):
+    """Fluid slab at rest between two blocks of Dirichlet wall particles (three layers each,
+    Sec. 3.3.4) along x; periodic across (y, and z in 3D).
+
+    The fluid fills [0, nx dx) on the dx lattice and starts at T0; the walls sit at
+    [-3 dx, 0) and [nx dx, nx dx + 3 dx) with prescribed temperatures T_left and T_right.
+    With ``linear`` every particle (fluid and wall) starts on the straight line through
+    (0, T_left) and (nx dx, T_right).  ``wall_kappa`` is the conductivity of the wall
+    material (the heat sum must not use it: walls take kappa_b = kappa_a); ``wall_density``
+    is the wall particles' given density (default rho0).  A tiny sound speed keeps the
+    lattice at rest.
+    """
+    L = nx * dx
+    tr = [ny] * (dim - 1)
+    fl = _pad3(lattice([0.0] * dim, [nx] + tr, dx))
+    wl = _pad3(lattice([-3 * dx] + [0.0] * (dim - 1), [3] + tr, dx))
+    wr = _pad3(lattice([L] + [0.0] * (dim - 1), [3] + tr, dx))
+    line = lambda x: T_left + (T_right - T_left) * x / L  # noqa: E731
+    rw = rho0 if wall_density is None else wall_density
+    b = _Builder(dim)
+    mats = [material(FLUID, rho0, c=c, eta=0.0, cp=cp, kappa=kappa), material(WALL, rho0, cp=cp, kappa=wall_kappa)]
+    b.add(fl, 0, rho0 * dx ** dim, rho0, line(fl[:, 0]) if linear else T0)
+    b.add(wl, 1, rho0 * dx ** dim, rw, 300.0, wall_T=line(wl[:, 0]) if linear else T_left)
+    b.add(wr, 1, rho0 * dx ** dim, rw, 300.0, wall_T=line(wr[:, 0]) if linear else T_right)
+    if dt is None:
+        dt = 0.05 * rho0 * cp * dx * dx / kappa
+    W = ny * dx
+    p = default_params(dim, dx, [-3 * dx] + [0.0] * (dim - 1), [L + 3 * dx] + [W] * (dim - 1),
+                       periodic=[0] + [1] * (dim - 1) + [0] * (3 - dim), dt_mode=0, dt_fixed=dt,
+                       precision=precision)
+    return b.finish(p, mats)
+
+
+def rigid_container2d(dx=0.01, inner=0.2, layers=3, rho_f=1.0, rho_c=2.0, c=10.0, eta=0.01, g=-1.0,
+                      omega=0.0, dt=None, precision=64):
+    """A closed square container of inner edge ``inner`` made of ONE rigid body (``layers``
+    rows of rigid particles on the dx lattice), filled with fluid, alone in open space (no
+    wall particles).  The fluid starts with the container's rigid-body velocity field:
+    rotation at ``omega`` about the container's centre (at the origin).  Gravity g along y."""
+    n = int(round(inner / dx))
+    lo = -0.5 * n * dx
+    fl = _pad3(lattice([lo, lo], [n, n], dx))
+    sh = wall_shell(2, [n, n], dx, layers=layers) + lo
+    vel = np.zeros_like(fl)
+    vel[:, 0] = -omega * fl[:, 1]
+    vel[:, 1] = omega * fl[:, 0]
+    b = _Builder(2)
+    mats = [material(FLUID, rho_f, c=c, eta=eta), material(RIGID, rho_c)]
+    b.add(fl, 0, rho_f * dx * dx, rho_f, 300.0, vel=vel)
+    kb = b.add_body(omega=(0.0, 0.0, omega))
+    b.add(_pad3(sh), 1, rho_c * dx * dx, rho_c, 300.0, body=kb)
+    if dt is None:
+        dt = 0.25 * dx / c
+    p = default_params(2, dx, [-2.0, -2.0], [2.0, 2.0], gravity=[0.0, g, 0.0], dt_mode=0, dt_fixed=dt,
+                       precision=precision)
+    return b.finish(p, mats)
+
+
+def ellipsoid_in_fluid(n=10, dx=0.1, semi_axes=(0.36, 0.24, 0.16), omega=(0.7, -0.4, 1.1), vel=(0.05, -0.02, 0.03),
+                       vel_amp=0.05, c=10.0, rho0=1.0, eta=0.05, body_density=2.0, g=(0.3, -0.5, -1.0), seed=3,
+                       precision=64):
+    """Wall-free, non-periodic 3D block of fluid (n^3 lattice sites, seeded random
+    velocities) with one rigid ellipsoid at its centre whose principal axes lie along the
+    coordinate axes (an anisotropic inertia tensor); the body spins about an axis that is
+    not principal.  Gravity and every vector are general, so the scene has no symmetry."""
+    rng = np.random.default_rng(seed)
+    sites = lattice([0.0] * 3, [n] * 3, dx)
+    mid = 0.5 * n * dx
+    a = np.asarray(semi_axes, float)
+    inside = np.sum(((sites - mid) / a) ** 2, axis=1) <= 1.0
+    mats = [material(FLUID, rho0, c=c, eta=eta), material(RIGID, body_density)]
+    b = _Builder(3)
+    fl = sites[~inside]
+    u = rng.uniform(-vel_amp, vel_amp, size=(len(fl), 3))
+    b.add(fl, 0, rho0 * dx ** 3, rho0, 300.0, vel=u)
+    kb = b.add_body(vel=vel, omega=omega)
+    b.add(sites[inside], 1, body_density * dx ** 3, body_density, 300.0, body=kb)
+    pad = 6 * dx
+    L = n * dx
+    p = default_params(3, dx, [-pad] * 3, [L + pad] * 3, gravity=list(g), dt_mode=0, dt_fixed=0.05 * dx / c,
+                       precision=precision)
+    return b.finish(p, mats)
+
+
+def heated_grains(dim=2, T0=(250.0, 290.0, 305.0, 309.0), spacing=1.0, dx=0.1, T_t=310.0, mushy=8.0,
+                  latent=40.0, cp_s=1.0, cp_l=2.0, rho_s=3.0, rho_l=3.0, Q0=2.0e3, dt=1e-3, precision=64):
+    """Single-particle grains of a melting material, ``spacing`` apart (no neighbour within
+    r_c), each its own rigid body, heated by the surface source made uniform over them (a
+    radius so large that its Gaussian factor rounds to 1, a depth that covers every grain):
+    every grain receives the same power density Q0 and nothing else."""
+    b = _Builder(dim)
+    mats = [material(RIGID, rho_s, cp=cp_s, T_transition=T_t, transitions_to=1, latent_heat=latent,
+                     mushy_width=mushy),
+            material(FLUID, rho_l, c=1.0, cp=cp_l, T_transition=T_t, transitions_to=0, latent_heat=latent,
+                     mushy_width=mushy)]
+    for q, T in enumerate(T0):
+        kb = b.add_body()
+        pos = np.zeros(3)
+        pos[0] = q * spacing
+        b.add(pos, 0, rho_s * dx ** dim, rho_s, T, body=kb)
+    lo = [-spacing] * dim
+    hi = [len(T0) * spacing] + [spacing] * (dim - 1)
+    p = default_params(dim, dx, lo, hi, dt_mode=0, dt_fixed=dt, precision=precision,
+                       src_power=Q0, src_radius=1e9, src_speed=[0.0, 0.0, 0.0], src_origin=[0.0, 0.0, 0.0],
+                       src_depth=1e12, src_ztop=1e6, body_capacity=len(T0) + 4)
+    return b.finish(p, mats)

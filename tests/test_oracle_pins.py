@@ -703,3 +703,301 @@ def test_shepard_filter_without_contributing_particles_is_nan():
     q = np.array([[0.5, 0.4, 0.0], [0.1, 0.9, 0.0]])  # disc centre; far from the disc
     v = o.interpolate(q, "vel", material_mask=1 << 2)  # the disc's material only
     assert np.isfinite(v[0]).all() and np.isnan(v[1]).all()
+
+
+# --------------------------------------------------------------------------- Dirichlet walls (Sec. 2.3, Eq. heat_equation)
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_linear_temperature_with_dirichlet_walls_on_its_extension_is_stationary(dim):
+    """Walls hold the straight-line temperature of the fluid's profile, extended into the
+    wall block.  Wall neighbours take kappa_b := kappa_a (the wall material's own kappa,
+    set to 0 here, must not enter), so every fluid particle, including those next to the
+    walls, sees a complete lattice of equal pair weights on a linear field: dT/dt = 0 to
+    rounding.  The wall density is set to the fluid's lattice density so that V_b is
+    equal on both sides.  A wrong wall conductance, a wrong sign of T_ab against a wall, or
+    the wall material's kappa would each leave the near-wall particles with a rate."""
+    dx = 1.0 / 24
+    sc = S.dirichlet_slab(dim=dim, nx=24, ny=6, dx=dx, linear=True, wall_kappa=0.0)
+    f = sc["particles"]["material"] == 0
+    rho = O.OracleScene(sc).get("rho")[f]
+    # the interior lattice density of the kernel remark (the partition-of-unity values)
+    assert abs(rho.mean() - (1.0000632246 if dim == 2 else 0.9999799597)) < 1e-10
+    sc["particles"]["density"][~f] = rho.mean()
+    dT = O.OracleScene(sc).get("dtemp")[f]
+    scale = 1.0 * 100.0 / (rho.mean() * 1.0 * 1.0 * dx)  # kappa (T2 - T1) / (rho c_p L dx)
+    assert np.abs(dT).max() < 1e-12 * scale
+
+
+def _dirichlet_series(x, t, T0, T1, T2, L, alpha, N=2000):
+    """Start-up of 1D conduction between walls held at T1 (x = 0) and T2 (x = L), uniform T0
+    at t = 0: T = T1 + (T2 - T1) x / L + sum_n B_n sin(n pi x / L) exp(-alpha (n pi / L)^2 t),
+    B_n = 2 / (n pi) [(T0 - T1)(1 - (-1)^n) + (T2 - T1)(-1)^n]."""
+    n = np.arange(1, N + 1)[:, None]
+    B = 2.0 / (n * np.pi) * ((T0 - T1) * (1 - (-1.0) ** n) + (T2 - T1) * (-1.0) ** n)
+    return T1 + (T2 - T1) * x / L + np.sum(B * np.sin(n * np.pi * x / L) * np.exp(-alpha * (n * np.pi / L) ** 2 * t),
+                                           axis=0)
+
+
+def test_dirichlet_walls_start_up_follows_the_series_and_converges():
+    """Fluid at T0 between walls at T1 = T0 and T2 = T0 + 100 (Dirichlet, Sec. 2.3): the
+    temperature at t = 0.02 follows the closed-form series of the 1D heat equation, with an
+    error that halves with dx (the wall temperature acts at the first wall row, dx/2 from
+    the fluid edge, which shifts the boundary by O(dx))."""
+    errs = []
+    for nx in (20, 40):
+        dx = 1.0 / nx
+        sc = S.dirichlet_slab(dim=2, nx=nx, ny=6, dx=dx, T_left=300.0, T_right=400.0, T0=300.0)
+        o = O.OracleScene(sc)
+        f = sc["particles"]["material"] == 0
+        alpha = 1.0 / o.get("rho")[f].mean()  # kappa / (rho c_p)
+        steps = int(round(0.02 / sc["params"]["dt_fixed"]))
+        o.step(steps)
+        x, T = o.get("pos")[f, 0], o.get("temp")[f]
+        errs.append(np.abs(T - _dirichlet_series(x, steps * sc["params"]["dt_fixed"], 300.0, 300.0, 400.0, 1.0,
+                                                 alpha)).max() / 100.0)
+    assert errs[0] < 0.12 and errs[1] < 0.06, errs
+    assert errs[0] / errs[1] > 1.8, errs
+
+
+def test_dirichlet_walls_steady_profile_is_linear_with_the_boundary_at_the_first_wall_row():
+    """Steady state between walls at T1 and T2: linear in x, and the line reaches T1 and T2
+    half a spacing outside the fluid (at the first row of wall particles, which carry the
+    prescribed temperature), for every dx.  A wall pair weight other than the fluid's
+    (kappa_b := kappa_a) moves this point by more than a spacing."""
+    for nx in (10, 20):
+        dx = 1.0 / nx
+        sc = S.dirichlet_slab(dim=2, nx=nx, ny=6, dx=dx, T_left=300.0, T_right=400.0, T0=350.0, dt=0.2 * dx * dx)
+        o = O.OracleScene(sc)
+        f = sc["particles"]["material"] == 0
+        o.step(int(round(0.8 / sc["params"]["dt_fixed"])))
+        x, T = o.get("pos")[f, 0], o.get("temp")[f]
+        A = np.stack([np.ones_like(x), x], 1)
+        c = np.linalg.lstsq(A, T, rcond=None)[0]
+        assert np.abs(T - A @ c).max() < 0.02 * 100.0 * dx
+        lo, hi = (300.0 - c[0]) / c[1], (400.0 - c[0]) / c[1]
+        assert abs(lo / dx + 0.5) < 0.1 and abs((hi - 1.0) / dx - 0.5) < 0.1, (lo / dx, (hi - 1.0) / dx)
+
+
+# --------------------------------------------------------------------------- moving rigid boundaries (R4)
+
+def test_free_falling_fluid_filled_container_keeps_uniform_pressure():
+    """A closed rigid container (one body) full of fluid, in free fall: container and fluid
+    share the acceleration g, so in the extrapolation of Sec. 3.3.4 (g - a_w) vanishes and
+    the fluid stays at uniform pressure with no motion relative to the container.  A wrong
+    sign of a_w doubles the effective gravity seen by the walls; a_w = 0 keeps it."""
+    g = -1.0
+    sc = S.rigid_container2d(dx=0.01, inner=0.2, g=g, eta=0.01)
+    o = O.OracleScene(sc)
+    f = sc["particles"]["material"] == 0
+    dt = sc["params"]["dt_fixed"]
+    for k in range(1, 7):
+        o.step(100)
+        p, u = o.get("pres")[f], o.get("vel")[f]
+        b = o.bodies()
+        assert (p.max() - p.min()) < 2e-3 * 1.0 * abs(g) * 0.2  # of rho |g| H
+        assert np.abs(u - b["vel"][0]).max() < 2e-5
+        # the body follows g t (up to the start-up, where a_w of the initial evaluation is 0)
+        assert abs(b["vel"][0][1] - g * 100 * k * dt) < 1e-5
+
+
+def test_spinning_container_pushes_the_adjacent_fluid_towards_its_centre():
+    """A closed rigid container spinning at w with the fluid in solid-body rotation (no
+    gravity, inviscid), initial evaluation: the fluid has uniform pressure, so only the
+    walls act, and they must supply a centripetal force, a_w = w x (w x r) entering
+    (g - a_w) of the extrapolation.  Fluid in the row next to the container accelerates
+    towards the centre at a fraction of w^2 r; the interior does not accelerate.  The
+    opposite sign of the term pulls the row outwards; without the term it stays put."""
+    w = 4.0
+    sc = S.rigid_container2d(dx=0.01, inner=0.2, g=0.0, eta=0.0, omega=w)
+    o = O.OracleScene(sc)
+    f = sc["particles"]["material"] == 0
+    x, a = o.get("pos")[f][:, :2], o.get("acc")[f][:, :2]
+    r = np.linalg.norm(x, axis=1)
+    ar = np.sum(a * x, 1) / r / (w * w * r)  # radial acceleration in units of w^2 r
+    dwall = 0.1 - np.abs(x).max(1)
+    first = dwall < 0.01
+    interior = dwall > 0.02
+    assert np.all(ar[first] < -0.2) and np.all(ar[first] > -1.0), (ar[first].min(), ar[first].max())
+    assert np.abs(ar[interior]).max() < 1e-9
+
+
+def test_melted_particle_takes_the_acceleration_of_its_material_point():
+    """A spinning rigid sphere pressed by one wall particle (contact force and torque), hot
+    enough to melt in its first step: each particle leaves the body with the acceleration
+    its material point had in the rigid motion, a_k + alpha_k x r + w_k x (w_k x r) (rigid
+    body kinematics; reading R10), with a_k = f_k / m_k and alpha_k = I_k^-1 m_k of the
+    step's evaluation.  The same helper gives a_w in the extrapolation of Sec. 3.3.4."""
+    sc = S.free_fall(dim=3, dx=0.1, radius=0.35, density=3.0, g=-9.81, omega=(1.5, -2.0, 3.0))
+    mats = sc["materials"]
+    mats[1].update(T_transition=1000.0, transitions_to=0)
+    mats.append(S.material(S.WALL, 1.0))
+    p = sc["particles"]
+    p["temperature"][:] = 1200.0
+    x = p["pos"]
+    top = int(np.argmax(x[:, 0] + 0.3 * x[:, 1]))  # an off-centre particle on the surface
+    wall = x[top] + np.array([0.09, 0.0, 0.0])
+    for k in p:
+        a = np.asarray(p[k])
+        p[k] = np.concatenate([a, a[top:top + 1]], axis=0)
+    p["pos"][-1] = wall
+    p["material"][-1] = 2
+    p["body"][-1] = -1
+    p["vel"][-1] = 0.0
+    p["wall_velocity"][-1] = 0.0
+    sc["params"]["k_contact"] = 50.0
+    sc["params"]["d_contact"] = 0.5
+    o = O.OracleScene(sc)
+    o.step(1)
+    b = o.bodies()
+    assert b["alive"][0] == 0 and np.all(o.get("mat")[:-1] == 0)
+    ak = b["force"][0] / b["mass"][0]
+    al = np.linalg.solve(b["inertia"][0], b["torque"][0])
+    assert np.linalg.norm(b["torque"][0]) > 1e-3 and np.linalg.norm(al) > 1e-2  # the contact acts
+    w = b["omega"][0]
+    r = o.get("pos")[:-1] - b["com"][0]
+    expect = ak + np.cross(al, r) + np.cross(w, np.cross(w, r))
+    acc = o.get("acc")[:-1]
+    assert np.abs(acc - expect).max() < 1e-12 * np.abs(expect).max()
+
+
+# --------------------------------------------------------------------------- anisotropic inertia (Eq. angularmomentum)
+
+def _qmul(a, b):
+    w1, x1, y1, z1 = a
+    w2, x2, y2, z2 = b
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+
+def test_frame_rotation_covariance_with_an_anisotropic_body():
+    """Rotating a whole scene (positions, velocities, gravity, body velocity and angular
+    velocity, and the body orientation q -> q_R o q) by a fixed rotation R maps every output
+    to R applied to the unrotated output (scalars unchanged), to rounding.  The body is an
+    ellipsoid with distinct principal moments spinning about a non-principal axis in a
+    viscous fluid (torque from the fluid), so alpha = R(q) I_body^-1 R(q)^T m: using the
+    body-frame inertia in place of the world inertia, or a transposed rotation, breaks it."""
+    sc = S.ellipsoid_in_fluid()
+    ax = np.array([0.3, -0.8, 0.5])
+    ax /= np.linalg.norm(ax)
+    ang = 1.1
+    qR = np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * ax])
+    R = O.quat_rot(qR)
+    c = 0.5
+    rot = copy.deepcopy(sc)
+    rp, rb = rot["particles"], rot["bodies"]
+    rp["pos"] = (sc["particles"]["pos"] - c) @ R.T + c
+    rp["vel"] = sc["particles"]["vel"] @ R.T
+    rot["params"]["gravity"] = list(R @ np.asarray(sc["params"]["gravity"]))
+    rb["vel"] = sc["bodies"]["vel"] @ R.T
+    rb["omega"] = sc["bodies"]["omega"] @ R.T
+    rb["quat"] = np.array([_qmul(qR, q) for q in sc["bodies"]["quat"]])
+    for s in (sc, rot):
+        s["params"]["box_min"] = [c - 1.0] * 3
+        s["params"]["box_max"] = [c + 1.0] * 3
+    oa, ob = O.OracleScene(sc), O.OracleScene(rot)
+    oa.step(30)
+    ob.step(30)
+    assert np.abs((oa.get("pos") - c) @ R.T + c - ob.get("pos")).max() < 1e-12
+    for f in ("vel", "acc", "force", "vext"):
+        B = ob.get(f)
+        assert np.abs(oa.get(f) @ R.T - B).max() < 1e-12 * np.abs(B).max(), f
+    for f in ("rho", "pres"):
+        B = ob.get(f)
+        assert np.abs(oa.get(f) - B).max() < 1e-12 * np.abs(B).max(), f
+    ba, bb = oa.bodies(), ob.bodies()
+    ev = np.linalg.eigvalsh(ba["inertia"][0])
+    assert ev[1] / ev[0] > 1.5 and ev[2] / ev[1] > 1.1  # anisotropic
+    for f in ("omega", "torque", "vel", "force"):
+        assert np.abs(ba[f] @ R.T - bb[f]).max() < 1e-12 * np.abs(bb[f]).max(), f
+    assert np.abs((ba["com"] - c) @ R.T + c - bb["com"]).max() < 1e-12
+    assert np.abs(np.array([_qmul(qR, q) for q in ba["quat"]]) - bb["quat"]).max() < 1e-12
+    assert np.abs(R @ ba["inertia"][0] @ R.T - bb["inertia"][0]).max() < 1e-12 * ev[2]
+
+
+# --------------------------------------------------------------------------- apparent capacity (R11)
+
+def test_temperature_of_grains_heated_through_the_mushy_interval():
+    """Isolated single-particle grains of a melting material under a uniform source: the
+    specific energy E(t) = sum dt q / rho they receive raises T at 1/c_s below the interval,
+    at w / (c_s w + L) inside it (the interval absorbs the latent heat L on top of c_s w)
+    and at 1 / c_l above it, with melting at T_t (apparent-capacity extension of the remark
+    on latent heat).  Grains start below, inside and just under T_t."""
+    T0 = np.array([250.0, 290.0, 305.0, 309.0])
+    Tt, w, L, cs, cl, Q = 310.0, 8.0, 40.0, 1.0, 2.0, 2.0e3
+    sc = S.heated_grains(T0=tuple(T0), T_t=Tt, mushy=w, latent=L, cp_s=cs, cp_l=cl, Q0=Q)
+    o = O.OracleScene(sc)
+    dt = sc["params"]["dt_fixed"]
+    Tlo = Tt - 0.5 * w
+    e1 = np.maximum(cs * (Tlo - T0), 0.0)                      # sensible heat up to the interval
+    e2 = cs * w + L - np.where(T0 > Tlo, (T0 - Tlo) * (cs + L / w), 0.0)  # what is left of it
+    E = np.zeros(len(T0))
+    melted = np.zeros(len(T0), bool)
+    for _ in range(200):
+        o.step(1)
+        E = E + dt * Q / o.get("rho")  # the source of the step at the step's density
+        T = o.get("temp")
+        expect = np.where(E <= e1, T0 + E / cs,
+                          np.where(E <= e1 + e2, np.maximum(T0, Tlo) + (E - e1) * w / (cs * w + L),
+                                   Tlo + w + (E - e1 - e2) / cl))
+        assert np.abs(T - expect).max() < 1e-9, (T, expect)
+        mat = o.get("mat")
+        assert np.all((mat == 1) == (melted | (T > Tt)))  # melt at the end of the step that crosses T_t
+        melted |= mat == 1
+    assert np.all(melted) and np.all(T > Tlo + w)
+
+
+# --------------------------------------------------------------------------- time step (Eq. timestepcond)
+
+def _dt_of(sc):
+    o = O.OracleScene(sc)
+    o.step(1)
+    return o.diagnostics()[11]
+
+
+def test_time_step_velocity_condition_with_moving_fluid():
+    """0.25 h / (c + |u|max): |u|max is the largest fluid speed at the step's start."""
+    sc = S.heat_slab(dim=2, n=(12, 12), dx=0.1, A=0.0, kappa=0.0, c=2.0, dt=1e-3)
+    sc["params"]["dt_mode"] = 1
+    u = np.zeros((144, 3))
+    u[:, 0] = 0.3
+    u[17] = [0.6, -0.8, 0.0]  # speed 1
+    sc["particles"]["vel"] = u
+    assert abs(_dt_of(sc) - 0.25 * 0.1 / (2.0 + 1.0)) < 1e-17
+
+
+def test_time_step_viscous_condition_takes_the_largest_kinematic_viscosity():
+    """0.125 h^2 / nu with nu = eta / rho0 of the most viscous fluid phase."""
+    sc = S.heat_slab(dim=2, n=(12, 12), dx=0.1, A=0.0, kappa=0.0, c=0.1, dt=1e-3)
+    sc["params"]["dt_mode"] = 1
+    sc["materials"][0]["eta"] = 0.5
+    sc["materials"].append(S.material(S.FLUID, 2.0, c=0.1, eta=3.0))  # nu = 1.5
+    sc["particles"]["material"][::7] = 1
+    assert abs(_dt_of(sc) - 0.125 * 0.01 / 1.5) < 1e-18
+
+
+def test_time_step_body_force_condition():
+    """0.25 sqrt(h / |b|max) with the body force of gravity."""
+    sc = S.heat_slab(dim=2, n=(12, 12), dx=0.1, A=0.0, kappa=0.0, c=0.01, dt=1e-3)
+    sc["params"]["dt_mode"] = 1
+    sc["params"]["periodic"] = [1, 0, 0]
+    sc["params"]["box_min"][1] = -10.0
+    sc["params"]["box_max"][1] = 10.0
+    sc["params"]["gravity"] = [0.0, -30.0, 40.0 * 0.0]
+    assert abs(_dt_of(sc) - 0.25 * math.sqrt(0.1 / 30.0)) < 1e-17
+
+
+def test_time_step_contact_condition_takes_the_lightest_rigid_particle():
+    """0.22 sqrt(m_r / k_c) with the smallest rigid particle mass."""
+    sc = S.contact_pair(dim=2, dx=0.1, k_contact=1e6, d_contact=0.0)
+    sc["params"]["dt_mode"] = 1
+    sc["particles"]["mass"][1] = 0.5 * sc["particles"]["mass"][0]
+    mr = sc["particles"]["mass"][1]
+    assert abs(_dt_of(sc) - 0.22 * math.sqrt(mr / 1e6)) < 1e-18
+
+
+def test_time_step_heat_condition_takes_the_smallest_diffusion_time():
+    """0.1 rho c_p h^2 / kappa, minimised over the conducting phases (fluid and rigid)."""
+    sc = S.heat_slab(dim=2, n=(12, 12), dx=0.1, A=0.0, kappa=2.0, cp=3.0, c=0.01)
+    sc["params"]["dt_mode"] = 1
+    sc["materials"].append(S.material(S.RIGID, 5.0, cp=0.2, kappa=10.0))  # rho c_p / kappa = 0.1
+    assert abs(_dt_of(sc) - 0.1 * 0.1 * 0.01) < 1e-18
