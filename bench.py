@@ -31,8 +31,7 @@ BYTES_PER_TARGET = 72   # algorithmic HBM bytes per target particle of the force
 # `ncu --set full` capture of this kernel version, per cell layout (key order, skin in h) it
 # was captured with; emptied whenever the kernel changes
 K_FORCE_TRAFFIC = {(1, 0.3): 734.6e6}
-FP32_LANES_PER_SM = 128
-N_SM = 152
+FP32_LANES_PER_SM = 128  # nominal, for the context figure beside the measured peak
 
 
 def parse():
@@ -136,11 +135,33 @@ def workload(dx, name="tank3d"):
     return scenes.tank3d_spheres(dx=dx)
 
 
+REF_BUDGET_S = 150.0  # timed oracle steps of the reference arm stop within about this
+
+
+def oracle_single_thread(dx, name):
+    """Pair rate of the oracle on one host thread: one step of the same scene in a child
+    process with OMP_NUM_THREADS=1 (the oracle's OpenMP loops then run serially)."""
+    code = ("import sys, time, json; sys.path.insert(0, %r)\n"
+            "import bench\n"
+            "from oracle.oracle import OracleScene\n"
+            "o = OracleScene(bench.workload(%r, %r))\n"
+            "t0 = time.perf_counter(); o.step(1); t = time.perf_counter() - t0\n"
+            "print(json.dumps({'value': o.diagnostics()[15] / t, 'seconds': t}))\n") % (ROOT, dx, name)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+            "sample": "1 FP64 oracle step of the same scene on one thread (%.1f s)" % d["seconds"]}
+
+
 def run_reference(args):
     """The FP64 CPU oracle on the host cores (rank 0 only) on the same scene as our arm.
-    Bounded sample: at most 1 warm-up step and 10 timed steps, whatever --steps/--warmup
-    say (one oracle step of the 1.28M-particle tank takes about a second on 16 cores); the
-    value is a rate, so it does not depend on the number of steps timed."""
+    It runs the requested warm-up and timed steps while they fit in about REF_BUDGET_S
+    seconds (one oracle step of the 1.28M-particle tank takes about 1.5 s on 16 cores) and
+    prints the numbers of steps it actually ran; the value is a rate.  A single-thread rate
+    of the oracle is reported beside it."""
     from oracle.oracle import OracleScene
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -149,8 +170,14 @@ def run_reference(args):
     dx = args.dx or DEFAULT_DX[name]
     sc = workload(dx, name)
     o = OracleScene(sc)
-    w, k = min(args.warmup, 1), max(1, min(args.steps, 10))
+    t0 = time.perf_counter()
+    o.step(1)  # one untimed step sizes the sample
+    t_one = time.perf_counter() - t0
+    fit = max(1, int(REF_BUDGET_S / max(t_one, 1e-9)))
+    k = max(1, min(args.steps, fit))
+    w = max(0, min(args.warmup - 1, fit - k))
     o.step(w)
+    w += 1
     t0 = time.perf_counter()
     pairs = 0.0
     for _ in range(k):
@@ -161,14 +188,16 @@ def run_reference(args):
     cores = os.cpu_count()
     n = len(sc["particles"]["mass"])
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "pair-interactions/s",
-           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "n_gpus": args.gpus, "steps": k, "warmup": w,
            "ms_per_step": 1e3 * t / k, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD_NAME[name] % dx, "particles": n,
-                      "l2": "inputs larger than L2"},
+                      "l2": "inputs larger than L2",
+                      "requested": {"steps": args.steps, "warmup": args.warmup}},
            "cpu_baseline": {"value": val, "unit": "pair-interactions/s", "cores": cores, "kind": "oracle",
                             "sample": "%d timed FP64 oracle steps (after %d warm-up) of the same %d-particle "
                                       "scene" % (k, w, n)},
+           "cpu_baseline_1thread": oracle_single_thread(dx, name),
            "e2e": {"value": val, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -357,8 +386,11 @@ def main():
     if args.workload == "serve":
         bench_serve(args, rank, world, allmax, allsum, barrier)
         return
-    from paper_2103_07925_gb300.sph import Scene
+    from paper_2103_07925_gb300.sph import Scene, fp32_peak
     hbm, smmax, peak_src = peaks()
+    # FP32 FMA peak of this GPU, measured by the library's own microbenchmark (best of four
+    # launches of about 40 ms), and the SM count it found
+    peak_tf, n_sm, _ = fp32_peak()
     dx = args.dx or DEFAULT_DX[args.workload]
     sc = workload(dx, args.workload)
     if args.p_background > 0:
@@ -408,8 +440,9 @@ def main():
     force_ms = prof["force"]
     pairs_per_step = pairs / args.steps
     achieved_tf = pairs_per_step * FLOP_PER_PAIR / (force_ms * 1e-3) / 1e12
-    clock_mhz = smmax
-    peak_tf = N_SM * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+    # context: the nominal FP32 peak at the SM clock sampled during the timed region
+    clock_mhz = clk["sm_mhz"] or smmax
+    nominal_tf = n_sm * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
     n_targets = info["n_fluid"] + info["n_rigid"]
     hbm_ach = n_targets * BYTES_PER_TARGET / (force_ms * 1e-3) / 1e9
     out = {"metric": METRIC, "value": value, "unit": "pair-interactions/s", "n_gpus": world,
@@ -438,7 +471,10 @@ def main():
                         if (args.workload == "tank3d" and dx == 0.01 and args.precision == 32
                             and args.p_background == 0) else None,
                         "kernel": "k_force",
-                        "peak_source": "FP32 FMA lanes x SMs x 2 x max SM clock (%s clocks)" % peak_src,
+                        "peak_source": "measured: FP32 FMA microbenchmark of the library (sph_fp32_peak) on this "
+                                       "GPU, %d SMs" % n_sm,
+                        "nominal_at_sampled_clock": {"value": nominal_tf, "sm_mhz": clock_mhz,
+                                                     "frac": achieved_tf / nominal_tf},
                         "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": hbm, "frac": hbm_ach / hbm,
                                 "peak_source": peak_src}},
            "profile_ms": prof, "clocks": clk}
@@ -479,11 +515,15 @@ def main():
         a32.step(99)
         a64.step(99)
         b100 = body_errors(a32.bodies(), a64.bodies(), sc, a64.read("body"))
+        # the same without term scales: relative to max(|x64|, RMS(x64)) of the field itself
+        plain1 = {f: rel_err(f32[f], f64[f]) for f in flds}
         out["fp32_vs_fp64"] = {"step1_fields": step1,
+                               "step1_fields_plain": plain1,
                                "step1_without_edge_only_boundary": dict(step1_edge, particles_excluded=int(edge.sum())),
                                "bodies_after_100_steps": b100,
                                "tolerance": {"fields_per_step": 1e-5, "bodies_100_steps": 1e-3},
-                               "metric": "max |x32 - x64| / max(|x64|, RMS(x64), term scale of the field)"}
+                               "metric": "max |x32 - x64| / max(|x64|, RMS(x64), term scale of the field); "
+                                         "plain: max |x32 - x64| / max(|x64|, RMS(x64))"}
         a32.close()
         a64.close()
     # end to end through the C ABI with host buffers: the host holds the fluid state; every

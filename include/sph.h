@@ -161,8 +161,12 @@ sph_status sph_create_scene(const sph_params* params, const sph_particles_in* pa
                             const sph_bodies_in* bodies, void* stream, sph_scene** out);
 
 /* Advance nsteps time steps of the velocity-Verlet scheme of Sec. 3.7 (asynchronous on
- * the scene's stream except for a final status read).  SPH_ERR_NONFINITE if the state
- * went non-finite. */
+ * the scene's stream except for a final status read).  Errors after the steps ran:
+ * SPH_ERR_NONFINITE if a fluid velocity went non-finite; SPH_ERR_CAPACITY if a phase
+ * relabel (Sec. 3.6) needed more new bodies than body_capacity; SPH_ERR_TIMEOUT if the
+ * bounded union-find hooking that groups solidifying particles into new bodies gave up.
+ * In the last two cases that relabel is not applied (materials and body ids stay as they
+ * were), and no later relabel of the scene is applied either. */
 sph_status sph_step(sph_scene* scene, int32_t nsteps);
 
 /* Same as sph_step without the final status read (no host synchronisation). */
@@ -268,6 +272,16 @@ const char* sph_profile_stage_name(int32_t stage);
 void sph_destroy_scene(sph_scene* scene);
 const char* sph_last_error(void);
 
+/* ------------------------------------------------------------------ measured FP32 peak
+ * A measurement aid (the paper has no counterpart): FP32 FMA throughput of the current
+ * device, measured by a kernel of this library that runs independent FMA chains on every
+ * SM (grid = 4 blocks of 256 threads per SM), timed with CUDA events on a stream of its own
+ * (best of four launches after a warm-up).  iters: loop trips per thread (each trip is 128
+ * FMA per thread); *tflops: 2 x FMA / s in 1e12; *sm_count (nullable): the device's SM
+ * count; *ms (nullable): the best launch time.  It allocates and frees a small output
+ * buffer.  Errors: SPH_ERR_INVALID (iters < 1 or tflops NULL), SPH_ERR_CUDA. */
+sph_status sph_fp32_peak(int32_t iters, double* tflops, int32_t* sm_count, double* ms);
+
 /* ------------------------------------------------------------------ allocation-free density
  * For callers that cannot allocate device memory: code running under a memory manager
  * that owns every device allocation, inside a region where allocation is not allowed, or
@@ -282,13 +296,16 @@ const char* sph_last_error(void);
  * The work is enqueued on stream (NULL: the default stream) and not synchronised.
  *
  * No device memory is allocated: the cell-list scratch is a fixed static device array of
- * this library (about 5 MB, held by every GPU that loads the library until exit).  Limits:
+ * this library (about 6 MB, held by every GPU that loads the library until exit).  Limits:
  * n <= SPH_STATIC_MAX_PARTICLES and at most SPH_STATIC_MAX_CELLS cells of edge >= r_c in
  * the box; larger inputs return SPH_ERR_CAPACITY without running.  The first call on a
  * device looks up the array's device address (once per device, with that device current),
- * so make that first call before any stream capture.  Every call uses the same array and
- * leaves its contents behind (the counters are cleared at the start of each call): calls
- * that overlap on the GPU, on different streams or threads, race and must be serialised. */
+ * so make that first call before any stream capture; the address is kept for the life of
+ * the process, so do not call this after cudaDeviceReset on that device.  Every call uses
+ * the same array and leaves its contents behind (the counters are cleared at the start of
+ * each call): calls that overlap on the GPU, on different streams or threads, race and
+ * must be serialised.  Particles of a cell are visited in index order: the result is the
+ * same bit for bit on every call with the same input. */
 #define SPH_STATIC_MAX_PARTICLES (1 << 18)
 #define SPH_STATIC_MAX_CELLS (1 << 18)
 sph_status sph_density_static(int32_t dim, int64_t n, const double* pos, const double* mass, double h,
@@ -318,10 +335,12 @@ sph_status sph_batch_admit(sph_batch* batch, const sph_job_desc* job, int64_t* j
 /* advance every resident, unfinished job by up to nsteps (jobs stop at nsteps_total) */
 sph_status sph_batch_step(sph_batch* batch, int32_t nsteps);
 /* ids of jobs that finished since the last poll (n_done <= max_done): jobs that reached
- * nsteps_total, and jobs whose fluid velocities became non-finite (those stop advancing;
- * sph_batch_job_state tells the two apart).  Synchronises the batch's stream. */
+ * nsteps_total, and failed jobs, which stop advancing: fluid velocities became non-finite,
+ * or a relabel could not be applied (new bodies beyond the body capacity, or the bounded
+ * union-find hooking gave up); sph_batch_job_state tells finished and failed apart.
+ * Synchronises the batch's stream. */
 sph_status sph_batch_poll(sph_batch* batch, int64_t* done_ids, int32_t max_done, int32_t* n_done);
-/* *state: 0 advancing, 1 finished (reached nsteps_total), 2 failed (non-finite velocity) */
+/* *state: 0 advancing, 1 finished (reached nsteps_total), 2 failed (see sph_batch_poll) */
 sph_status sph_batch_job_state(sph_batch* batch, int64_t job_id, int32_t* state);
 sph_status sph_batch_read_fields(sph_batch* batch, int64_t job_id, uint32_t field_mask,
                                  void* const* host_dst);

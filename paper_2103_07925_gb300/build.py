@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsph.so")
-UNITS = ["sph_capi.cu", "sph_f64.cu", "sph_f32.cu", "sph_static.cu"]
+UNITS = ["sph_capi.cu", "sph_f64.cu", "sph_f32.cu", "sph_static.cu", "sph_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler",
          "-fPIC,-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
@@ -38,15 +38,20 @@ def _stamp():
     return h.hexdigest()
 
 
-def build(force=False, verbose=False, extra=()):
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra=(), variant=None):
+    """Compile and link the library; returns its path.  ``variant``: a name for a build with
+    ``extra`` compile flags (e.g. a lowered compile-time limit), kept apart from the in-tree
+    library in ``_build/<variant>/libsph.so``."""
+    bdir = os.path.join(BUILD, variant) if variant else BUILD
+    lib = os.path.join(bdir, "libsph.so") if variant else LIB
+    os.makedirs(bdir, exist_ok=True)
     stamp = _stamp() + ("|" + " ".join(extra) if extra else "")
-    sfile = os.path.join(BUILD, "libsph.stamp")
-    if not force and os.path.exists(LIB) and os.path.exists(sfile) and open(sfile).read() == stamp:
-        return LIB
+    sfile = os.path.join(bdir, "libsph.stamp")
+    if not force and os.path.exists(lib) and os.path.exists(sfile) and open(sfile).read() == stamp:
+        return lib
 
     def compile_unit(u):
-        obj = os.path.join(BUILD, u.replace(".cu", ".o"))
+        obj = os.path.join(bdir, u.replace(".cu", ".o"))
         cmd = [nvcc()] + ARCH + FLAGS + list(extra) + ["-c", os.path.join(CSRC, u), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -57,15 +62,15 @@ def build(force=False, verbose=False, extra=()):
 
     with cf.ThreadPoolExecutor(len(UNITS)) as ex:
         objs = list(ex.map(compile_unit, UNITS))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stderr[-4000:])
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(sfile, "w") as f:
         f.write(stamp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

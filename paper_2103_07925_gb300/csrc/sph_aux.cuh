@@ -46,7 +46,7 @@ __global__ void k_import(Scene<R>* const* sc, ImportArgs a) {
     int c[3] = {0, 0, 0};
     for (int k = 0; k < S.dim; k++) {
       double v = floor(__ddiv_rn(__dsub_rn(x[k], S.lo[k]), S.ell[k]));
-      c[k] = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
+      c[k] = clamp_cell(v, S.ncell[k]);
     }
     int lin = c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]);
     S.key[i] = part_key(S, kind, lin);
@@ -121,7 +121,7 @@ __global__ void k_import_fluid(Scene<R>* const* sc, const double* pos, const dou
         if (far) {  // a jump across the box: new cell, and the lists are rebuilt next step
           for (int k = 0; k < S.dim; k++) {
             double v = floor((x[k] - S.lo[k]) / S.ell[k]);
-            c[k] = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
+            c[k] = clamp_cell(v, S.ncell[k]);
             o[k] = x[k] - (S.lo[k] + c[k] * S.ell[k]);
           }
           S.key[i] = part_key(S, S.matR[S.P.mt[i]].kind, c[0] + S.ncell[0] * (c[1] + S.ncell[1] * c[2]));
@@ -366,7 +366,7 @@ __global__ void k_interpolate(Scene<R>* const* sc, int nq, const double* q, int 
         else if (xq[k] < S.lo[k]) xq[k] += S.L[k];
       }
       double v = floor((xq[k] - S.lo[k]) / S.ell[k]);
-      c[k] = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
+      c[k] = clamp_cell(v, S.ncell[k]);
     }
     double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
     const int zl = DIM == 3 ? -1 : 0, zh = DIM == 3 ? 1 : 0;

@@ -149,7 +149,8 @@ struct Scene {
                        // [4] rebuild in this step [5] steps since rebuild [6] rebuild count
                        // [7] solidifiers without a rigid neighbour [8] new bodies this step
                        // [9] relabelled particles so far [10] lists stale (kinds changed, or a particle was moved
-                       // to another cell by a write) since they were built
+                       // to another cell by a write) since they were built [11] the union-find hooking of
+                       // new bodies gave up (retry cap): that step's relabel is not applied
   int* pfx1;           // prefix tables of this scene alone (6 x 2 ints)
   Scene<R>** self;     // device array holding the address of this descriptor
   unsigned long long* pairs;  // [0] force-sweep pairs of the last evaluation
@@ -168,6 +169,16 @@ struct BatchView {
   const int* pfx_cblk;   // scan blocks of 1024 cells
   const int* pfx_slot;   // rigid slots
 };
+
+// cell index along one axis from v = floor((x - lo) / edge), clamped to [0, n - 1]; a NaN
+// (a non-finite position) maps to cell 0 explicitly, so no index depends on how a NaN
+// converts to an integer
+__device__ __forceinline__ int clamp_cell(double v, int n) {
+  return v >= 0.0 ? (v < (double)(n - 1) ? (int)v : n - 1) : 0;
+}
+
+// status words of a scene that stop its phase relabelling (checked by the host after a step)
+enum { ST_NONFINITE = 0, ST_CAPACITY = 2, ST_HOOK_TIMEOUT = 11 };
 
 __device__ __forceinline__ int find_scene(const int* __restrict__ pfx, int nsc, int g) {
   int lo = 0, hi = nsc - 1;

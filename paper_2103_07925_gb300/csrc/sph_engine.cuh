@@ -71,10 +71,11 @@ inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
     if (d < p->dim) {
       double L = p->box_max[d] - p->box_min[d];
       if (!(L > 0)) { set_error("box_max must exceed box_min"); return SPH_ERR_INVALID; }
-      int nc = (int)std::floor(L / (S.rc + (p->skin > 0.0 ? p->skin : 0.0)));
-      if (nc < 1) nc = 1;
+      // the cell count stays a double until it is known to fit (no overflowing conversion)
+      double ncd = std::floor(L / (S.rc + (p->skin > 0.0 ? p->skin : 0.0)));
+      if (!(ncd <= (double)(1 << 20))) { set_error("too many cells on axis %d", d); return SPH_ERR_INVALID; }
+      int nc = ncd < 1.0 ? 1 : (int)ncd;
       if (S.per[d] && nc < 3) { set_error("periodic axis %d needs at least 3 cells of edge >= r_c + skin", d); return SPH_ERR_INVALID; }
-      if (nc > (1 << 20)) { set_error("too many cells on axis %d", d); return SPH_ERR_INVALID; }
       S.ncell[d] = nc;
       S.L[d] = L;
       S.ell[d] = L / nc;
@@ -971,9 +972,14 @@ sph_status Engine<R, DIM>::check_status(int idx, bool* nonfinite) {
     set_error("inconsistent cell table or particle kinds (scene %d)", idx);
     return SPH_ERR_INVALID;
   }
-  if (st[2] != 0) {
+  if (st[ST_CAPACITY] != 0) {
     set_error("body capacity exceeded by new bodies from solidification (scene %d)", idx);
     return SPH_ERR_CAPACITY;
+  }
+  if (st[ST_HOOK_TIMEOUT] != 0) {
+    set_error("union-find hooking of new bodies gave up after %d retries (scene %d): relabel not applied",
+              (int)SPH_RL_HOOK_TRIES, idx);
+    return SPH_ERR_TIMEOUT;
   }
   return SPH_OK;
 }

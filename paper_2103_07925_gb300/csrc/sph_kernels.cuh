@@ -432,8 +432,7 @@ __global__ void k_bin(BatchView<R> B, int force) {
       double x[3] = {(double)S.P.px[i], (double)S.P.py[i], (double)S.P.pz[i]};
       for (int k = 0; k < S.dim; k++) {
         double v = floor(__ddiv_rn(__dsub_rn(x[k], S.lo[k]), S.ell[k]));
-        int ci = v < 0.0 ? 0 : (v > (double)(S.ncell[k] - 1) ? S.ncell[k] - 1 : (int)v);
-        c[k] = ci;
+        c[k] = clamp_cell(v, S.ncell[k]);
       }
     } else {
       // cell-relative positions: new cell = old cell + floor(offset / edge)
@@ -441,7 +440,9 @@ __global__ void k_bin(BatchView<R> B, int force) {
       lin_xyz(S, key_lin(S, S.key[i]), co[0], co[1], co[2]);
       R o[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
       for (int k = 0; k < S.dim; k++) {
-        int d = (int)floorf((float)o[k] / (float)S.ellR[k]);
+        // cells moved along k; a non-finite offset keeps its cell (no integer conversion of a NaN)
+        float q = floorf((float)o[k] / (float)S.ellR[k]);
+        int d = q >= -1048576.f && q <= 1048576.f ? (int)q : 0;
         int cu = co[k] + d;
         int cn;
         if (S.per[k]) cn = ((cu % S.ncell[k]) + S.ncell[k]) % S.ncell[k];
@@ -1076,10 +1077,14 @@ __global__ void k_final(BatchView<R> B) {
   }
 }
 
-// non-finite flag of every scene in the batch tables (one copy to the host per poll)
+// failure flag of every scene in the batch tables (one copy to the host per poll): non-finite
+// velocities, or a relabel that could not be applied (body capacity, union-find retry cap)
 template <class R>
 __global__ void k_gather_failed(Scene<R>* const* sc, int ns, int* out) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) out[s] = sc[s]->status[0];
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
+    const int* st = sc[s]->status;
+    out[s] = st[ST_NONFINITE] != 0 || st[ST_CAPACITY] != 0 || st[ST_HOOK_TIMEOUT] != 0;
+  }
 }
 
 template <class R>
@@ -1217,7 +1222,8 @@ __global__ void k_rigid_vel(BatchView<R> B, int after_relabel) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     int s = find_scene(B.pfx_part, B.nsc, g);
     const Scene<R>& S = *B.sc[s];
-    if (after_relabel && !(S.has_transition && S.status[1] > 0 && S.status[2] == 0)) continue;
+    if (after_relabel && !(S.has_transition && S.status[1] > 0 && S.status[ST_CAPACITY] == 0 &&
+                           S.status[ST_HOOK_TIMEOUT] == 0)) continue;
     int i = g - __ldg(B.pfx_part + s);
     if (S.matR[S.P.mt[i]].kind != KRIGID) continue;
     int k = S.P.body[i], sl = S.P.slot[i];

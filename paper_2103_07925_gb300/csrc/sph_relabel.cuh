@@ -20,7 +20,7 @@ namespace sph {
 
 template <class R>
 __device__ __forceinline__ bool relabel_now(const Scene<R>& S) {
-  return S.has_transition && S.status[1] > 0 && S.status[2] == 0;
+  return S.has_transition && S.status[1] > 0 && S.status[ST_CAPACITY] == 0 && S.status[ST_HOOK_TIMEOUT] == 0;
 }
 
 // neighbours j (r < r_c) of particle i, from its list or a scan of its cells
@@ -116,6 +116,12 @@ __global__ void k_rl_join(BatchView<R> B) {
   }
 }
 
+// retry cap of one union-find hook (CAS contention on a root); compile-time so that a test
+// build can lower it and reach the timeout path without any fault
+#ifndef SPH_RL_HOOK_TRIES
+#define SPH_RL_HOOK_TRIES 1000000
+#endif
+
 __device__ __forceinline__ int uf_find(int* par, int x) {
   int p = ((volatile int*)par)[x];
   while (p != x) {
@@ -138,13 +144,17 @@ __global__ void k_rl_hook(BatchView<R> B) {
     if (S.bucket[i] < 0) continue;
     for_each_neighbor<R, DIM>(S, i, [&](int j, R) {
       if (j < i || S.bucket[j] < 0) return;
-      // hook the larger root under the smaller one; only roots are rewritten
-      for (int it = 0; it < 1000000; it++) {
+      // hook the larger root under the smaller one; only roots are rewritten.  Bounded
+      // retries: a hook that still fails after SPH_RL_HOOK_TRIES attempts sets the scene's
+      // timeout word, and the relabel of this step is not applied (SPH_ERR_TIMEOUT)
+      bool done = false;
+      for (int it = 0; it < SPH_RL_HOOK_TRIES && !done; it++) {
         int a = uf_find(S.bucket, i), b = uf_find(S.bucket, j);
-        if (a == b) break;
+        if (a == b) { done = true; break; }
         int hi = a > b ? a : b, lo = a > b ? b : a;
-        if (atomicCAS(&S.bucket[hi], hi, lo) == hi) break;
+        done = atomicCAS(&S.bucket[hi], hi, lo) == hi;
       }
+      if (!done) S.status[ST_HOOK_TIMEOUT] = 1;
     });
   }
 }
@@ -176,7 +186,7 @@ __global__ void k_rl_number(BatchView<R> B) {
     int C = S.status[8];
     int K = *S.K;
     if (K + C > S.Kcap) {
-      if (threadIdx.x == 0) S.status[2] = 1;  // body capacity exceeded: no relabel this step
+      if (threadIdx.x == 0) S.status[ST_CAPACITY] = 1;  // body capacity exceeded: no relabel this step
       continue;
     }
     for (int a = threadIdx.x; a < C; a += blockDim.x) {

@@ -12,7 +12,9 @@
 // library holds it until the process exits.  Every call shares it, and it keeps the last
 // call's contents (the counters are cleared at the start of each call), so calls that
 // overlap on the GPU -- on different streams, or from different host threads -- race on
-// it and must be serialised by the caller.
+// it and must be serialised by the caller.  Particles of a cell are visited in increasing
+// index order, so every density sum has a fixed order and the result is the same bit for
+// bit on every call.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,7 +33,8 @@ constexpr int kMaxCells = SPH_STATIC_MAX_CELLS;
 
 struct StaticScratch {
   int cell_of[kMaxN];         // cell index of every particle
-  int order[kMaxN];           // particles grouped by cell
+  int order[kMaxN];           // particles grouped by cell, in arrival order within a cell
+  int byidx[kMaxN];           // particles grouped by cell, in increasing index within a cell
   int count[kMaxCells];       // particles per cell
   int start[kMaxCells + 1];   // first slot of every cell
   int cursor[kMaxCells];      // fill position during the scatter
@@ -39,7 +42,10 @@ struct StaticScratch {
 
 static __device__ __align__(256) StaticScratch g_scratch;
 
-// device address of g_scratch on each device (host code may not use the symbol itself)
+// device address of g_scratch on each device (host code may not use the symbol itself),
+// looked up by the first call on that device and kept for the life of the process; a
+// cudaDeviceReset unloads the library's device image, after which the kept address is
+// stale (documented at the declaration)
 std::mutex g_mu;
 StaticScratch* g_addr[64] = {nullptr};
 
@@ -82,7 +88,7 @@ __global__ void ks_clear(StaticScratch* S, int ncells) {
 
 __device__ __forceinline__ int ks_axis_cell(double x, double lo, double ell, int n) {
   double v = floor(__ddiv_rn(__dsub_rn(x, lo), ell));
-  return v < 0.0 ? 0 : (v > (double)(n - 1) ? n - 1 : (int)v);
+  return v >= 0.0 ? (v < (double)(n - 1) ? (int)v : n - 1) : 0;  // NaN -> 0
 }
 
 __global__ void ks_bin(StaticScratch* S, Grid g, const double* pos, int n) {
@@ -136,6 +142,16 @@ __global__ void ks_scatter(StaticScratch* S, int n) {
   }
 }
 
+// the scatter fills a cell in arrival order; each particle's slot in index order is the
+// number of particles of its cell with a smaller index (one thread per particle)
+__global__ void ks_rank(StaticScratch* S, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c = S->cell_of[i], a = S->start[c], e = S->start[c + 1], r = 0;
+    for (int t = a; t < e; t++) r += S->order[t] < i;
+    S->byidx[a + r] = i;
+  }
+}
+
 // rho_i = m_i (W(0) + sum_j W_ij) over the 3^d neighbour cells (quintic spline, r < r_c)
 __global__ void ks_density(const StaticScratch* S, Grid g, const double* pos, const double* mass, int n,
                            double* rho) {
@@ -152,7 +168,7 @@ __global__ void ks_density(const StaticScratch* S, Grid g, const double* pos, co
           if (cc[0] < 0 || cc[0] >= g.nc[0] || cc[1] < 0 || cc[1] >= g.nc[1] || cc[2] < 0 || cc[2] >= g.nc[2]) continue;
           int cl = cc[0] + g.nc[0] * (cc[1] + g.nc[1] * cc[2]);
           for (int s = S->start[cl]; s < S->start[cl + 1]; s++) {
-            int j = S->order[s];
+            int j = S->byidx[s];
             if (j == i) continue;
             double d0 = __dsub_rn(xi[0], pos[3 * j]), d1 = __dsub_rn(xi[1], pos[3 * j + 1]);
             double r2 = __dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1));
@@ -162,7 +178,7 @@ __global__ void ks_density(const StaticScratch* S, Grid g, const double* pos, co
             }
             if (!(r2 < g.rc2)) continue;
             double q = sqrt(r2) / g.h;
-            double t3 = 3.0 - q, t2 = fmax(2.0 - q, 0.0), t1 = fmax(1.0 - q, 0.0);
+            double t3 = fmax(3.0 - q, 0.0), t2 = fmax(2.0 - q, 0.0), t1 = fmax(1.0 - q, 0.0);
             double a2 = t3 * t3, b2 = t2 * t2, c2 = t1 * t1;
             sum += a2 * a2 * t3 - 6.0 * b2 * b2 * t2 + 15.0 * c2 * c2 * t1;
           }
@@ -196,8 +212,14 @@ extern "C" sph_status sph_density_static(int32_t dim, int64_t n, const double* p
     if (k < dim) {
       double L = box_max[k] - box_min[k];
       if (!(L > 0)) { sph::set_error("box_max must exceed box_min"); return SPH_ERR_INVALID; }
-      int c = (int)std::floor(L / rc);
-      g.nc[k] = c < 1 ? 1 : c;
+      // kept as a double until it is known to fit (no overflowing conversion)
+      double c = std::floor(L / rc);
+      if (!(c <= (double)kMaxCells)) {
+        sph::set_error("sph_density_static handles at most %d cells (box needs more than that along axis %d)",
+                       kMaxCells, k);
+        return SPH_ERR_CAPACITY;
+      }
+      g.nc[k] = c < 1.0 ? 1 : (int)c;
       g.lo[k] = box_min[k];
       g.ell[k] = L / g.nc[k];
     } else {
@@ -222,6 +244,7 @@ extern "C" sph_status sph_density_static(int32_t dim, int64_t n, const double* p
   ks_bin<<<gb, 256, 0, s>>>(S, g, pos, ni);
   ks_scan<<<1, 1024, 0, s>>>(S, nci);
   ks_scatter<<<gb, 256, 0, s>>>(S, ni);
+  ks_rank<<<gb, 256, 0, s>>>(S, ni);
   ks_density<<<gb, 256, 0, s>>>(S, g, pos, mass, ni, rho);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -4,6 +4,9 @@ Every step of the method runs in the CUDA kernels of ``libsph.so``; this module 
 converts numpy arrays and scene dictionaries into the C structures, and raises
 ``SphError`` for any non-zero status.  There is no fallback: if the library is
 missing or no CUDA device is present the calls fail.
+
+The environment variable ``SPH_LIBRARY`` names another build of the same library to load
+instead of the in-tree ``libsph.so`` (a build with different compile-time limits).
 """
 from __future__ import annotations
 
@@ -13,7 +16,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsph.so")
+LIB_PATH = os.environ.get("SPH_LIBRARY") or os.path.join(HERE, "libsph.so")
 
 FLUID, RIGID, WALL = 0, 1, 2
 FIELDS = dict(pos=0, vel=1, acc=2, rho=3, pres=4, temp=5, dtemp=6, mat=7, body=8, force=9,
@@ -28,7 +31,8 @@ EXPORTS = ["sph_create_scene", "sph_step", "sph_step_async", "sph_read_fields", 
            "sph_batch_step", "sph_batch_poll", "sph_batch_read_fields", "sph_batch_job_diagnostics",
            "sph_batch_release", "sph_batch_info", "sph_batch_destroy", "sph_profile",
            "sph_profile_stage_name", "sph_density_static", "sph_set_launch", "sph_time_steps",
-           "sph_batch_set_launch", "sph_batch_time_steps", "sph_batch_job_state", "sph_interpolate"]
+           "sph_batch_set_launch", "sph_batch_time_steps", "sph_batch_job_state", "sph_interpolate",
+           "sph_fp32_peak"]
 PROFILE_STAGES = 21
 
 
@@ -88,7 +92,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise SphError(-3, "libsph.so is not built (run __graft_entry__.build())")
+            raise SphError(-3, "%s is not built (run __graft_entry__.build())" % LIB_PATH)
         L = C.CDLL(LIB_PATH)
         vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
         sig = {
@@ -128,6 +132,8 @@ def lib():
         L.sph_density_static.argtypes = [i32, i64, vp, vp, C.c_double, C.c_double, C.POINTER(C.c_double),
                                          C.POINTER(C.c_double), vp, vp]
         L.sph_density_static.restype = C.c_int
+        L.sph_fp32_peak.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(C.c_double)]
+        L.sph_fp32_peak.restype = C.c_int
         L.sph_profile_stage_name.restype = C.c_char_p
         L.sph_profile_stage_name.argtypes = [i32]
         L.sph_last_error.restype = C.c_char_p
@@ -384,7 +390,8 @@ class Batch:
         return [int(x) for x in ids[:nd.value]]
 
     def state(self, job_id):
-        """'advancing', 'finished' or 'failed' (non-finite velocities)."""
+        """'advancing', 'finished' or 'failed' (non-finite velocities, or a relabel that could
+        not be applied: body capacity exhausted or the union-find retry cap reached)."""
         st = C.c_int32()
         _check(lib().sph_batch_job_state(self.h, job_id, C.byref(st)))
         return ("advancing", "finished", "failed")[st.value]
@@ -434,3 +441,11 @@ def density_static(dim, n, pos_ptr, mass_ptr, h, kernel_support, box_min, box_ma
     hi = (C.c_double * 3)(*[float(v) for v in box_max])
     _check(lib().sph_density_static(dim, n, C.c_void_p(pos_ptr), C.c_void_p(mass_ptr), h, kernel_support, lo, hi,
                                     C.c_void_p(rho_ptr), C.c_void_p(stream) if stream else None))
+
+
+def fp32_peak(iters=20000):
+    """Measured FP32 FMA throughput of the current device: (TFLOP/s, SM count, ms)."""
+    tf, ms = C.c_double(), C.c_double()
+    sms = C.c_int32()
+    _check(lib().sph_fp32_peak(iters, C.byref(tf), C.byref(sms), C.byref(ms)))
+    return tf.value, sms.value, ms.value

@@ -65,6 +65,25 @@ def test_static_density_matches_scene_path_on_two_calls_in_a_row():
         ref = _scene_path_rho(sc)
         assert np.all(np.isfinite(got))
         assert _err(got, ref) < 1e-12
+    # particles of a cell are visited in index order: a repeated call gives the same bits
+    assert np.array_equal(_static_rho(first), _static_rho(first))
+
+
+def test_static_density_particles_on_the_box_edge():
+    """2D particles sitting exactly on box_max fall into the last cell (clamped), and their
+    density still equals the scene path's."""
+    sc = _fluid_block(2, 40, 0.025, seed=13)
+    p = sc["params"]
+    L = 40 * 0.025
+    p["box_min"] = [0.0, 0.0, 0.0]
+    p["box_max"] = [L, L, 0.0]
+    pos = sc["particles"]["pos"]
+    pos[:, :2] = np.clip(pos[:, :2], 0.0, L)
+    pos[:40, 0] = L  # a column exactly on the upper x edge
+    pos[40:80, 1] = L
+    got = _static_rho(sc)
+    ref = _scene_path_rho(sc)
+    assert _err(got, ref) < 1e-12
 
 
 def test_static_density_rejects_oversized_input():
@@ -77,3 +96,21 @@ def test_static_density_rejects_oversized_input():
     with pytest.raises(SphError) as e:
         density_static(3, n, pos.data_ptr(), mass.data_ptr(), 0.1, 3.0, [0, 0, 0], [1, 1, 1], rho.data_ptr())
     assert e.value.status == -6
+
+
+def test_static_density_rejects_a_box_with_too_many_cells():
+    """n within the limit but a box that needs more than 2^18 cells of edge >= r_c: the call
+    returns SPH_ERR_CAPACITY before launching anything, and the output is untouched."""
+    import torch
+    from paper_2103_07925_gb300.sph import SphError, density_static
+    n = 1000
+    pos = torch.rand((n, 3), dtype=torch.float64, device="cuda")
+    mass = torch.ones(n, dtype=torch.float64, device="cuda")
+    rho = torch.full((n,), 7.0, dtype=torch.float64, device="cuda")
+    h = 0.01  # r_c = 0.03: 66 cells along each edge of 2, 66^3 > 2^18
+    for box_max in ([2.0, 2.0, 2.0], [1e12, 1.0, 1.0]):
+        with pytest.raises(SphError) as e:
+            density_static(3, n, pos.data_ptr(), mass.data_ptr(), h, 3.0, [0, 0, 0], box_max, rho.data_ptr())
+        assert e.value.status == -6
+    torch.cuda.synchronize()
+    assert bool(torch.all(rho == 7.0))
