@@ -270,7 +270,8 @@ __global__ void k_diag_fin(Scene<R>* const* sc, const double* part, int nblk, do
 // ------------------------------------------------------------------ neighbour-set export
 template <class R, int DIM>
 struct NbPol {
-  R *sx, *sy, *sz, *sxs;
+  R *sx, *sy, *sz;
+  float4* s4;
   int* sox;
   float *fx, *fy, *fz;
   float tf[3];
@@ -297,14 +298,15 @@ struct NbPol {
 template <class R, int DIM>
 __global__ void __launch_bounds__(128) k_neighbors(Scene<R>* const* sc, int ngroups, int64_t* counts,
                                                    const int64_t* offs, int32_t* list) {
-  __shared__ R sm[4][4][32];
+  __shared__ R sm[4][3][32];
   __shared__ float smf[4][3][32];
+  __shared__ float4 sm4[sizeof(R) == 4 ? 4 : 1][32];
   __shared__ int smo[4][32], smx[4][32];
   const Scene<R>& S = **sc;
   int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   NbPol<R, DIM> pol;
   pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2]; pol.so = smo[wib];
-  pol.sxs = sm[wib][3]; pol.sox = smx[wib];
+  pol.s4 = sm4[sizeof(R) == 4 ? wib : 0]; pol.sox = smx[wib];
   pol.fx = smf[wib][0]; pol.fy = smf[wib][1]; pol.fz = smf[wib][2];
   pol.list = list;
   pol.cmask = (1u << NCLS) - 1u;  // every neighbour, whatever its kind

@@ -56,7 +56,16 @@ struct PBank {  // particle fields (one bank)
 // hold them across the list walk).  Nothing in it changes after the scene is created.
 struct SweepK {
   const float4 *pa, *pb, *pc, *pd;  // packed neighbour records (pd: TVF / concentration)
-  const int* nbl;                   // neighbour lists, entry k of particle i at nbl[k * n + i]
+  const int* nbl;                   // neighbour lists, entry k of particle i at nbl[nb_at(n, i, k)]
+  // the in-range part of each fluid or rigid particle's list (r < r_c at this evaluation, in
+  // list order), written by the density / extrapolation sweep: entries 4q .. 4q + 3 of
+  // particle i in nbq[q * n + i]; nbqc[i] entries, or -1 when they did not fit (cq)
+  const int4* nbq;
+  const int* nbqc;
+  int cq;
+  // cell offset of a list entry's code, -(ox ell_x, oy ell_y, oz ell_z): added to p_i - p_j
+  // (27 entries, code = (ox + 1) + 3 (oy + 1) + 9 (oz + 1))
+  const float4* shift;
   int n;
   float ell[3];                     // cell edges (positions are relative to the cell origin)
   float rc2, sig_dw, inv_h;         // r_c^2, dW/dr = sig_dw w'(r / h)
@@ -109,8 +118,12 @@ struct Scene {
   float4 *pa, *pb, *pc;
   SweepK k;            // FP32 scenes: the per-entry constants of the pair sweeps
   float4* pd;          // (u~ - u, C): transport-velocity formulation and concentration
-  int* nbl;            // neighbour lists: entry k of particle i at nbl[k * n + i] = j << 5 | cell code
+  int* nbl;            // neighbour lists: entry k of particle i at nbl[nb_at(n, i, k)] = j << 5 | cell code
   int* nbc;            // neighbour count of each particle (may exceed maxnb: then cells are scanned)
+  int4* nbq;           // FP32 scenes: in-range entries of this evaluation (see SweepK)
+  int* nbqc;
+  int cq;              // capacity of the in-range lists (entries, a multiple of 4)
+  float4* shift;       // FP32 scenes: cell offsets of the 27 entry codes (see SweepK)
   R *xr, *yr, *zr;     // positions at the last list rebuild (same frame as the bank)
   unsigned long long* disp;  // bits of the largest squared displacement since the rebuild
   int maxnb;           // list capacity per particle
@@ -179,6 +192,13 @@ __device__ __forceinline__ int clamp_cell(double v, int n) {
 
 // status words of a scene that stop its phase relabelling (checked by the host after a step)
 enum { ST_NONFINITE = 0, ST_CAPACITY = 2, ST_HOOK_TIMEOUT = 11 };
+
+// neighbour lists in chunks of four entries: entries 4q .. 4q + 3 of particle i form the
+// int4 at index q n + i (one 16-byte store by the search, one 16-byte load by a sweep);
+// the int offset of entry k of particle i
+__device__ __forceinline__ size_t nb_at(size_t n, int i, int k) {
+  return 4 * ((size_t)(k >> 2) * n + (size_t)i) + (size_t)(k & 3);
+}
 
 __device__ __forceinline__ int find_scene(const int* __restrict__ pfx, int nsc, int g) {
   int lo = 0, hi = nsc - 1;

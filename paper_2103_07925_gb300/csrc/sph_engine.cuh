@@ -51,6 +51,15 @@ struct HostScene {
 
 // geometry and constants derived from the parameters exactly as the checker does
 // (cell count floor(L / r_c), edge L / count)
+// ------------------------------------------------------------------------------ helpers
+// list capacity: 1.3 x the lattice sites inside the list radius, rounded up to 32
+inline int list_capacity(int dim, double radius_in_dx) {
+  double ball = dim == 3 ? 4.0 / 3.0 * M_PI * radius_in_dx * radius_in_dx * radius_in_dx
+                         : M_PI * radius_in_dx * radius_in_dx;
+  int c = (int)std::ceil(1.3 * ball / 32.0) * 32;
+  return c < 32 ? 32 : c;
+}
+
 template <class R>
 inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
   if (p->dim != 2 && p->dim != 3) { set_error("dim must be 2 or 3"); return SPH_ERR_INVALID; }
@@ -388,8 +397,10 @@ class Engine {
   }
 
   static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans, bool tvf) {
+    // FP32: the packed records and the in-range lists of each evaluation (capacity at r_c)
     size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 9 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
-                 (DIM == 3 ? 192 : 64) * sizeof(int) + (sizeof(R) == 4 ? 3 * sizeof(float4) : 0);
+                 (DIM == 3 ? 192 : 64) * sizeof(int) +
+                 (sizeof(R) == 4 ? 3 * sizeof(float4) + (size_t)(list_capacity(DIM, 3.0) + 1) * sizeof(int) : 0);
     size_t cells = (size_t)(NCLS * ncells + 1) * 2 * sizeof(int) + (size_t)ncells * 2 * sizeof(int) +
                    (size_t)(NCLS * ncells / 1024 + 2) * sizeof(int);
     size_t bodies = (size_t)kcap * (69 * sizeof(double) + 3 * sizeof(int));
@@ -460,14 +471,6 @@ class Engine {
 
 namespace sph {
 
-// ------------------------------------------------------------------------------ helpers
-// list capacity: 1.3 x the lattice sites inside the list radius, rounded up to 32
-inline int list_capacity(int dim, double radius_in_dx) {
-  double ball = dim == 3 ? 4.0 / 3.0 * M_PI * radius_in_dx * radius_in_dx * radius_in_dx
-                         : M_PI * radius_in_dx * radius_in_dx;
-  int c = (int)std::ceil(1.3 * ball / 32.0) * 32;
-  return c < 32 ? 32 : c;
-}
 
 inline int grid_for(int64_t items, int per_block, int max_grid) {
   int64_t b = (items + per_block - 1) / per_block;
@@ -602,6 +605,20 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   S.maxnb = list_capacity(DIM, (S.rc + S.skin) / S.dx);
   SPH_TRY(A(&S.nbl, (size_t)S.maxnb * n));
   SPH_TRY(A(&S.nbc, (size_t)n));
+  if (sizeof(R) == 4) {  // in-range lists of each evaluation, and the cell offsets of the codes
+    S.cq = list_capacity(DIM, S.rc / S.dx);
+    SPH_TRY(A(&S.nbq, (size_t)(S.cq / 4) * n));
+    SPH_TRY(A(&S.nbqc, (size_t)n));
+    SPH_TRY(A(&S.shift, 32));
+    float4 sh[32];
+    for (int c = 0; c < 32; c++) {
+      int ox = c % 3 - 1, oy = (c / 3) % 3 - 1, oz = c / 9 - 1;
+      // the same products the sweeps formed from the code: exact (0 or +-ell)
+      sh[c] = make_float4(-((float)ox * (float)S.ellR[0]), -((float)oy * (float)S.ellR[1]),
+                          DIM == 3 ? -((float)oz * (float)S.ellR[2]) : 0.f, 0.f);
+    }
+    SPH_CU(cudaMemcpyAsync(S.shift, sh, sizeof(sh), cudaMemcpyHostToDevice, stream));
+  }
   SPH_TRY(A(&S.xr, (size_t)n));
   SPH_TRY(A(&S.yr, (size_t)n));
   SPH_TRY(A(&S.zr, (size_t)n));
@@ -725,6 +742,10 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     if (sizeof(R) == 4) {
       S.k.pa = S.pa; S.k.pb = S.pb; S.k.pc = S.pc; S.k.pd = S.pd;
       S.k.nbl = S.nbl;
+      S.k.nbq = S.nbq;
+      S.k.nbqc = S.nbqc;
+      S.k.cq = S.cq;
+      S.k.shift = S.shift;
       S.k.n = n;
       for (int d = 0; d < 3; d++) S.k.ell[d] = (float)S.ellR[d];
       S.k.rc2 = (float)S.rc2R; S.k.sig_dw = (float)S.sig_dw; S.k.inv_h = (float)S.inv_h;

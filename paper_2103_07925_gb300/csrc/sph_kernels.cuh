@@ -863,7 +863,7 @@ __device__ __forceinline__ void for_each_run(const Scene<R>& S, int cx0, int ncx
 
 // generic traversal.  Pol provides: stage(S, j, lane), active, tp[3], idx, cmask (the
 // candidate kinds visited, the same for the whole warp), shared arrays sox (column offset
-// of each staged candidate) and sxs (FP32: staged x plus that offset), pair(S, k, j, dx, dy,
+// of each staged candidate) and s4 (FP32: staged x plus that offset, y, z), pair(S, k, j, dx, dy,
 // dz, r2) with cox/cdy/cdz set to the candidate's cell offset, kExact (pair() sees exactly
 // the pairs with r^2 < rc2, with their offset; otherwise every pre-test hit, a superset,
 // without it), and for FP64 scenes FP32 copies fx/fy/fz of the staged positions and tf of
@@ -894,9 +894,10 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
           }
         }
         pol.sox[lane] = ox;
-        if constexpr (sizeof(R) == 4) pol.sxs[lane] = pol.sx[lane] + (R)ox * S.ellR[0];
+        if constexpr (sizeof(R) == 4)
+          pol.s4[lane] = make_float4(pol.sx[lane] + (R)ox * S.ellR[0], pol.sy[lane], pol.sz[lane], 0.f);
       } else if (sizeof(R) == 4) {
-        pol.sxs[lane] = 1e30f;  // padding: fails every test
+        pol.s4[lane] = make_float4(1e30f, 0.f, 0.f, 0.f);  // padding: fails every test
       } else {
         pol.fx[lane] = 1e30f;
       }
@@ -926,9 +927,10 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
           for (int k0 = 0; k0 < cnt; k0 += 4) {
 #pragma unroll
             for (int k = k0; k < k0 + 4; k++) {
-              R dx = pol.tp[0] - pol.sxs[k];
-              R dy2 = qy - pol.sy[k];
-              R dz2 = DIM == 3 ? qz - pol.sz[k] : R(0);
+              float4 c = pol.s4[k];  // one broadcast load per candidate
+              R dx = pol.tp[0] - c.x;
+              R dy2 = qy - c.y;
+              R dz2 = DIM == 3 ? qz - c.z : R(0);
               R r2 = dist2<R, DIM>(dx, dy2, dz2);
               if (r2 < rc2m) mask |= 1u << k;
             }

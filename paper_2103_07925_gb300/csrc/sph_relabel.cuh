@@ -36,7 +36,7 @@ __device__ __forceinline__ void for_each_neighbor(const Scene<R>& S, int i, F&& 
   int cnt = S.nbc[i];
   if (cnt <= S.maxnb) {
     for (int k = 0; k < cnt; k++) {
-      int e = S.nbl[(size_t)k * S.n + i];
+      int e = S.nbl[nb_at(S.n, i, k)];
       visit(e >> 5, e & 31);
     }
   } else {

@@ -56,7 +56,8 @@ __device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p,
 // ---------------------------------------------------------------- neighbour search
 template <class R, int DIM>
 struct SearchPol {
-  R *sx, *sy, *sz, *sxs;  // staged candidates (see traverse)
+  R *sx, *sy, *sz;     // staged candidates (see traverse)
+  float4* s4;
   int* sox;
   float *fx, *fy, *fz;    // FP32 copies of the staged positions (FP64 scenes)
   float tf[3];
@@ -65,29 +66,43 @@ struct SearchPol {
   bool active;
   int idx, tx, n, maxnb, cnt;
   int cox, cdy, cdz;
-  int* list;           // where the target's next list entry goes (list + cnt * n)
+  int4* list;          // the target's list chunks (chunk q at list[q * n])
+  int4 buf;            // the chunk being filled (entries cnt & ~3 .. cnt - 1)
   R tp[3];
   // a list may hold a few pairs just beyond its radius (the pre-test's margin): every sweep
   // decides r < r_c itself, so the exact per-pair test is skipped here
   static constexpr bool kExact = false;
   __device__ void stage(const Scene<R>& S, int j, int lane) {
-    sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
-    if (sizeof(R) == 8) { fx[lane] = (float)sx[lane]; fy[lane] = (float)sy[lane]; fz[lane] = (float)sz[lane]; }
+    if constexpr (sizeof(R) == 4) {  // the packed position record: one 16-byte load
+      float4 a = S.pa[j];
+      sx[lane] = a.x; sy[lane] = a.y; sz[lane] = a.z;
+    } else {
+      sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
+      fx[lane] = (float)sx[lane]; fy[lane] = (float)sy[lane]; fz[lane] = (float)sz[lane];
+    }
   }
+  // entries collect in a register chunk that is stored whole (16 bytes); entries past the
+  // capacity are counted, not stored (the sweeps then scan the cells of that target)
   __device__ void pair(const Scene<R>&, int, int j, R, R, R, R) {
     int code = (cox - tx + 1) + 3 * (cdy + 1) + 9 * (cdz + 1);
-    if (cnt < maxnb) {
-      *list = (j << 5) | code;
-      list += n;
-    }
+    int e = (j << 5) | code;
+    int u = cnt & 3;
+    if (u == 0) buf.x = e;
+    else if (u == 1) buf.y = e;
+    else if (u == 2) buf.z = e;
+    else buf.w = e;
     cnt++;
+    if ((cnt & 3) == 0 && cnt <= maxnb) list[(size_t)((cnt >> 2) - 1) * n] = buf;
+  }
+  __device__ void flush() {
+    if ((cnt & 3) != 0 && cnt <= maxnb) list[(size_t)(cnt >> 2) * n] = buf;
   }
 };
 
 // resident blocks of 128 threads per SM the search is compiled for (register budget; six
 // measured fastest for FP32, against eight and ten)
 #ifndef SPH_SEARCH_MIN_BLOCKS
-#define SPH_SEARCH_MIN_BLOCKS 6
+#define SPH_SEARCH_MIN_BLOCKS 5
 #endif
 #ifndef SPH_SEARCH_MIN_BLOCKS_64
 #define SPH_SEARCH_MIN_BLOCKS_64 6
@@ -96,12 +111,14 @@ struct SearchPol {
 template <class R, int DIM>
 __global__ void __launch_bounds__(128, sizeof(R) == 8 ? SPH_SEARCH_MIN_BLOCKS_64 : SPH_SEARCH_MIN_BLOCKS)
     k_search(BatchView<R> B) {
-  __shared__ R sm[4][4][32];
+  __shared__ R sm[4][3][32];
   __shared__ float smf[sizeof(R) == 8 ? 4 : 1][3][32];
+  __shared__ float4 sm4[sizeof(R) == 4 ? 4 : 1][32];
   __shared__ int smo[4][32];
   int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   SearchPol<R, DIM> pol;
-  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2]; pol.sxs = sm[wib][3];
+  pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
+  pol.s4 = sm4[sizeof(R) == 4 ? wib : 0];
   pol.sox = smo[wib];
   int wf = sizeof(R) == 8 ? wib : 0;
   pol.fx = smf[wf][0]; pol.fy = smf[wf][1]; pol.fz = smf[wf][2];
@@ -133,9 +150,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 8 ? SPH_SEARCH_MIN_BLOCKS_64
       }
       pol.tf[0] = (float)pol.tp[0]; pol.tf[1] = (float)pol.tp[1]; pol.tf[2] = (float)pol.tp[2];
       pol.cnt = 0;
-      pol.list = S.nbl + (valid ? i : 0);
+      pol.list = (int4*)S.nbl + (valid ? i : 0);
       traverse<R, DIM>(S, G, pol, lane, S.rl2R, S.rl2f);
-      if (valid) S.nbc[i] = pol.cnt;
+      if (valid) {
+        pol.flush();
+        S.nbc[i] = pol.cnt;
+      }
     }
   }
 }
@@ -163,14 +183,37 @@ __device__ __forceinline__ void list_delta(const Scene<R>& S, const R* ti, int j
   }
 }
 
-// the same offset from a packed FP32 neighbour record
+// the same offset from a packed FP32 neighbour record: the cell offset of the entry's code
+// comes from the scene's table of the 27 products -(o ell) (each exact), so the sum is the
+// one the code would give
 template <int DIM>
 __device__ __forceinline__ void pack_delta(const SweepK& K, const float* ti, float4 a, int code, float* d) {
-  int ox = code % 3 - 1, oy = (code / 3) % 3 - 1, oz = code / 9 - 1;
-  d[0] = (ti[0] - a.x) - (float)ox * K.ell[0];
-  d[1] = (ti[1] - a.y) - (float)oy * K.ell[1];
-  d[2] = DIM == 3 ? (ti[2] - a.z) - (float)oz * K.ell[2] : 0.f;
+  float4 sh = __ldg(K.shift + code);
+  d[0] = (ti[0] - a.x) + sh.x;
+  d[1] = (ti[1] - a.y) + sh.y;
+  d[2] = DIM == 3 ? (ti[2] - a.z) + sh.z : 0.f;
 }
+
+// writer of particle i's in-range list (int4 chunks, see SweepK): entries collect in a
+// register chunk that is stored whole; more than cq entries (the capacity) mark the list
+// as not kept (-1), and the force sweep then walks the full list itself
+struct InRange {
+  int4 buf;
+  int m = 0;
+  __device__ __forceinline__ void put(int4* nbq, size_t n, int i, int cq, int e) {
+    int u = m & 3;
+    if (u == 0) buf.x = e;
+    else if (u == 1) buf.y = e;
+    else if (u == 2) buf.z = e;
+    else buf.w = e;
+    m++;
+    if ((m & 3) == 0 && m <= cq) nbq[(size_t)((m >> 2) - 1) * n + i] = buf;
+  }
+  __device__ __forceinline__ int finish(int4* nbq, size_t n, int i, int cq) {
+    if ((m & 3) != 0 && m <= cq) nbq[(size_t)(m >> 2) * n + i] = buf;
+    return m <= cq ? m : -1;
+  }
+};
 template <int DIM>
 __device__ __forceinline__ void pack_delta(const Scene<float>& S, const float* ti, float4 a, int code, float* d) {
   pack_delta<DIM>(S.k, ti, a, code, d);
@@ -230,40 +273,50 @@ __global__ void __launch_bounds__(256, SPH_DENSITY_MIN_BLOCKS) k_density(BatchVi
       };
       int cnt = S.nbc[i];
       if (cnt <= S.maxnb) {
-        const int* L = S.nbl + i;
         int k = 0;
         if constexpr (sizeof(R) == 4) {
-          // entries four at a time: the four position gathers are in flight together (a
-          // latency-bound walk), the next four list entries while they are summed; the sum
-          // keeps the list order
+          // one list chunk (four entries) at a time: the four position gathers are in flight
+          // together (a latency-bound walk), the next chunk while they are summed; the sum
+          // keeps the list order.  The entries inside the support are copied, in list order,
+          // into the in-range list the force sweep of this evaluation walks.
           size_t n = S.n;
           const float4* pa = S.pa;
-          int e[4], en[4];
-#pragma unroll
-          for (int q = 0; q < 4; q++) e[q] = q < cnt ? __ldg(L + (size_t)q * n) : 0;
-          for (; k + 4 <= cnt; k += 4) {
-#pragma unroll
-            for (int q = 0; q < 4; q++) en[q] = k + 4 + q < cnt ? __ldg(L + (size_t)(k + 4 + q) * n) : 0;
+          const int4* L4 = (const int4*)S.nbl + i;
+          InRange ir;
+          const int cq = S.cq;
+          int4 c = cnt > 0 ? __ldg(L4) : make_int4(0, 0, 0, 0);
+          for (; k < cnt; k += 4) {
+            int4 cn = k + 4 < cnt ? __ldg(L4 + (size_t)((k >> 2) + 1) * n) : make_int4(0, 0, 0, 0);
+            int e[4] = {c.x, c.y, c.z, c.w};
+            bool ok[4];
             float4 a[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) a[q] = pa[e[q] >> 5];
+            for (int q = 0; q < 4; q++) {
+              ok[q] = k + q < cnt;  // the last chunk may be partial
+              a[q] = pa[ok[q] ? e[q] >> 5 : i];
+            }
 #pragma unroll
             for (int q = 0; q < 4; q++) {
+              if (!ok[q]) continue;
               R d[3];
               pack_delta<DIM>(S, ti, a[q], e[q] & 31, d);
               R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
-              if (r2 < S.rc2R) acc += quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
+              if (r2 < S.rc2R) {
+                acc += quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
+                ir.put(S.nbq, n, i, cq, e[q]);
+              }
             }
-#pragma unroll
-            for (int q = 0; q < 4; q++) e[q] = en[q];
+            c = cn;
           }
+          S.nbqc[i] = ir.finish(S.nbq, n, i, cq);
         }
         for (; k < cnt; k++) {
-          int e = __ldg(L + (size_t)k * S.n);
+          int e = __ldg(S.nbl + nb_at(S.n, i, k));
           visit(e >> 5, e & 31);
         }
       } else {
         scan_cells<R, DIM>(S, i, visit);
+        if constexpr (sizeof(R) == 4) S.nbqc[i] = -1;
       }
       rho = S.P.m[i] * (S.w0 + S.sig_w * acc);
       S.P.rho[i] = rho;
@@ -327,53 +380,63 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
     };
     int cnt = S.nbc[i];
     if (cnt <= S.maxnb) {
-      const int* L = S.nbl + i;
       int k = 0;
       if constexpr (sizeof(R) == 4) {
-        // entries two at a time, both records of both in flight together (a latency-bound
-        // walk), the next two list entries while they are summed; the sums keep the list
-        // order
+        // one list chunk (four entries) at a time, two entries with both their records in
+        // flight together (a latency-bound walk); the sums keep the list order.  A rigid
+        // target also copies every entry inside the support (all kinds), in list order, into
+        // the in-range list of the force sweep.
         size_t n = S.n;
-        int e[2], en[2];
+        const int4* L4 = (const int4*)S.nbl + i;
+        InRange ir;
+        const int cq = S.cq;
+        int4 c = cnt > 0 ? __ldg(L4) : make_int4(0, 0, 0, 0);
+        for (; k < cnt; k += 4) {
+          int4 cn = k + 4 < cnt ? __ldg(L4 + (size_t)((k >> 2) + 1) * n) : make_int4(0, 0, 0, 0);
+          int ec[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-        for (int q = 0; q < 2; q++) e[q] = q < cnt ? __ldg(L + (size_t)q * n) : 0;
-        for (; k + 2 <= cnt; k += 2) {
-#pragma unroll
-          for (int q = 0; q < 2; q++) en[q] = k + 2 + q < cnt ? __ldg(L + (size_t)(k + 2 + q) * n) : 0;
+          for (int h = 0; h < 4; h += 2) {
+          int e[2] = {ec[h], ec[h + 1]};
           float4 a[2], b[2];
-          bool fl[2];
+          bool fl[2], ok[2];
 #pragma unroll
           for (int q = 0; q < 2; q++) {
-            int j = e[q] >> 5;
+            ok[q] = k + h + q < cnt;  // the last chunk may be partial
+            int j = ok[q] ? e[q] >> 5 : i;
             a[q] = S.pa[j];  // loaded whatever the kind: both loads of both entries in flight
             b[q] = S.pb[j];
             fl[q] = wall || j < nf;
           }
 #pragma unroll
           for (int q = 0; q < 2; q++) {
-            if (!fl[q]) continue;
+            if (!ok[q]) continue;
             R d[3];
             pack_delta<DIM>(S, ti, a[q], e[q] & 31, d);
             R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
             if (r2 < S.rc2R) {
-              R W = quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
-              S0 += W;
-              P0 += b[q].w * W;
-              R rw = a[q].w * W;
-              Rv[0] += rw * d[0]; Rv[1] += rw * d[1]; Rv[2] += rw * d[2];
-              U[0] += b[q].x * W; U[1] += b[q].y * W; U[2] += b[q].z * W;
+              if (!wall) ir.put(S.nbq, n, i, cq, e[q]);
+              if (fl[q]) {
+                R W = quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
+                S0 += W;
+                P0 += b[q].w * W;
+                R rw = a[q].w * W;
+                Rv[0] += rw * d[0]; Rv[1] += rw * d[1]; Rv[2] += rw * d[2];
+                U[0] += b[q].x * W; U[1] += b[q].y * W; U[2] += b[q].z * W;
+              }
             }
           }
-#pragma unroll
-          for (int q = 0; q < 2; q++) e[q] = en[q];
+          }
+          c = cn;
         }
+        if (!wall) S.nbqc[i] = ir.finish(S.nbq, n, i, cq);
       }
       for (; k < cnt; k++) {
-        int e = __ldg(L + (size_t)k * S.n);
+        int e = __ldg(S.nbl + nb_at(S.n, i, k));
         visit(e >> 5, e & 31);
       }
     } else {
       scan_cells<R, DIM>(S, i, visit);
+      if constexpr (sizeof(R) == 4) S.nbqc[i] = -1;
     }
     R uw[3] = {S.P.vx[i], S.P.vy[i], S.P.vz[i]};  // prescribed wall / rigid velocity
     if (S0 > R(0)) {
@@ -654,15 +717,41 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
         }
       };
       int cnt = S.nbc[i];
-      if (cnt <= S.maxnb) {
+      int cin = -1;
+      if constexpr (sizeof(R) == 4) cin = __ldg(K.nbqc + i);
+      if (cin >= 0) {
+        if constexpr (sizeof(R) == 4) {
+          // the in-range list of this evaluation (every entry inside the support, in list
+          // order): no distance test, every lane has a pair at every entry but the last few;
+          // four entries per load, the next four loaded while these are evaluated
+          const int4* Q = K.nbq + i;
+          int4 cur = cin > 0 ? __ldg(Q) : make_int4(0, 0, 0, 0);
+          for (int m = 0; m < cin; m += 4) {
+            int4 nxt = m + 4 < cin ? __ldg(Q + (size_t)((m >> 2) + 1) * K.n) : make_int4(0, 0, 0, 0);
+            int ee[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+              if (m + u < cin) {
+                int e = ee[u], j = e >> 5;
+                float4 a = K.pa[j], b = K.pb[j], c = K.pc[j];
+                float d[3];
+                pack_delta<DIM>(K, ti, a, e & 31, d);
+                float r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+                force_pair_packed<DIM, TVF>(S, K, t, j, d, r2, a, b, c, acc, heat);
+              }
+            }
+            cur = nxt;
+          }
+          npairs += (unsigned long long)cin;
+        }
+      } else if (cnt <= S.maxnb) {
         int k = 0;
         if constexpr (sizeof(R) == 4) {
           // software pipeline: the next list entry is loaded while this pair is evaluated,
           // and the three records of a neighbour are loaded together (one latency per entry)
-          const int* L = K.nbl + i;
-          int e = k < cnt ? __ldg(L + (size_t)k * K.n) : 0;
+          int e = k < cnt ? __ldg(K.nbl + nb_at(K.n, i, k)) : 0;
           for (; k < cnt; k++) {
-            int en = k + 1 < cnt ? __ldg(L + (size_t)(k + 1) * K.n) : 0;
+            int en = k + 1 < cnt ? __ldg(K.nbl + nb_at(K.n, i, k + 1)) : 0;
             int j = e >> 5;
 #if SPH_FORCE_SPECULATE
             float4 a = K.pa[j], b = K.pb[j], c = K.pc[j];
@@ -682,9 +771,8 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
             e = en;
           }
         }
-        const int* L = S.nbl + i;
         for (; k < cnt; k++) {
-          int e = __ldg(L + (size_t)k * S.n);
+          int e = __ldg(S.nbl + nb_at(S.n, i, k));
           visit(e >> 5, e & 31);
         }
       } else {
