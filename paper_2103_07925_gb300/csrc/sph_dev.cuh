@@ -55,7 +55,8 @@ struct PBank {  // particle fields (one bank)
 // (kernel parameters are read from the constant bank: no cache traffic and no registers to
 // hold them across the list walk).  Nothing in it changes after the scene is created.
 struct SweepK {
-  const float4 *pa, *pb, *pc, *pd;  // packed neighbour records (pd: TVF / concentration)
+  const float4 *pa, *pb, *pd;       // packed neighbour records (pd: TVF / concentration)
+  const float2* pv;                 // (V, material | kind << 16) of every particle
   const int* nbl;                   // neighbour lists, entry k of particle i at nbl[nb_at(n, i, k)]
   // the in-range part of each fluid or rigid particle's list (r < r_c at this evaluation, in
   // list order), written by the density / extrapolation sweep: entries 4q .. 4q + 3 of
@@ -112,10 +113,12 @@ struct Scene {
   R *vex, *vey, *vez;  // extrapolated velocity of wall and rigid particles
   R* vol;              // particle volume m / rho of the current evaluation
   // FP32 scenes: what a pair sweep gathers from a neighbour, packed per particle after the
-  // density summation (three 16-byte loads per neighbour instead of twelve scalar ones):
-  // pa = (x, y, z, rho), pb = (u or extrapolated v_w, p or p_w), pc = (T, V, material |
-  // kind << 16, body)
-  float4 *pa, *pb, *pc;
+  // density summation (two 16-byte and one 8-byte load per neighbour instead of eleven
+  // scalar ones): pa = (x, y, z, rho), pb = (u or extrapolated v_w, p or p_w),
+  // pv = (V, material | kind << 16); the force sweep reads T (heat) and the body id (rigid
+  // targets) from the particle arrays where it needs them
+  float4 *pa, *pb;
+  float2* pv;
   SweepK k;            // FP32 scenes: the per-entry constants of the pair sweeps
   float4* pd;          // (u~ - u, C): transport-velocity formulation and concentration
   int* nbl;            // neighbour lists: entry k of particle i at nbl[nb_at(n, i, k)] = j << 5 | cell code

@@ -400,7 +400,7 @@ class Engine {
     // FP32: the packed records and the in-range lists of each evaluation (capacity at r_c)
     size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 9 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
                  (DIM == 3 ? 192 : 64) * sizeof(int) +
-                 (sizeof(R) == 4 ? 3 * sizeof(float4) + (size_t)(list_capacity(DIM, 3.0) + 1) * sizeof(int) : 0);
+                 (sizeof(R) == 4 ? 2 * sizeof(float4) + sizeof(float2) + (size_t)(list_capacity(DIM, 3.0) + 1) * sizeof(int) : 0);
     size_t cells = (size_t)(NCLS * ncells + 1) * 2 * sizeof(int) + (size_t)ncells * 2 * sizeof(int) +
                    (size_t)(NCLS * ncells / 1024 + 2) * sizeof(int);
     size_t bodies = (size_t)kcap * (69 * sizeof(double) + 3 * sizeof(int));
@@ -596,7 +596,10 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   R** rx[] = {&S.prs, &S.dT, &S.vex, &S.vey, &S.vez, &S.vol};
   for (R** f : rx) SPH_TRY(A(f, (size_t)n));
   if (sizeof(R) == 4)
-    for (float4** f : {&S.pa, &S.pb, &S.pc}) SPH_TRY(A(f, (size_t)n));
+  {
+    for (float4** f : {&S.pa, &S.pb}) SPH_TRY(A(f, (size_t)n));
+    SPH_TRY(A(&S.pv, (size_t)n));
+  }
   if (sizeof(R) == 4 && (S.tvf || S.any_conc)) SPH_TRY(A(&S.pd, (size_t)n));
   if (S.any_conc) {
     SPH_TRY(A(&S.dC, (size_t)n));
@@ -740,7 +743,7 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     cudaMemcpyAsync(dslot, slot.data(), 4 * nd, cudaMemcpyHostToDevice, stream);
     S.k = SweepK{};
     if (sizeof(R) == 4) {
-      S.k.pa = S.pa; S.k.pb = S.pb; S.k.pc = S.pc; S.k.pd = S.pd;
+      S.k.pa = S.pa; S.k.pb = S.pb; S.k.pv = S.pv; S.k.pd = S.pd;
       S.k.nbl = S.nbl;
       S.k.nbq = S.nbq;
       S.k.nbqc = S.nbqc;

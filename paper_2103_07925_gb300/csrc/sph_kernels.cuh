@@ -878,6 +878,11 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
     int cs = max(cs0, 0), ce = min(ce0, S.n);
     pol.cdy = dy;
     pol.cdz = dz;
+    // interior cell bounds of a run of up to five columns, loaded once for the run
+    int bnd[4];
+#pragma unroll
+    for (int m = 0; m < 4; m++)
+      bnd[m] = (oxf == kOxKey && m + 1 < ncols && ncols <= 5) ? __ldg(S.cstart + kfirst + m + 1) : 0x7fffffff;
     for (int cb = cs; cb < ce; cb += 32) {
       int cnt = min(32, ce - cb);
       __syncwarp();
@@ -888,7 +893,8 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
         if (oxf == kOxKey) {
           if (ncols <= 5) {  // the column from the cell bounds of the run
             ox = ox0;
-            for (int m = 1; m < ncols; m++) ox += j >= __ldg(S.cstart + kfirst + m) ? 1 : 0;
+#pragma unroll
+            for (int m = 0; m < 4; m++) ox += j >= bnd[m] ? 1 : 0;
           } else {  // row-major keys: the key modulo ncell[0] (ncells is a multiple of it)
             ox = S.key[j] % S.ncell[0] - G.cx0;
           }

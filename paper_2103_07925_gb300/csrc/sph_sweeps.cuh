@@ -46,7 +46,7 @@ __device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p,
     else
       S.pa[i].w = rho;
     S.pb[i] = make_float4(S.P.vx[i], S.P.vy[i], S.P.vz[i], p);
-    S.pc[i] = make_float4(S.P.T[i], vol, __int_as_float(mt | (S.matR[mt].kind << 16)), __int_as_float(S.P.body[i]));
+    S.pv[i] = make_float2(vol, __int_as_float(mt | (S.matR[mt].kind << 16)));
     if (S.tvf || S.any_conc)
       S.pd[i] = make_float4(S.tvf ? S.P.tx[i] : 0.f, S.tvf ? S.P.ty[i] : 0.f, S.tvf ? S.P.tz[i] : 0.f,
                             S.any_conc ? S.P.C[i] : 0.f);
@@ -553,9 +553,9 @@ __device__ __forceinline__ void force_pair(const Scene<R>& S, Target<R>& t, int 
 // force_pair on packed FP32 neighbour records (same arithmetic in the same order)
 template <int DIM, bool TVF>
 __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const SweepK& K, Target<float>& t, int j,
-                                                  const float* d, float r2, float4 a, float4 b, float4 c, float* acc,
+                                                  const float* d, float r2, float4 a, float4 b, float2 c, float* acc,
                                                   float& heat) {
-  int mk = __float_as_int(c.z);
+  int mk = __float_as_int(c.y);
   int bk = mk >> 16;
   int mj = mk & 0xffff;
   bool same = mj == t.mi;  // the material constants of a pair of one material are the target's
@@ -563,9 +563,9 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const S
   float r = r2 * inv_r;
   float dW = K.sig_dw * quintic_dw<float>(r * K.inv_h);
   float ex = d[0] * inv_r, ey = d[1] * inv_r, ez = d[2] * inv_r;
-  float Vj = c.y;
+  float Vj = c.x;
   if (K.any_heat) {
-    float Tb = c.x;
+    float Tb = S.P.T[j];
     if (!(bk == KWALL && isnan(Tb))) {
       float kb = bk == KWALL || same ? t.kap : S.matR[mj].kappa;
       float ks = t.kap + kb;
@@ -630,7 +630,7 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const S
       acc[1] += coef * 0.5f * rhoj * b.y * sj;
       acc[2] += coef * 0.5f * rhoj * b.z * sj;
     }
-  } else if (bk == KWALL || __float_as_int(c.w) != t.body) {
+  } else if (bk == KWALL || S.P.body[j] != t.body) {
     if (r < K.dx) {  // Eq. contactforce with tension cut-off (particle velocities, not v_w)
       float ev = ex * (t.u[0] - S.P.vx[j]) + ey * (t.u[1] - S.P.vy[j]) + ez * (t.u[2] - S.P.vz[j]);
       float fn = K.kc * (r - K.dx) + K.dc * ev;
@@ -702,7 +702,8 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
           pack_delta<DIM>(K, ti, a, code, d);
           R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
           if (r2 < K.rc2) {
-            float4 b = K.pb[j], c = K.pc[j];
+            float4 b = K.pb[j];
+            float2 c = K.pv[j];
             force_pair_packed<DIM, TVF>(S, K, t, j, d, r2, a, b, c, acc, heat);
             npairs++;
           }
@@ -733,7 +734,8 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
             for (int u = 0; u < 4; u++) {
               if (m + u < cin) {
                 int e = ee[u], j = e >> 5;
-                float4 a = K.pa[j], b = K.pb[j], c = K.pc[j];
+                float4 a = K.pa[j], b = K.pb[j];
+                float2 c = K.pv[j];
                 float d[3];
                 pack_delta<DIM>(K, ti, a, e & 31, d);
                 float r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
@@ -754,7 +756,8 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
             int en = k + 1 < cnt ? __ldg(K.nbl + nb_at(K.n, i, k + 1)) : 0;
             int j = e >> 5;
 #if SPH_FORCE_SPECULATE
-            float4 a = K.pa[j], b = K.pb[j], c = K.pc[j];
+            float4 a = K.pa[j], b = K.pb[j];
+                float2 c = K.pv[j];
 #else
             float4 a = K.pa[j];
 #endif
@@ -763,7 +766,8 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
             float r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
             if (r2 < K.rc2) {
 #if !SPH_FORCE_SPECULATE
-              float4 b = K.pb[j], c = K.pc[j];
+              float4 b = K.pb[j];
+            float2 c = K.pv[j];
 #endif
               force_pair_packed<DIM, TVF>(S, K, t, j, d, r2, a, b, c, acc, heat);
               npairs++;
