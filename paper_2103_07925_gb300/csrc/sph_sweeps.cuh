@@ -186,6 +186,8 @@ __device__ __forceinline__ void list_delta(const Scene<R>& S, const R* ti, int j
 // the same offset from a packed FP32 neighbour record: the cell offset of the entry's code
 // comes from the scene's table of the 27 products -(o ell) (each exact), so the sum is the
 // one the code would give
+// (measured faster than decoding the code with integer selects: the sweeps are bound by
+// the L1 data pipe only partly through this load, and the selects cost more issue slots)
 template <int DIM>
 __device__ __forceinline__ void pack_delta(const SweepK& K, const float* ti, float4 a, int code, float* d) {
   float4 sh = __ldg(K.shift + code);
