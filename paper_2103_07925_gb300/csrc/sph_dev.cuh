@@ -88,6 +88,7 @@ struct Scene {
   R gR[3];
   double h, rc, rc2, dx, skin;
   R rc2R, rl2R, inv_h, sig_w, sig_dw, w0;  // W = sig_w w(q), dW/dr = sig_dw w'(q); rl: list radius
+  double sig_wd, w0d;  // the same factors in FP64 (the FP32 density is formed in FP64 from its sum)
   R half_skin2;
   float rc2f, rl2f;    // FP64 scenes: FP32 pre-test radii (squared) with the rounding margin
   double kc, dc;

@@ -116,6 +116,8 @@ inline sph_status fill_constants(const sph_params* p, Scene<R>& S) {
   S.sig_w = (R)sig;
   S.sig_dw = (R)(sig / S.h);
   S.w0 = (R)(sig * 66.0);  // w(0) = 3^5 - 6 * 2^5 + 15
+  S.sig_wd = sig;
+  S.w0d = sig * 66.0;
   S.nmat = p->n_materials;
   S.has_transition = S.has_enthalpy = 0;
   S.any_heat = 0;

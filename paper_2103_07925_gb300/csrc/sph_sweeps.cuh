@@ -196,6 +196,20 @@ __device__ __forceinline__ void pack_delta(const SweepK& K, const float* ti, flo
   d[2] = DIM == 3 ? (ti[2] - a.z) + sh.z : 0.f;
 }
 
+// compensated FP32 sum (Kahan): the rounding error of each addition is carried into the
+// next, so the sum of the positive kernel terms keeps about twice the working precision;
+// sum() is the compensated value in FP64
+struct KSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double sum() const { return (double)s - (double)c; }
+};
+
 // writer of particle i's in-range list (int4 chunks, see SweepK): entries collect in a
 // register chunk that is stored whole; more than cq entries (the capacity) mark the list
 // as not kept (-1), and the force sweep then walks the full list itself
@@ -264,6 +278,7 @@ __global__ void __launch_bounds__(256, SPH_DENSITY_MIN_BLOCKS) k_density(BatchVi
     if (A.kind == KFLUID) {
       R ti[3] = {S.P.px[i], S.P.py[i], S.P.pz[i]};
       R acc = R(0);
+      KSum ks;  // FP32 scenes: the sum, compensated
       auto visit = [&](int j, int code) {
         R d[3];
         if constexpr (sizeof(R) == 4)
@@ -271,7 +286,10 @@ __global__ void __launch_bounds__(256, SPH_DENSITY_MIN_BLOCKS) k_density(BatchVi
         else
           list_delta<R, DIM>(S, ti, j, code, d);
         R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
-        if (r2 < S.rc2R) acc += quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
+        if (r2 < S.rc2R) {
+          if constexpr (sizeof(R) == 4) ks.add(quintic_w<R>(pair_dist<R>(r2) * S.inv_h));
+          else acc += quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
+        }
       };
       int cnt = S.nbc[i];
       if (cnt <= S.maxnb) {
@@ -304,7 +322,7 @@ __global__ void __launch_bounds__(256, SPH_DENSITY_MIN_BLOCKS) k_density(BatchVi
               pack_delta<DIM>(S, ti, a[q], e[q] & 31, d);
               R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
               if (r2 < S.rc2R) {
-                acc += quintic_w<R>(pair_dist<R>(r2) * S.inv_h);
+                ks.add(quintic_w<R>(pair_dist<R>(r2) * S.inv_h));
                 ir.put(S.nbq, n, i, cq, e[q]);
               }
             }
@@ -320,9 +338,20 @@ __global__ void __launch_bounds__(256, SPH_DENSITY_MIN_BLOCKS) k_density(BatchVi
         scan_cells<R, DIM>(S, i, visit);
         if constexpr (sizeof(R) == 4) S.nbqc[i] = -1;
       }
-      rho = S.P.m[i] * (S.w0 + S.sig_w * acc);
-      S.P.rho[i] = rho;
-      S.prs[i] = A.c2 * (rho - A.rho0);
+      if constexpr (sizeof(R) == 4) {
+        // FP32 scenes: rho = m (W(0) + sum W) and p = c^2 (rho - rho0) in FP64 from the
+        // compensated sum, so that the pressure, a small difference of large numbers, does
+        // not carry the rounding of the stored density (Eq. eos)
+        double rd = (double)S.P.m[i] * (S.w0d + S.sig_wd * ks.sum());
+        const MatD& Ad = S.mat[S.P.mt[i]];
+        rho = (R)rd;
+        S.P.rho[i] = rho;
+        S.prs[i] = (R)(Ad.c * Ad.c * (rd - Ad.rho0));
+      } else {
+        rho = S.P.m[i] * (S.w0 + S.sig_w * acc);
+        S.P.rho[i] = rho;
+        S.prs[i] = A.c2 * (rho - A.rho0);
+      }
     }
     R vol = qdiv<R>(S.P.m[i], rho);
     S.vol[i] = vol;

@@ -27,6 +27,14 @@ def rel_err(a, b, mask=None, scale=0.0):
     return float(np.max(np.abs(a - b) / den))
 
 
+# Achieved bounds of the FP32 path against FP64, one step from the same state, relative to the
+# field itself, max(|y|, RMS(y)) (no term scale); pressure and extrapolated velocity without
+# the boundary particles whose fluid neighbours all sit at the support edge.  The rigid
+# particle force is a small net of pressure terms of order p0 h^(d-1) and keeps the relative
+# rounding of p0; the force on a body, its sum, keeps the precision of the other fields.
+PLAIN32 = dict(pos=1e-7, rho=1e-6, pres=5e-5, acc=3e-5, vel=3e-5, vext=5e-4, force=3e-2, body_force=5e-5)
+
+
 def field_scales(sc):
     """Magnitude of the terms that make up each field at the scene's reference state.
 

@@ -54,6 +54,11 @@ def test_tank_full_size_fp32_in_bench_configuration(tank):
     for f in ("pos", "vel", "acc", "rho", "pres", "temp", "dtemp", "force", "vext"):
         e = rel_err(g.read(f), o.get(f), mask=~edge if f in ("pres", "vext") else None, scale=sca.get(f, 0.0))
         assert e < 1e-5, (f, e)
+    # relative to each field itself (no term scale): the achieved bounds
+    from paper_2103_07925_gb300.errors import PLAIN32
+    for f in ("pos", "vel", "acc", "rho", "pres", "force", "vext"):
+        e = rel_err(g.read(f), o.get(f), mask=~edge if f in ("pres", "vext") else None)
+        assert e < PLAIN32[f], (f, e)
     g.close()
 
 

@@ -175,7 +175,9 @@ def test_skin_lists_give_the_same_step(name):
 @pytest.mark.parametrize("layout", [dict(), dict(key_order=1, cells_per_group=-1, skin=0.3)])
 def test_fp32_fields_from_shared_state(name, layout):
     """FP32 pair sums with cell-relative positions: every per-step field within 1e-5 of
-    the FP64 oracle, relative to max(|y|, RMS(y), the field's term scale)."""
+    the FP64 oracle relative to max(|y|, RMS(y), the field's term scale), and within the
+    achieved bounds of PLAIN32 relative to the field itself, max(|y|, RMS(y))."""
+    from paper_2103_07925_gb300.errors import PLAIN32, edge_only_boundary
     sc = SCENES[name]
     lay = dict(layout)
     if "skin" in lay:
@@ -187,6 +189,39 @@ def test_fp32_fields_from_shared_state(name, layout):
     errs = compare_fields(g, o, fields=["pos", "vel", "rho", "pres", "temp", "acc", "dtemp", "force", "vext"],
                           ints=["mat", "body"], scales=field_scales(sc))
     assert max(errs.values()) < 1e-5, errs
+    edge = edge_only_boundary(sc, o.get("pos"), o.get("mat"))
+    plain = {f: rel_err(g.read(f), o.get(f), mask=~edge if f in ("pres", "vext") else None)
+             for f in PLAIN32 if f != "body_force"}
+    bad = {f: e for f, e in plain.items() if not e < PLAIN32[f]}
+    assert not bad, bad
+    gb, ob = g.bodies(), o.bodies()
+    if len(ob["mass"]):
+        ef = np.max(np.abs(gb["force"] - ob["force"])) / np.max(np.abs(ob["force"]))
+        assert ef < PLAIN32["body_force"], ef
+
+
+def test_fp32_bodies_3d_100_steps():
+    """3D tank with spheres, FP32 pair sums / FP64 bodies, 100 steps against the oracle:
+    centres of mass within 1e-3 of their displacement, orientations and angular velocities
+    within 1e-3 of the rotation they made and of their magnitude."""
+    sc = S.tank3d_spheres(dx=0.04, n_spheres=6, r_range=(0.08, 0.12))
+    g = _gpu(sc, precision=32)
+    o = OracleScene(sc)
+    b0 = o.bodies()
+    g.step(100)
+    o.step(100)
+    bg, bo = g.bodies(), o.bodies()
+    disp = np.linalg.norm(bo["com"] - b0["com"], axis=1)
+    assert disp.min() > 0
+    assert np.max(np.linalg.norm(bg["com"] - bo["com"], axis=1) / disp) < 1e-3
+    # rotation made: the angle between the final and the initial orientation
+    dq = np.abs(np.sum(bo["quat"] * b0["quat"], axis=1))
+    ang = 2 * np.arccos(np.minimum(dq, 1.0))
+    assert ang.min() > 0
+    qerr = np.minimum(np.linalg.norm(bg["quat"] - bo["quat"], axis=1), np.linalg.norm(bg["quat"] + bo["quat"], axis=1))
+    assert np.max(2 * qerr / ang) < 1e-3
+    wn = np.linalg.norm(bo["omega"], axis=1)
+    assert np.max(np.linalg.norm(bg["omega"] - bo["omega"], axis=1) / wn) < 1e-3
 
 
 def test_fp32_rigid_trajectory_100_steps():
