@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--p-background", type=float, default=0.0,
                     help="tank/powder: background pressure of the transport-velocity formulation, in "
                          "units of p0 = rho0 c^2 of the first fluid (the paper's examples use 1); 0: off")
+    ap.add_argument("--preheat", default=None,
+                    help="powder: 'A,wavelength': grains start at T_melt + A sin(2 pi x / wavelength) (gas at "
+                         "T_melt), so metal melts and solidifies throughout the timed steps")
     ap.add_argument("--scenes", type=int, default=256, help="batch: number of scenes")
     ap.add_argument("--jobs", type=int, default=32, help="serve: number of jobs")
     ap.add_argument("--job-steps", type=int, default=1000, help="serve: steps per job")
@@ -126,10 +129,10 @@ WORKLOAD_NAME = {"tank3d": "tank3d_64spheres (1x1x2 tank, fluid to z=1, dx=%g)",
                  "powder": "powder_bed (1x0.5x0.5 box, gas, metal grains melting under a moving source, dx=%g)"}
 
 
-def workload(dx, name="tank3d"):
+def workload(dx, name="tank3d", preheat=None):
     from paper_2103_07925_gb300 import scenes
     if name == "powder":
-        return scenes.powder_bed(dx=dx)
+        return scenes.powder_bed(dx=dx, preheat=preheat)
     if abs(dx - 0.01) < 1e-12:
         return scenes.tank3d_spheres()
     return scenes.tank3d_spheres(dx=dx)
@@ -138,15 +141,15 @@ def workload(dx, name="tank3d"):
 REF_BUDGET_S = 150.0  # timed oracle steps of the reference arm stop within about this
 
 
-def oracle_single_thread(dx, name):
+def oracle_single_thread(dx, name, preheat=None):
     """Pair rate of the oracle on one host thread: one step of the same scene in a child
     process with OMP_NUM_THREADS=1 (the oracle's OpenMP loops then run serially)."""
     code = ("import sys, time, json; sys.path.insert(0, %r)\n"
             "import bench\n"
             "from oracle.oracle import OracleScene\n"
-            "o = OracleScene(bench.workload(%r, %r))\n"
+            "o = OracleScene(bench.workload(%r, %r, %r))\n"
             "t0 = time.perf_counter(); o.step(1); t = time.perf_counter() - t0\n"
-            "print(json.dumps({'value': o.diagnostics()[15] / t, 'seconds': t}))\n") % (ROOT, dx, name)
+            "print(json.dumps({'value': o.diagnostics()[15] / t, 'seconds': t}))\n") % (ROOT, dx, name, preheat)
     env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
     if r.returncode != 0:
@@ -168,7 +171,8 @@ def run_reference(args):
         return
     name = args.workload if args.workload in DEFAULT_DX else "tank3d"
     dx = args.dx or DEFAULT_DX[name]
-    sc = workload(dx, name)
+    preheat = tuple(float(v) for v in args.preheat.split(",")) if args.preheat else None
+    sc = workload(dx, name, preheat)
     o = OracleScene(sc)
     t0 = time.perf_counter()
     o.step(1)  # one untimed step sizes the sample
@@ -197,7 +201,7 @@ def run_reference(args):
            "cpu_baseline": {"value": val, "unit": "pair-interactions/s", "cores": cores, "kind": "oracle",
                             "sample": "%d timed FP64 oracle steps (after %d warm-up) of the same %d-particle "
                                       "scene" % (k, w, n)},
-           "cpu_baseline_1thread": oracle_single_thread(dx, name),
+           "cpu_baseline_1thread": oracle_single_thread(dx, name, preheat),
            "e2e": {"value": val, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -392,7 +396,8 @@ def main():
     # launches of about 40 ms), and the SM count it found
     peak_tf, n_sm, _ = fp32_peak()
     dx = args.dx or DEFAULT_DX[args.workload]
-    sc = workload(dx, args.workload)
+    preheat = tuple(float(v) for v in args.preheat.split(",")) if args.preheat else None
+    sc = workload(dx, args.workload, preheat)
     if args.p_background > 0:
         fl = [m for m in sc["materials"] if m["kind"] == 0][0]
         sc["params"]["p_background"] = args.p_background * fl["rho0"] * fl["c"] ** 2
@@ -410,12 +415,22 @@ def main():
         layout, launch = dict(tn.params), dict(tn.launch)
         tuned = dict(layout, **launch, ms_per_step=tn.ms_per_step, seconds=time.perf_counter() - t_tune,
                      trials=len(tn.table))
+    relabel_step1 = None
+    if args.workload == "powder" and any(m["transitions_to"] >= 0 for m in sc["materials"]):
+        # the first step of a fresh scene, stage by stage (the preheated bed melts the hot
+        # parts of its grains there): relabelled particles and the time of each stage
+        g1 = Scene(sc, precision=args.precision, stream=stream.cuda_stream, **layout)
+        g1.set_launch(**launch)
+        prof1 = g1.profile(1)
+        relabel_step1 = {"relabelled": g1.info()["relabelled"], "profile_ms": prof1}
+        g1.close()
     g = Scene(sc, precision=args.precision, stream=stream.cuda_stream, **layout)
     g.set_launch(**launch)
     info = g.info()
     g.step(args.warmup)
     clocks = Clocks(local)
     p_before = g.info()["pairs_total"]
+    rl_before = g.info()["relabelled"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.start()
     time.sleep(0.3)
@@ -454,6 +469,8 @@ def main():
                       "wall": info["n_wall"], "bodies": info["n_bodies"], "cells": info["n_cells"],
                       "precision": "FP32 pair sums, FP64 bodies" if args.precision == 32 else "FP64",
                       "p_background_over_p0": args.p_background,
+                      "preheat": preheat,
+                      "grains": sc.get("info", {}).get("grains"),
                       "key_order": "morton" if layout["key_order"] == 0 else "row-major",
                       "cells_per_group": layout.get("cells_per_group", 0),
                       "skin_h": layout["skin"] / sc["params"]["h"],
@@ -464,6 +481,8 @@ def main():
            "pairs_per_step": pairs_per_step,
            "list_rebuilds": g.info()["rebuilds"],
            "relabelled": g.info()["relabelled"],
+           "relabelled_per_timed_step": (g.info()["relabelled"] - rl_before) / args.steps,
+           "first_step_of_a_fresh_scene": relabel_step1,
            "gpu_launches": args.steps * g.info()["kernels_per_step"],
            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                         "frac": achieved_tf / peak_tf,

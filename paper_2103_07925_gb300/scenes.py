@@ -573,7 +573,7 @@ def batch_mix(count=256, seed=2103, n_lo=1e4, n_hi=5e5, max_bodies=50, precision
 def powder_bed(dx=0.005, size=(1.0, 0.5, 0.5), n_grains=2000, r_median=0.02, r_sigma=0.3,
                r_clip=(0.01, 0.05), bed_frac=0.8, seed=2103, T0=300.0, T_melt=1700.0, mushy=20.0,
                c_metal=1.0, nu=1e-3, Q0=1e10, src_radius=0.05, src_speed=0.5, src_depth=None,
-               g=-9.81, max_tries=4, precision=32):
+               g=-9.81, max_tries=4, preheat=None, precision=32):
     """Powder bed with melting grains (the shape of Sec. 4.4 in 3D).
 
     Box ``size`` (periodic in x and y) filled on a dx lattice: a three-layer wall slab
@@ -589,6 +589,12 @@ def powder_bed(dx=0.005, size=(1.0, 0.5, 0.5), n_grains=2000, r_median=0.02, r_s
     (c_gas = c_metal sqrt(1000)).  A Gaussian surface source of power density Q0, radius
     ``src_radius`` moves along x at ``src_speed`` over the top of the bed, heating metal
     within ``src_depth`` (default 10 dx) below the bed top.
+
+    ``preheat=(A, wavelength)``: the grains start at T_melt + A sin(2 pi x / wavelength)
+    instead of T0 (the gas at T_melt), so that every grain crossing a zero of the sine is
+    part above and part below the melting temperature: the hot parts melt at the end of
+    the first step, and conduction inside the grains then moves the melting fronts, which
+    keeps metal melting and solidifying step after step.
     """
     rng = np.random.default_rng(seed)
     nx, ny, nz = (int(round(s / dx)) for s in size)
@@ -644,7 +650,7 @@ def powder_bed(dx=0.005, size=(1.0, 0.5, 0.5), n_grains=2000, r_median=0.02, r_s
             material(FLUID, rho_m, c=c_metal, eta=rho_m * nu, cp=1.0, kappa=10.0, T_transition=T_melt,
                      transitions_to=2, latent_heat=L, mushy_width=mushy)]
     b = _Builder(3)
-    b.add(sites[owner < 0], 0, rho_g * dx ** 3, rho_g, T0)
+    b.add(sites[owner < 0], 0, rho_g * dx ** 3, rho_g, T0 if preheat is None else T_melt)
     order = np.argsort(owner[owner >= 0], kind="stable")
     rig = sites[owner >= 0][order]
     rid = owner[owner >= 0][order]
@@ -654,7 +660,8 @@ def powder_bed(dx=0.005, size=(1.0, 0.5, 0.5), n_grains=2000, r_median=0.02, r_s
     for _ in range(len(used)):
         b.add_body()
     if len(rig):
-        b.add(rig, 2, rho_m * dx ** 3, rho_m, T0, body=remap[rid].astype(np.int32))
+        Tg = T0 if preheat is None else T_melt + preheat[0] * np.sin(2 * np.pi * rig[:, 0] / preheat[1])
+        b.add(rig, 2, rho_m * dx ** 3, rho_m, Tg, body=remap[rid].astype(np.int32))
     # substrate slab (Dirichlet T0) and adiabatic lid, three layers each
     slab = lattice([0.0, 0.0, -3 * dx], [nx, ny, 3], dx)
     b.add(slab, 1, rho_g * dx ** 3, rho_g, T0, wall_T=T0)

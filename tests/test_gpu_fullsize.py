@@ -104,3 +104,39 @@ def test_batched_mix_full_size_sampled_scenes():
             assert e < 1e-5, (q, f, e)
         assert np.array_equal(B.read(ids[q], "mat"), o.get("mat"))
     B.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_preheated_powder_bed_full_size_step_with_relabels(precision):
+    """The 2.1M-particle powder bed with its grains across the melting temperature
+    (T_melt + 30 sin(2 pi x / 0.1)): the first step melts the hot parts of every grain
+    (Sec. 3.6 with the apparent-capacity extension).  Materials bit-exact against the
+    oracle; body ids bit-exact in FP64, valid joins in FP32; fields within the tolerance
+    of the path.  Rigid positions after a step agree with the oracle's to rounding, not bit
+    for bit, so a pair of lattice sites exactly r_c apart may fall on either side of r_c:
+    a wall or rigid particle whose only fluid neighbours are such pairs has an extrapolated
+    pressure and velocity that are weighted means of nearly nothing (acting on no particle),
+    and is left out of those two fields in both precisions."""
+    from oracle.oracle import OracleScene
+    from paper_2103_07925_gb300.sph import Scene
+    from tests.test_gpu_powder import _edge_only_boundary, _joins_valid
+    sc = S.powder_bed(preheat=(30.0, 0.1), precision=precision)
+    g = Scene(sc, precision=precision, **LAYOUT)
+    g.step(1)
+    o = OracleScene(sc)
+    o.step(1)
+    assert g.info()["relabelled"] > 1000
+    assert np.array_equal(g.read("mat"), o.get("mat"))
+    if precision == 64:
+        assert np.array_equal(g.read("body"), o.get("body"))
+        mask = np.ones(len(sc["particles"]["mass"]), bool)
+    else:
+        mask, nd = _joins_valid(sc, g, o)
+        assert nd <= 0.01 * g.info()["relabelled"], nd
+    tol = 1e-12 if precision == 64 else 1e-5
+    ext = mask & ~_edge_only_boundary(sc, o)
+    sca = dict(field_scales(sc), enth=0.0)
+    for f in ("pos", "vel", "acc", "rho", "pres", "temp", "dtemp", "force", "vext", "enth"):
+        e = rel_err(g.read(f), o.get(f), mask=ext if f in ("pres", "vext") else mask, scale=sca.get(f, 0.0))
+        assert e < tol, (f, e)
+    g.close()
