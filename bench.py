@@ -27,10 +27,16 @@ sys.path.insert(0, ROOT)
 METRIC = "SPH pair-interactions/s & steps/s at 1M particles; p50/p99 job latency vs plain"
 FLOP_PER_PAIR = 62      # FP32 pair arithmetic of the force/heat sweep, FMA = 2 (see the design notes)
 BYTES_PER_TARGET = 72   # algorithmic HBM bytes per target particle of the force sweep (FP32)
-# DRAM bytes (read + write) of one k_force launch on the default workload, from an
-# `ncu --set full` capture of this kernel version, per cell layout (key order, skin in h) it
-# was captured with; emptied whenever the kernel changes
-K_FORCE_TRAFFIC = {(1, 0.3): 734.6e6}
+# density sweep: offset 6, squared distance 5, root 1, q 1, kernel polynomial 11,
+# accumulation 1 FP32 operations per pair inside the support; 28 algorithmic bytes per
+# fluid target (position, mass and material in, density out)
+FLOP_PER_DENSITY_PAIR = 25
+BYTES_PER_DENSITY_TARGET = 28
+# DRAM bytes (read + write) of one launch on the default workload, from `ncu --set full`
+# captures of this kernel version (a smaller tank, scaled by the targets), per kernel and
+# cell layout (key order, skin in h) they were captured with; emptied whenever a kernel
+# changes
+TRAFFIC = {("k_force", 1, 0.5): 579.6e6, ("k_density", 1, 0.5): 1192.9e6}
 FP32_LANES_PER_SM = 128  # nominal, for the context figure beside the measured peak
 
 
@@ -452,14 +458,29 @@ def main():
     steps_per_s = args.steps / (ms_max / 1e3)
     # per-kernel device times over the same number of steps, kernels launched one by one
     prof = g.profile(min(args.steps, 50))
-    force_ms = prof["force"]
     pairs_per_step = pairs / args.steps
-    achieved_tf = pairs_per_step * FLOP_PER_PAIR / (force_ms * 1e-3) / 1e12
     # context: the nominal FP32 peak at the SM clock sampled during the timed region
     clock_mhz = clk["sm_mhz"] or smmax
     nominal_tf = n_sm * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
-    n_targets = info["n_fluid"] + info["n_rigid"]
-    hbm_ach = n_targets * BYTES_PER_TARGET / (force_ms * 1e-3) / 1e9
+    full_tank = args.workload == "tank3d" and dx == 0.01 and args.precision == 32 and args.p_background == 0
+    skin_h = round(layout["skin"] / sc["params"]["h"], 3)
+
+    def roofline(kernel, ms, flop, alg_bytes):
+        ach = flop / (ms * 1e-3) / 1e12
+        hb = alg_bytes / (ms * 1e-3) / 1e9
+        return {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
+                "traffic": TRAFFIC.get((kernel, layout["key_order"], skin_h)) if full_tank else None,
+                "kernel": kernel, "ms_per_launch": ms,
+                "peak_source": "measured: FP32 FMA microbenchmark of the library (sph_fp32_peak) on this "
+                               "GPU, %d SMs" % n_sm,
+                "nominal_at_sampled_clock": {"value": nominal_tf, "sm_mhz": clock_mhz, "frac": ach / nominal_tf},
+                "hbm": {"achieved_gbs": hb, "peak_gbs": hbm, "frac": hb / hbm, "peak_source": peak_src}}
+
+    rl_force = roofline("k_force", prof["force"], pairs_per_step * FLOP_PER_PAIR,
+                        (info["n_fluid"] + info["n_rigid"]) * BYTES_PER_TARGET)
+    rl_density = roofline("k_density", prof["density"], pairs_per_step * FLOP_PER_DENSITY_PAIR,
+                          info["n_fluid"] * BYTES_PER_DENSITY_TARGET)
+    dominant, other = (rl_density, rl_force) if prof["density"] >= prof["force"] else (rl_force, rl_density)
     out = {"metric": METRIC, "value": value, "unit": "pair-interactions/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -484,18 +505,8 @@ def main():
            "relabelled_per_timed_step": (g.info()["relabelled"] - rl_before) / args.steps,
            "first_step_of_a_fresh_scene": relabel_step1,
            "gpu_launches": args.steps * g.info()["kernels_per_step"],
-           "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                        "frac": achieved_tf / peak_tf,
-                        "traffic": K_FORCE_TRAFFIC.get((layout["key_order"], round(layout["skin"] / sc["params"]["h"], 3)))
-                        if (args.workload == "tank3d" and dx == 0.01 and args.precision == 32
-                            and args.p_background == 0) else None,
-                        "kernel": "k_force",
-                        "peak_source": "measured: FP32 FMA microbenchmark of the library (sph_fp32_peak) on this "
-                                       "GPU, %d SMs" % n_sm,
-                        "nominal_at_sampled_clock": {"value": nominal_tf, "sm_mhz": clock_mhz,
-                                                     "frac": achieved_tf / nominal_tf},
-                        "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": hbm, "frac": hbm_ach / hbm,
-                                "peak_source": peak_src}},
+           "roofline": dominant,
+           "roofline_" + other["kernel"]: other,
            "profile_ms": prof, "clocks": clk}
     # plain FP64 path on the same workload
     if not args.no_fp64 and args.precision == 32:
