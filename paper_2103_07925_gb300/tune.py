@@ -24,7 +24,7 @@ from dataclasses import dataclass, field
 
 # cells_per_group = -1: row-major keys searched in windows of 32 consecutive particles
 LAYOUTS = [dict(key_order=0, cells_per_group=0)] + [dict(key_order=1, cells_per_group=g) for g in (1, 2, 3, -1)]
-SKINS_H = (0.0, 0.1, 0.15, 0.2, 0.3, 0.5)
+SKINS_H = (0.0, 0.1, 0.15, 0.2, 0.3, 0.5, 0.7, 1.0)
 SWEEP_BLOCKS = (64, 128, 256)
 WAVES = (0, 1, 2, 4)
 
