@@ -112,10 +112,13 @@ def test_admission_by_memory_footprint():
 
 
 def test_batch_fp32_against_oracle_on_sampled_scenes():
-    """FP32 in the mix against the FP64 oracle after one step (per-step field tolerance)."""
+    """FP32 in the mix against the FP64 oracle after one step: every output field within the
+    per-step tolerance (pres and vext without the edge-only boundary particles, whose weighted
+    means of nearly nothing act on no particle)."""
     from oracle.oracle import OracleScene
+    from paper_2103_07925_gb300.errors import edge_only_boundary
     from paper_2103_07925_gb300.sph import Batch
-    from tests.parity import compare_fields, field_scales
+    from tests.parity import compare_fields, field_scales, rel_err
     mix = _mix()
     B = Batch(capacity=16, precision=32)
     ids = {name: B.admit(sc, 1) for name, sc, _ in mix}
@@ -128,8 +131,12 @@ def test_batch_fp32_against_oracle_on_sampled_scenes():
             def read(self, f, _id=ids[name]):
                 return B.read(_id, f)
 
-        errs = compare_fields(View(), o, fields=["pos", "vel", "rho", "pres", "temp"], ints=["mat", "body"],
-                              scales=field_scales(sc))
+        errs = compare_fields(View(), o, fields=["pos", "vel", "acc", "rho", "temp", "dtemp", "force"],
+                              ints=["mat", "body"], scales=field_scales(sc))
+        edge = edge_only_boundary(sc, o.get("pos"), o.get("mat"))
+        sca = field_scales(sc)
+        for f in ("pres", "vext"):
+            errs[f] = rel_err(B.read(ids[name], f), o.get(f), mask=~edge, scale=sca.get(f, 0.0))
         bad = {f: e for f, e in errs.items() if not e < 1e-5}
         assert not bad, (name, bad)
     B.close()
