@@ -51,3 +51,59 @@ def test_edge_neighbour_keeps_fp32_finite_and_fp64_exact(eps, dim):
     bad = {k: e for k, e in errs.items() if not e < 1e-12}
     assert not bad, bad
     g64.close()
+
+
+def _clump_scene(n_rigid=20, seed=4):
+    """3D: a lattice block of fluid and, more than r_c away from it, a dense clump: the sites
+    of a lattice of spacing 0.37 dx inside a ball of radius 0.45 r_c (jittered by 1e-3 of
+    that spacing), the n_rigid sites nearest its centre rigid (one body), the others fluid.
+    Every clump particle has every other one inside the support: more neighbours than the
+    in-range list of the FP32 sweeps holds (the list capacity at r_c), while its full
+    neighbour list (radius r_c + 0.3 h) still fits."""
+    rng = np.random.default_rng(seed)
+    dx = 0.05
+    h = dx
+    rc = 3 * h
+    b = S._Builder(3)
+    mats = [S.material(S.FLUID, 1.0, c=10.0, eta=0.01), S.material(S.RIGID, 2.0)]
+    b.add(S.lattice([0.0] * 3, [4] * 3, dx), 0, dx ** 3, 1.0, 300.0)
+    s = 0.37 * dx
+    g = (np.arange(-8, 9) + 0.5) * s
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    r = np.linalg.norm(pts, axis=1)
+    pts = pts[r < 0.45 * rc]
+    pts = pts[np.argsort(np.linalg.norm(pts, axis=1), kind="stable")]
+    pts = pts + 0.7 + rng.uniform(-1e-3 * s, 1e-3 * s, pts.shape)
+    b.add(pts[n_rigid:], 0, dx ** 3, 1.0, 300.0)
+    kb = b.add_body(vel=(0.05, 0.0, 0.0))
+    b.add(pts[:n_rigid], 1, 2.0 * dx ** 3, 2.0, 300.0, body=kb)
+    p = S.default_params(3, dx, [-0.1] * 3, [1.0] * 3, dt_mode=0, dt_fixed=1e-5, skin=0.3 * h)
+    return b.finish(p, mats)
+
+
+def test_dense_clump_beyond_the_in_range_capacity():
+    """Targets whose neighbours inside the support exceed the in-range list capacity (the
+    list capacity at r_c): the FP32 force sweep walks their full list with the distance test
+    instead; both precisions against the oracle after one step."""
+    from oracle.oracle import OracleScene
+    from paper_2103_07925_gb300.sph import Scene
+    sc = _clump_scene()
+    o = OracleScene(sc)
+    counts, _ = o.neighbors()
+    clump = np.arange(len(counts)) >= 4 ** 3
+    nb = int(clump.sum()) - 1
+    assert counts[clump].min() == nb
+    g0 = Scene(sc, precision=32, skin=0.0)
+    cap_rc = g0.info()["list_capacity"]  # the in-range capacity: the list capacity at r_c
+    g0.close()
+    assert nb > cap_rc
+    for precision, tol in ((64, 1e-12), (32, 1e-5)):
+        g = Scene(sc, precision=precision)
+        assert g.info()["list_capacity"] >= nb  # the full list (radius r_c + 0.3 h) holds them
+        g.step(1)
+        o2 = OracleScene(sc)
+        o2.step(1)
+        errs = compare_fields(g, o2, ints=["mat", "body"], scales=field_scales(sc))
+        bad = {k: e for k, e in errs.items() if not e < tol}
+        assert not bad, (precision, bad)
+        g.close()
