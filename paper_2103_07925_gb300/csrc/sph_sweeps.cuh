@@ -263,11 +263,10 @@ __device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
 
 // ---------------------------------------------------------------- density on steps without rebuild
 // Eq. densum + Eq. eos over the list, every step
-#ifndef SPH_DENSITY_MIN_BLOCKS
-#define SPH_DENSITY_MIN_BLOCKS 4
-#endif
+// resident blocks per SM: five for the FP32 walk (48 registers), four for FP64 (which
+// would spill at five)
 template <class R, int DIM>
-__global__ void __launch_bounds__(256, SPH_DENSITY_MIN_BLOCKS) k_density(BatchView<R> B) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) k_density(BatchView<R> B) {
   int total = __ldg(B.pfx_part + B.nsc);
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     int s = find_scene(B.pfx_part, B.nsc, g);
@@ -295,9 +294,10 @@ __global__ void __launch_bounds__(256, SPH_DENSITY_MIN_BLOCKS) k_density(BatchVi
       if (cnt <= S.maxnb) {
         int k = 0;
         if constexpr (sizeof(R) == 4) {
-          // one list chunk (four entries) at a time: the four position gathers are in flight
-          // together (a latency-bound walk), the next chunk while they are summed; the sum
-          // keeps the list order.  The entries inside the support are copied, in list order,
+          // one list chunk (four entries) at a time, its position gathers two by two (two in
+          // flight and the next chunk's load while they are summed: fewer registers than four
+          // gathers at once, so five blocks fit on an SM, measured 3.5% faster on the 3D
+          // tank); the sum keeps the list order.  The entries inside the support are copied, in list order,
           // into the in-range list the force sweep of this evaluation walks.
           size_t n = S.n;
           const float4* pa = S.pa;
@@ -307,23 +307,28 @@ __global__ void __launch_bounds__(256, SPH_DENSITY_MIN_BLOCKS) k_density(BatchVi
           int4 c = cnt > 0 ? __ldg(L4) : make_int4(0, 0, 0, 0);
           for (; k < cnt; k += 4) {
             int4 cn = k + 4 < cnt ? __ldg(L4 + (size_t)((k >> 2) + 1) * n) : make_int4(0, 0, 0, 0);
-            int e[4] = {c.x, c.y, c.z, c.w};
-            bool ok[4];
-            float4 a[4];
+            int ec[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-              ok[q] = k + q < cnt;  // the last chunk may be partial
-              a[q] = pa[ok[q] ? e[q] >> 5 : i];
-            }
+            for (int h = 0; h < 4; h += 2) {
+              int e[2];
+              bool ok[2];
+              float4 a[2];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-              if (!ok[q]) continue;
-              R d[3];
-              pack_delta<DIM>(S, ti, a[q], e[q] & 31, d);
-              R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
-              if (r2 < S.rc2R) {
-                ks.add(quintic_w<R>(pair_dist<R>(r2) * S.inv_h));
-                ir.put(S.nbq, n, i, cq, e[q]);
+              for (int q = 0; q < 2; q++) {
+                e[q] = ec[h + q];
+                ok[q] = k + h + q < cnt;  // the last chunk may be partial
+                a[q] = pa[ok[q] ? e[q] >> 5 : i];
+              }
+#pragma unroll
+              for (int q = 0; q < 2; q++) {
+                if (!ok[q]) continue;
+                R d[3];
+                pack_delta<DIM>(S, ti, a[q], e[q] & 31, d);
+                R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+                if (r2 < S.rc2R) {
+                  ks.add(quintic_w<R>(pair_dist<R>(r2) * S.inv_h));
+                  ir.put(S.nbq, n, i, cq, e[q]);
+                }
               }
             }
             c = cn;
