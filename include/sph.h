@@ -135,7 +135,7 @@ typedef struct {
  *  concentration    initial concentration C (nullable: zero; phases with C_fixed start
  *                   at C_fixed) */
 typedef struct {
-  int64_t n;
+  int64_t n;  /* 1 .. 2^26 (a neighbour list entry holds the index in 26 bits) */
   const double *pos, *vel, *mass, *density, *temperature;
   const int32_t *material, *body;
   const double *wall_velocity, *wall_temperature;

@@ -64,11 +64,12 @@ struct SweepK {
   const int4* nbq;
   const int* nbqc;
   int cq;
-  // cell offset of a list entry's code, -(ox ell_x, oy ell_y, oz ell_z): added to p_i - p_j
-  // (27 entries, code = (ox + 1) + 3 (oy + 1) + 9 (oz + 1))
+  // the cell offsets -(o_x ell_x, o_y ell_y, o_z ell_z) of the 64 codes (27 of them used):
+  // the density sweep's form of the offset (a load where the other sweeps decode the code)
   const float4* shift;
   int n;
   float ell[3];                     // cell edges (positions are relative to the cell origin)
+  float nell[3];                    // -ell: the cell offset of an entry is nb_of(code) nell
   float rc2, sig_dw, inv_h;         // r_c^2, dW/dr = sig_dw w'(r / h)
   float dx, kc, dc;                 // contact: cut-off distance, spring and damper
   int any_heat, any_conc, tvf;
@@ -122,12 +123,12 @@ struct Scene {
   float2* pv;
   SweepK k;            // FP32 scenes: the per-entry constants of the pair sweeps
   float4* pd;          // (u~ - u, C): transport-velocity formulation and concentration
-  int* nbl;            // neighbour lists: entry k of particle i at nbl[nb_at(n, i, k)] = j << 5 | cell code
+  int* nbl;            // neighbour lists: entry k of particle i at nbl[nb_at(n, i, k)] = nb_entry(j, code)
   int* nbc;            // neighbour count of each particle (may exceed maxnb: then cells are scanned)
   int4* nbq;           // FP32 scenes: in-range entries of this evaluation (see SweepK)
   int* nbqc;
   int cq;              // capacity of the in-range lists (entries, a multiple of 4)
-  float4* shift;       // FP32 scenes: cell offsets of the 27 entry codes (see SweepK)
+  float4* shift;       // FP32 scenes: cell offsets of the entry codes (see SweepK)
   R *xr, *yr, *zr;     // positions at the last list rebuild (same frame as the bank)
   unsigned long long* disp;  // bits of the largest squared displacement since the rebuild
   int maxnb;           // list capacity per particle
@@ -202,6 +203,22 @@ enum { ST_NONFINITE = 0, ST_CAPACITY = 2, ST_HOOK_TIMEOUT = 11 };
 // the int offset of entry k of particle i
 __device__ __forceinline__ size_t nb_at(size_t n, int i, int k) {
   return 4 * ((size_t)(k >> 2) * n + (size_t)i) + (size_t)(k & 3);
+}
+
+// a list entry: the neighbour's sorted index j (26 bits) and the offset o = c_j - c_i of its
+// cell from the target's, o + 1 in two bits per axis: e = j << 6 | code (read unsigned)
+constexpr int kMaxListIndex = 1 << 26;
+__device__ __forceinline__ int nb_code(int ox, int oy, int oz) {
+  return (ox + 1) | ((oy + 1) << 2) | ((oz + 1) << 4);
+}
+__device__ __forceinline__ int nb_entry(int j, int code) { return (int)(((unsigned)j << 6) | (unsigned)code); }
+__device__ __forceinline__ int nb_j(int e) { return (int)((unsigned)e >> 6); }
+__device__ __forceinline__ int nb_cd(int e) { return e & 63; }
+__device__ __forceinline__ int nb_o(int code, int a) { return ((code >> (2 * a)) & 3) - 1; }
+// the same offset as an exact float: the two bits b end the mantissa of 1.5 2^23 + b (unit
+// in the last place 1), so subtracting 1.5 2^23 + 1 leaves b - 1 exactly
+__device__ __forceinline__ float nb_of(int code, int a) {
+  return __int_as_float(0x4B400000 | ((code >> (2 * a)) & 3)) - 12582913.0f;
 }
 
 __device__ __forceinline__ int find_scene(const int* __restrict__ pfx, int nsc, int g) {

@@ -252,7 +252,7 @@ class Engine {
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, k_force<R, DIM, true, false>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs1, k_force<R, DIM, false, true>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt1, k_force<R, DIM, true, true>, sweep_block, 0));
-    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_density<R, DIM>, sweep_block, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_density<R, DIM, true>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_extrap<R, DIM>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, k_search<R, DIM>, 128, 0));
     // resident blocks per SM: the kernel's occupancy, capped by the requested waves
@@ -511,7 +511,8 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   memset(&S, 0, sizeof(S));
   SPH_TRY(fill_constants(p, S));
   int64_t n64 = in->n;
-  if (n64 < 1 || n64 > (1LL << 30)) { set_error("particle count must be in [1, 2^30]"); return SPH_ERR_INVALID; }
+  // a list entry holds a sorted index in 26 bits
+  if (n64 < 1 || n64 > kMaxListIndex) { set_error("particle count must be in [1, 2^26]"); return SPH_ERR_INVALID; }
   if (!in->pos || !in->vel || !in->mass || !in->density || !in->temperature || !in->material || !in->body) {
     set_error("pos, vel, mass, density, temperature, material and body are required");
     return SPH_ERR_INVALID;
@@ -614,13 +615,13 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
     S.cq = list_capacity(DIM, S.rc / S.dx);
     SPH_TRY(A(&S.nbq, (size_t)(S.cq / 4) * n));
     SPH_TRY(A(&S.nbqc, (size_t)n));
-    SPH_TRY(A(&S.shift, 32));
-    float4 sh[32];
-    for (int c = 0; c < 32; c++) {
-      int ox = c % 3 - 1, oy = (c / 3) % 3 - 1, oz = c / 9 - 1;
-      // the same products the sweeps formed from the code: exact (0 or +-ell)
-      sh[c] = make_float4(-((float)ox * (float)S.ellR[0]), -((float)oy * (float)S.ellR[1]),
-                          DIM == 3 ? -((float)oz * (float)S.ellR[2]) : 0.f, 0.f);
+    SPH_TRY(A(&S.shift, 64));
+    float4 sh[64];
+    for (int c = 0; c < 64; c++) {
+      int ox = (c & 3) - 1, oy = ((c >> 2) & 3) - 1, oz = ((c >> 4) & 3) - 1;
+      // the products the other sweeps form from the code: exact (0 or +-ell)
+      sh[c] = make_float4((float)ox * -(float)S.ellR[0], (float)oy * -(float)S.ellR[1],
+                          DIM == 3 ? (float)oz * -(float)S.ellR[2] : 0.f, 0.f);
     }
     SPH_CU(cudaMemcpyAsync(S.shift, sh, sizeof(sh), cudaMemcpyHostToDevice, stream));
   }
@@ -752,7 +753,10 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
       S.k.cq = S.cq;
       S.k.shift = S.shift;
       S.k.n = n;
-      for (int d = 0; d < 3; d++) S.k.ell[d] = (float)S.ellR[d];
+      for (int d = 0; d < 3; d++) {
+        S.k.ell[d] = (float)S.ellR[d];
+        S.k.nell[d] = -(float)S.ellR[d];
+      }
       S.k.rc2 = (float)S.rc2R; S.k.sig_dw = (float)S.sig_dw; S.k.inv_h = (float)S.inv_h;
       S.k.dx = (float)S.dxR; S.k.kc = (float)S.kcR; S.k.dc = (float)S.dcR;
       S.k.any_heat = S.any_heat; S.k.any_conc = S.any_conc; S.k.tvf = S.tvf;
@@ -809,7 +813,7 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   k_rigid_vel<R><<<gp, 256, 0, stream>>>(B, 0);
   int gw = grid_for((int64_t)S.ngroups * 32, 128, grid_warp);
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
-  k_density<R, DIM><<<grid_for(n, sweep_block, grid_dens), sweep_block, 0, stream>>>(B);
+  k_density<R, DIM, true><<<grid_for(n, sweep_block, grid_dens), sweep_block, 0, stream>>>(B, S.k);
   k_extrap<R, DIM><<<grid_for(n, sweep_block, grid_extrap), sweep_block, 0, stream>>>(B);
   if (S.tvf || S.any_conc)
     k_force<R, DIM, true, true><<<grid_for(n, sweep_block, grid_tvf1), sweep_block, 0, stream>>>(B, S.k);
@@ -897,7 +901,8 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   rec();
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   rec();
-  k_density<R, DIM><<<gsd, sweep_block, 0, stream>>>(B);
+  if (ns == 1) k_density<R, DIM, true><<<gsd, sweep_block, 0, stream>>>(B, hs[act[0]].k);
+  else k_density<R, DIM, false><<<gsd, sweep_block, 0, stream>>>(B, SweepK{});
   rec();
   k_extrap<R, DIM><<<gse, sweep_block, 0, stream>>>(B);
   rec();

@@ -37,7 +37,7 @@ __device__ __forceinline__ void for_each_neighbor(const Scene<R>& S, int i, F&& 
   if (cnt <= S.maxnb) {
     for (int k = 0; k < cnt; k++) {
       int e = S.nbl[nb_at(S.n, i, k)];
-      visit(e >> 5, e & 31);
+      visit(nb_j(e), nb_cd(e));
     }
   } else {
     scan_cells<R, DIM>(S, i, visit);

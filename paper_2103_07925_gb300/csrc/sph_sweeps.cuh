@@ -84,8 +84,7 @@ struct SearchPol {
   // entries collect in a register chunk that is stored whole (16 bytes); entries past the
   // capacity are counted, not stored (the sweeps then scan the cells of that target)
   __device__ void pair(const Scene<R>&, int, int j, R, R, R, R) {
-    int code = (cox - tx + 1) + 3 * (cdy + 1) + 9 * (cdz + 1);
-    int e = (j << 5) | code;
+    int e = nb_entry(j, nb_code(cox - tx, cdy, cdz));
     int u = cnt & 3;
     if (u == 0) buf.x = e;
     else if (u == 1) buf.y = e;
@@ -176,20 +175,26 @@ __device__ __forceinline__ void list_delta(const Scene<R>& S, const R* ti, int j
         else if (d[k] < -h) d[k] = dsub(d[k], -S.LR[k]);
       }
   } else {
-    int ox = code % 3 - 1, oy = (code / 3) % 3 - 1, oz = code / 9 - 1;
-    d[0] = (ti[0] - S.P.px[j]) - (R)ox * S.ellR[0];
-    d[1] = (ti[1] - S.P.py[j]) - (R)oy * S.ellR[1];
-    d[2] = DIM == 3 ? (ti[2] - S.P.pz[j]) - (R)oz * S.ellR[2] : R(0);
+    d[0] = (ti[0] - S.P.px[j]) - (R)nb_o(code, 0) * S.ellR[0];
+    d[1] = (ti[1] - S.P.py[j]) - (R)nb_o(code, 1) * S.ellR[1];
+    d[2] = DIM == 3 ? (ti[2] - S.P.pz[j]) - (R)nb_o(code, 2) * S.ellR[2] : R(0);
   }
 }
 
-// the same offset from a packed FP32 neighbour record: the cell offset of the entry's code
-// comes from the scene's table of the 27 products -(o ell) (each exact), so the sum is the
-// one the code would give
-// (measured faster than decoding the code with integer selects: the sweeps are bound by
-// the L1 data pipe only partly through this load, and the selects cost more issue slots)
+// the same offset from a packed FP32 neighbour record: the cell offset o ell of the entry's
+// code is formed exactly (o in {-1, 0, 1} from its two bits, the product one of 0, +-ell),
+// so the sum is rounded once, as above.  Two forms of the same values: decoded from the
+// code in registers (the force and extrapolation sweeps, whose several gathers per pair
+// load the L1 data pipe), or loaded from the scene's table of the offsets (the density
+// sweep, bound by issue more than by its loads)
 template <int DIM>
 __device__ __forceinline__ void pack_delta(const SweepK& K, const float* ti, float4 a, int code, float* d) {
+  d[0] = (ti[0] - a.x) + nb_of(code, 0) * K.nell[0];
+  d[1] = (ti[1] - a.y) + nb_of(code, 1) * K.nell[1];
+  d[2] = DIM == 3 ? (ti[2] - a.z) + nb_of(code, 2) * K.nell[2] : 0.f;
+}
+template <int DIM>
+__device__ __forceinline__ void pack_delta_tab(const SweepK& K, const float* ti, float4 a, int code, float* d) {
   float4 sh = __ldg(K.shift + code);
   d[0] = (ti[0] - a.x) + sh.x;
   d[1] = (ti[1] - a.y) + sh.y;
@@ -256,7 +261,7 @@ __device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
     for (int j = a; j < e; j++) {
       if (j == i) continue;
       int ox = oxf != kOxKey ? oxf : S.key[j] % S.ncell[0] - cx;
-      f(j, (ox + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+      f(j, nb_code(ox, dy, dz));
     }
   });
 }
@@ -265,8 +270,9 @@ __device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
 // Eq. densum + Eq. eos over the list, every step
 // resident blocks per SM: five for the FP32 walk (48 registers), four for FP64 (which
 // would spill at five)
-template <class R, int DIM>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) k_density(BatchView<R> B) {
+// ONE: a launch over one scene, its sweep constants by value (kp)
+template <class R, int DIM, bool ONE>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) k_density(BatchView<R> B, SweepK kp) {
   int total = __ldg(B.pfx_part + B.nsc);
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     int s = find_scene(B.pfx_part, B.nsc, g);
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) k_density(BatchVi
       auto visit = [&](int j, int code) {
         R d[3];
         if constexpr (sizeof(R) == 4)
-          pack_delta<DIM>(S, ti, S.pa[j], code, d);  // positions packed by the drift
+          pack_delta_tab<DIM>(S.k, ti, S.pa[j], code, d);  // positions packed by the drift
         else
           list_delta<R, DIM>(S, ti, j, code, d);
         R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
@@ -299,11 +305,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) k_density(BatchVi
           // gathers at once, so five blocks fit on an SM, measured 3.5% faster on the 3D
           // tank); the sum keeps the list order.  The entries inside the support are copied, in list order,
           // into the in-range list the force sweep of this evaluation walks.
-          size_t n = S.n;
-          const float4* pa = S.pa;
-          const int4* L4 = (const int4*)S.nbl + i;
+          const SweepK& K = sweep_k<ONE>(kp, S.k);
+          size_t n = K.n;
+          const float4* pa = K.pa;
+          const int4* L4 = (const int4*)K.nbl + i;
           InRange ir;
-          const int cq = S.cq;
+          const int cq = K.cq;
           int4 c = cnt > 0 ? __ldg(L4) : make_int4(0, 0, 0, 0);
           for (; k < cnt; k += 4) {
             int4 cn = k + 4 < cnt ? __ldg(L4 + (size_t)((k >> 2) + 1) * n) : make_int4(0, 0, 0, 0);
@@ -317,27 +324,27 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) k_density(BatchVi
               for (int q = 0; q < 2; q++) {
                 e[q] = ec[h + q];
                 ok[q] = k + h + q < cnt;  // the last chunk may be partial
-                a[q] = pa[ok[q] ? e[q] >> 5 : i];
+                a[q] = pa[ok[q] ? nb_j(e[q]) : i];
               }
 #pragma unroll
               for (int q = 0; q < 2; q++) {
                 if (!ok[q]) continue;
                 R d[3];
-                pack_delta<DIM>(S, ti, a[q], e[q] & 31, d);
+                pack_delta_tab<DIM>(K, ti, a[q], nb_cd(e[q]), d);
                 R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
                 if (r2 < S.rc2R) {
                   ks.add(quintic_w<R>(pair_dist<R>(r2) * S.inv_h));
-                  ir.put(S.nbq, n, i, cq, e[q]);
+                  ir.put((int4*)K.nbq, n, i, cq, e[q]);
                 }
               }
             }
             c = cn;
           }
-          S.nbqc[i] = ir.finish(S.nbq, n, i, cq);
+          S.nbqc[i] = ir.finish((int4*)K.nbq, n, i, cq);
         }
         for (; k < cnt; k++) {
           int e = __ldg(S.nbl + nb_at(S.n, i, k));
-          visit(e >> 5, e & 31);
+          visit(nb_j(e), nb_cd(e));
         }
       } else {
         scan_cells<R, DIM>(S, i, visit);
@@ -438,7 +445,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
 #pragma unroll
           for (int q = 0; q < 2; q++) {
             ok[q] = k + h + q < cnt;  // the last chunk may be partial
-            int j = ok[q] ? e[q] >> 5 : i;
+            int j = ok[q] ? nb_j(e[q]) : i;
             a[q] = S.pa[j];  // loaded whatever the kind: both loads of both entries in flight
             b[q] = S.pb[j];
             fl[q] = wall || j < nf;
@@ -447,7 +454,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
           for (int q = 0; q < 2; q++) {
             if (!ok[q]) continue;
             R d[3];
-            pack_delta<DIM>(S, ti, a[q], e[q] & 31, d);
+            pack_delta<DIM>(S, ti, a[q], nb_cd(e[q]), d);
             R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
             if (r2 < S.rc2R) {
               if (!wall) ir.put(S.nbq, n, i, cq, e[q]);
@@ -468,7 +475,7 @@ __global__ void __launch_bounds__(256) k_extrap(BatchView<R> B) {
       }
       for (; k < cnt; k++) {
         int e = __ldg(S.nbl + nb_at(S.n, i, k));
-        visit(e >> 5, e & 31);
+        visit(nb_j(e), nb_cd(e));
       }
     } else {
       scan_cells<R, DIM>(S, i, visit);
@@ -769,11 +776,11 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
 #pragma unroll
             for (int u = 0; u < 4; u++) {
               if (m + u < cin) {
-                int e = ee[u], j = e >> 5;
+                int e = ee[u], j = nb_j(e);
                 float4 a = K.pa[j], b = K.pb[j];
                 float2 c = K.pv[j];
                 float d[3];
-                pack_delta<DIM>(K, ti, a, e & 31, d);
+                pack_delta<DIM>(K, ti, a, nb_cd(e), d);
                 float r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
                 force_pair_packed<DIM, TVF>(S, K, t, j, d, r2, a, b, c, acc, heat);
               }
@@ -790,7 +797,7 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
           int e = k < cnt ? __ldg(K.nbl + nb_at(K.n, i, k)) : 0;
           for (; k < cnt; k++) {
             int en = k + 1 < cnt ? __ldg(K.nbl + nb_at(K.n, i, k + 1)) : 0;
-            int j = e >> 5;
+            int j = nb_j(e);
 #if SPH_FORCE_SPECULATE
             float4 a = K.pa[j], b = K.pb[j];
                 float2 c = K.pv[j];
@@ -798,7 +805,7 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
             float4 a = K.pa[j];
 #endif
             float d[3];
-            pack_delta<DIM>(K, ti, a, e & 31, d);
+            pack_delta<DIM>(K, ti, a, nb_cd(e), d);
             float r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
             if (r2 < K.rc2) {
 #if !SPH_FORCE_SPECULATE
@@ -813,7 +820,7 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
         }
         for (; k < cnt; k++) {
           int e = __ldg(S.nbl + nb_at(S.n, i, k));
-          visit(e >> 5, e & 31);
+          visit(nb_j(e), nb_cd(e));
         }
       } else {
         scan_cells<R, DIM>(S, i, visit);

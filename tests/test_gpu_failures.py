@@ -8,6 +8,8 @@
 * The bounded retries of the union-find hooking of new bodies (Sec. 3.6, new bodies by
   connected components): a build of the library with the retry cap lowered to zero makes
   every hook give up; ``sph_step`` returns SPH_ERR_TIMEOUT and the relabel is not applied.
+* A particle count past the 26 bits of a neighbour index: ``sph_create_scene`` rejects it
+  before it reads any particle array.
 """
 import os
 import subprocess
@@ -165,3 +167,18 @@ def test_union_find_retry_cap_gives_timeout_and_skips_the_relabel():
     g.step(1)
     assert g.info()["relabelled"] > 0
     g.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_particle_count_beyond_the_list_index_is_rejected(precision):
+    """n = 2^26 + 1 with the arrays of a 256-particle scene: SPH_ERR_INVALID from the count
+    check, which comes before any array is read; 2^26 itself passes that check."""
+    import ctypes as C
+    from paper_2103_07925_gb300.sph import _Inputs, lib
+    inp = _Inputs(S.periodic_box(dim=2, n=16, bodies=0), precision)
+    inp.parts.n = (1 << 26) + 1
+    h = C.c_void_p()
+    L = lib()
+    st = L.sph_create_scene(C.byref(inp.params), C.byref(inp.parts), C.byref(inp.bodies), None, C.byref(h))
+    assert st == -1 and not h.value
+    assert b"2^26" in L.sph_last_error()
