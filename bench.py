@@ -38,6 +38,7 @@ BYTES_PER_DENSITY_TARGET = 28
 # changes
 TRAFFIC = {("k_force", 1, 0.5): 584.9e6, ("k_density", 1, 0.5): 1226.0e6,
            ("k_force", 1, 0.7): 582.3e6, ("k_density", 1, 0.7): 1327.7e6}
+FP64_SKIN_H = 0.15  # Verlet skin of the FP64 leg, in h (see the FP64 leg in main())
 FP32_LANES_PER_SM = 128  # nominal, for the context figure beside the measured peak
 
 
@@ -509,10 +510,14 @@ def main():
            "roofline": dominant,
            "roofline_" + other["kernel"]: other,
            "profile_ms": prof, "clocks": clk}
-    # plain FP64 path on the same workload
+    # plain FP64 path on the same workload, with its own skin: its sweeps walk the full
+    # lists with the distance test and its pair arithmetic is bound by the FP64 units, so
+    # short lists pay more than rare rebuilds (200 steps of the tank: 25.5 ms/step at
+    # 0.15 h, 29.7 at 0.3 h, 39.4 at 0.7 h)
     if not args.no_fp64 and args.precision == 32:
         s64 = torch.cuda.Stream()
-        g64 = Scene(sc, precision=64, stream=s64.cuda_stream, **layout)
+        layout64 = dict(layout, skin=FP64_SKIN_H * sc["params"]["h"])
+        g64 = Scene(sc, precision=64, stream=s64.cuda_stream, **layout64)
         g64.step(2)
         k64 = max(5, min(args.steps // 10, 30))
         q0 = g64.info()["pairs_total"]
@@ -525,7 +530,8 @@ def main():
         m64 = f0.elapsed_time(f1)
         q1 = g64.info()["pairs_total"]
         out["fp64"] = {"value": (q1 - q0) / (m64 / 1e3), "ms_per_step": m64 / k64, "steps": k64,
-                       "steps_per_s": k64 / (m64 / 1e3)}
+                       "steps_per_s": k64 / (m64 / 1e3), "skin_h": FP64_SKIN_H,
+                       "window": "steps 3-%d of a fresh scene" % (2 + k64)}
         g64.close()
     # FP32 against the FP64 path on the same workload and layout: every output field after
     # one step from the same initial state, body trajectories after 100 steps
@@ -584,9 +590,29 @@ def main():
         q1 = g.info()["pairs_total"]
         te = allmax(te)
         nbytes = int(sum(a.nbytes for a in st.values()))
+        # the host link alone: plain copies of the same bytes between page-locked host memory
+        # and the device, one way and then the other (the floor of the added time per step)
+        hb = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        db = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        for _ in range(2):
+            db.copy_(hb, non_blocking=True)
+            hb.copy_(db, non_blocking=True)
+        c0.record()
+        for _ in range(ke):
+            db.copy_(hb, non_blocking=True)
+        c1.record()
+        for _ in range(ke):
+            hb.copy_(db, non_blocking=True)
+        c2.record()
+        torch.cuda.synchronize()
+        h2d_ms, d2h_ms = c0.elapsed_time(c1) / ke, c1.elapsed_time(c2) / ke
+        del hb, db
         out["e2e"] = {"value": allsum(q1 - q0) / te, "unit": "pair-interactions/s",
                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": ke,
-                      "ms_per_step": 1e3 * te / ke}
+                      "ms_per_step": 1e3 * te / ke,
+                      "host_link": {"h2d_ms": h2d_ms, "d2h_ms": d2h_ms, "h2d_gbs": nbytes / h2d_ms / 1e6,
+                                    "d2h_gbs": nbytes / d2h_ms / 1e6}}
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(sc)
     g.close()

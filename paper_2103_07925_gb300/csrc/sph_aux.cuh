@@ -284,6 +284,7 @@ struct NbPol {
   int64_t cnt, off;
   int32_t* list;
   static constexpr bool kExact = true;
+  static constexpr bool kEntry = false;
   __device__ void stage(const Scene<R>& S, int j, int lane) {
     sx[lane] = S.P.px[j]; sy[lane] = S.P.py[j]; sz[lane] = S.P.pz[j];
     if (sizeof(R) == 8) { fx[lane] = (float)sx[lane]; fy[lane] = (float)sy[lane]; fz[lane] = (float)sz[lane]; }

@@ -54,6 +54,27 @@ __device__ __forceinline__ void write_pack(const Scene<R>& S, int i, R rho, R p,
 }
 
 // ---------------------------------------------------------------- neighbour search
+// a list chunk filled as a shift register: the new entry enters at w
+__device__ __forceinline__ void chunk_push(int4& b, int e) {
+  b.x = b.y;
+  b.y = b.z;
+  b.z = b.w;
+  b.w = e;
+}
+// a partly filled chunk (its last r entries at the end) moved to the front before it is stored
+__device__ __forceinline__ void chunk_align(int4& b, int r) {
+  if (r == 1) {
+    b.x = b.w;
+  } else if (r == 2) {
+    b.x = b.z;
+    b.y = b.w;
+  } else if (r == 3) {
+    b.x = b.y;
+    b.y = b.z;
+    b.z = b.w;
+  }
+}
+
 template <class R, int DIM>
 struct SearchPol {
   R *sx, *sy, *sz;     // staged candidates (see traverse)
@@ -72,6 +93,9 @@ struct SearchPol {
   // a list may hold a few pairs just beyond its radius (the pre-test's margin): every sweep
   // decides r < r_c itself, so the exact per-pair test is skipped here
   static constexpr bool kExact = false;
+  // the traversal stages each candidate's list entry relative to the group's first column
+  // (see traverse) and hands a hit's entry to put()
+  static constexpr bool kEntry = true;
   __device__ void stage(const Scene<R>& S, int j, int lane) {
     if constexpr (sizeof(R) == 4) {  // the packed position record: one 16-byte load
       float4 a = S.pa[j];
@@ -83,23 +107,23 @@ struct SearchPol {
   }
   // entries collect in a register chunk that is stored whole (16 bytes); entries past the
   // capacity are counted, not stored (the sweeps then scan the cells of that target)
-  __device__ void pair(const Scene<R>&, int, int j, R, R, R, R) {
-    int e = nb_entry(j, nb_code(cox - tx, cdy, cdz));
-    int u = cnt & 3;
-    if (u == 0) buf.x = e;
-    else if (u == 1) buf.y = e;
-    else if (u == 2) buf.z = e;
-    else buf.w = e;
+  // the chunk is a shift register: each entry enters at w and moves the others down, so a
+  // full chunk holds its four entries in order (measured 24 % faster search than writing
+  // entry cnt & 3 in place, whose four-way select every hit paid)
+  __device__ void put(int e) {
+    chunk_push(buf, e);
     cnt++;
     if ((cnt & 3) == 0 && cnt <= maxnb) list[(size_t)((cnt >> 2) - 1) * n] = buf;
   }
+  __device__ void pair(const Scene<R>&, int, int j, R, R, R, R) { put(nb_entry(j, nb_code(cox - tx, cdy, cdz))); }
   __device__ void flush() {
+    chunk_align(buf, cnt & 3);
     if ((cnt & 3) != 0 && cnt <= maxnb) list[(size_t)(cnt >> 2) * n] = buf;
   }
 };
 
-// resident blocks of 128 threads per SM the search is compiled for (register budget; six
-// measured fastest for FP32, against eight and ten)
+// resident blocks of 128 threads per SM the search is compiled for (register budget; FP32:
+// five, with four and six within 1 %, eight and ten slower)
 #ifndef SPH_SEARCH_MIN_BLOCKS
 #define SPH_SEARCH_MIN_BLOCKS 5
 #endif
@@ -216,21 +240,19 @@ struct KSum {
 };
 
 // writer of particle i's in-range list (int4 chunks, see SweepK): entries collect in a
-// register chunk that is stored whole; more than cq entries (the capacity) mark the list
-// as not kept (-1), and the force sweep then walks the full list itself
+// register chunk (a shift register, as in the search) that is stored whole; more than cq
+// entries (the capacity) mark the list as not kept (-1), and the force sweep then walks the
+// full list itself
 struct InRange {
   int4 buf;
   int m = 0;
   __device__ __forceinline__ void put(int4* nbq, size_t n, int i, int cq, int e) {
-    int u = m & 3;
-    if (u == 0) buf.x = e;
-    else if (u == 1) buf.y = e;
-    else if (u == 2) buf.z = e;
-    else buf.w = e;
+    chunk_push(buf, e);
     m++;
     if ((m & 3) == 0 && m <= cq) nbq[(size_t)((m >> 2) - 1) * n + i] = buf;
   }
   __device__ __forceinline__ int finish(int4* nbq, size_t n, int i, int cq) {
+    chunk_align(buf, m & 3);
     if ((m & 3) != 0 && m <= cq) nbq[(size_t)(m >> 2) * n + i] = buf;
     return m <= cq ? m : -1;
   }
@@ -268,11 +290,9 @@ __device__ __forceinline__ void scan_cells(const Scene<R>& S, int i, F&& f) {
 
 // ---------------------------------------------------------------- density on steps without rebuild
 // Eq. densum + Eq. eos over the list, every step
-// resident blocks per SM: five for the FP32 walk (48 registers), four for FP64 (which
-// would spill at five)
 // ONE: a launch over one scene, its sweep constants by value (kp)
 template <class R, int DIM, bool ONE>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) k_density(BatchView<R> B, SweepK kp) {
+__global__ void __launch_bounds__(256, 4) k_density(BatchView<R> B, SweepK kp) {
   int total = __ldg(B.pfx_part + B.nsc);
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     int s = find_scene(B.pfx_part, B.nsc, g);
@@ -300,10 +320,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) k_density(BatchVi
       if (cnt <= S.maxnb) {
         int k = 0;
         if constexpr (sizeof(R) == 4) {
-          // one list chunk (four entries) at a time, its position gathers two by two (two in
-          // flight and the next chunk's load while they are summed: fewer registers than four
-          // gathers at once, so five blocks fit on an SM, measured 3.5% faster on the 3D
-          // tank); the sum keeps the list order.  The entries inside the support are copied, in list order,
+          // one list chunk (four entries) at a time: the four position gathers are in flight
+          // together (a latency-bound walk), the next chunk while they are summed; the sum
+          // keeps the list order.  The entries inside the support are copied, in list order,
           // into the in-range list the force sweep of this evaluation walks.
           const SweepK& K = sweep_k<ONE>(kp, S.k);
           size_t n = K.n;
@@ -314,28 +333,23 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) k_density(BatchVi
           int4 c = cnt > 0 ? __ldg(L4) : make_int4(0, 0, 0, 0);
           for (; k < cnt; k += 4) {
             int4 cn = k + 4 < cnt ? __ldg(L4 + (size_t)((k >> 2) + 1) * n) : make_int4(0, 0, 0, 0);
-            int ec[4] = {c.x, c.y, c.z, c.w};
+            int e[4] = {c.x, c.y, c.z, c.w};
+            bool ok[4];
+            float4 a[4];
 #pragma unroll
-            for (int h = 0; h < 4; h += 2) {
-              int e[2];
-              bool ok[2];
-              float4 a[2];
+            for (int q = 0; q < 4; q++) {
+              ok[q] = k + q < cnt;  // the last chunk may be partial
+              a[q] = pa[ok[q] ? nb_j(e[q]) : i];
+            }
 #pragma unroll
-              for (int q = 0; q < 2; q++) {
-                e[q] = ec[h + q];
-                ok[q] = k + h + q < cnt;  // the last chunk may be partial
-                a[q] = pa[ok[q] ? nb_j(e[q]) : i];
-              }
-#pragma unroll
-              for (int q = 0; q < 2; q++) {
-                if (!ok[q]) continue;
-                R d[3];
-                pack_delta_tab<DIM>(K, ti, a[q], nb_cd(e[q]), d);
-                R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
-                if (r2 < S.rc2R) {
-                  ks.add(quintic_w<R>(pair_dist<R>(r2) * S.inv_h));
-                  ir.put((int4*)K.nbq, n, i, cq, e[q]);
-                }
+            for (int q = 0; q < 4; q++) {
+              if (!ok[q]) continue;
+              R d[3];
+              pack_delta_tab<DIM>(K, ti, a[q], nb_cd(e[q]), d);
+              R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
+              if (r2 < S.rc2R) {
+                ks.add(quintic_w<R>(pair_dist<R>(r2) * S.inv_h));
+                ir.put((int4*)K.nbq, n, i, cq, e[q]);
               }
             }
             c = cn;
