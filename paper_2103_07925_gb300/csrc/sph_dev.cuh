@@ -64,9 +64,6 @@ struct SweepK {
   const int4* nbq;
   const int* nbqc;
   int cq;
-  // the cell offsets -(o_x ell_x, o_y ell_y, o_z ell_z) of the 64 codes (27 of them used):
-  // the density sweep's form of the offset (a load where the other sweeps decode the code)
-  const float4* shift;
   int n;
   float ell[3];                     // cell edges (positions are relative to the cell origin)
   float nell[3];                    // -ell: the cell offset of an entry is nb_of(code) nell
@@ -128,7 +125,6 @@ struct Scene {
   int4* nbq;           // FP32 scenes: in-range entries of this evaluation (see SweepK)
   int* nbqc;
   int cq;              // capacity of the in-range lists (entries, a multiple of 4)
-  float4* shift;       // FP32 scenes: cell offsets of the entry codes (see SweepK)
   R *xr, *yr, *zr;     // positions at the last list rebuild (same frame as the bank)
   unsigned long long* disp;  // bits of the largest squared displacement since the rebuild
   int maxnb;           // list capacity per particle

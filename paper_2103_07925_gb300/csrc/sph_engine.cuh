@@ -611,19 +611,10 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
   S.maxnb = list_capacity(DIM, (S.rc + S.skin) / S.dx);
   SPH_TRY(A(&S.nbl, (size_t)S.maxnb * n));
   SPH_TRY(A(&S.nbc, (size_t)n));
-  if (sizeof(R) == 4) {  // in-range lists of each evaluation, and the cell offsets of the codes
+  if (sizeof(R) == 4) {  // in-range lists of each evaluation
     S.cq = list_capacity(DIM, S.rc / S.dx);
     SPH_TRY(A(&S.nbq, (size_t)(S.cq / 4) * n));
     SPH_TRY(A(&S.nbqc, (size_t)n));
-    SPH_TRY(A(&S.shift, 64));
-    float4 sh[64];
-    for (int c = 0; c < 64; c++) {
-      int ox = (c & 3) - 1, oy = ((c >> 2) & 3) - 1, oz = ((c >> 4) & 3) - 1;
-      // the products the other sweeps form from the code: exact (0 or +-ell)
-      sh[c] = make_float4((float)ox * -(float)S.ellR[0], (float)oy * -(float)S.ellR[1],
-                          DIM == 3 ? (float)oz * -(float)S.ellR[2] : 0.f, 0.f);
-    }
-    SPH_CU(cudaMemcpyAsync(S.shift, sh, sizeof(sh), cudaMemcpyHostToDevice, stream));
   }
   SPH_TRY(A(&S.xr, (size_t)n));
   SPH_TRY(A(&S.yr, (size_t)n));
@@ -751,7 +742,6 @@ sph_status Engine<R, DIM>::add_scene(const sph_params* p, const sph_particles_in
       S.k.nbq = S.nbq;
       S.k.nbqc = S.nbqc;
       S.k.cq = S.cq;
-      S.k.shift = S.shift;
       S.k.n = n;
       for (int d = 0; d < 3; d++) {
         S.k.ell[d] = (float)S.ellR[d];

@@ -207,22 +207,14 @@ __device__ __forceinline__ void list_delta(const Scene<R>& S, const R* ti, int j
 
 // the same offset from a packed FP32 neighbour record: the cell offset o ell of the entry's
 // code is formed exactly (o in {-1, 0, 1} from its two bits, the product one of 0, +-ell),
-// so the sum is rounded once, as above.  Two forms of the same values: decoded from the
-// code in registers (the force and extrapolation sweeps, whose several gathers per pair
-// load the L1 data pipe), or loaded from the scene's table of the offsets (the density
-// sweep, bound by issue more than by its loads)
+// so the sum is rounded once, as above.  Decoded in registers: the sweeps are bound by
+// their gathers through the L1 data pipe, which a table of the offsets loaded once per
+// entry had loaded further (measured 2-4 % slower in each sweep)
 template <int DIM>
 __device__ __forceinline__ void pack_delta(const SweepK& K, const float* ti, float4 a, int code, float* d) {
   d[0] = (ti[0] - a.x) + nb_of(code, 0) * K.nell[0];
   d[1] = (ti[1] - a.y) + nb_of(code, 1) * K.nell[1];
   d[2] = DIM == 3 ? (ti[2] - a.z) + nb_of(code, 2) * K.nell[2] : 0.f;
-}
-template <int DIM>
-__device__ __forceinline__ void pack_delta_tab(const SweepK& K, const float* ti, float4 a, int code, float* d) {
-  float4 sh = __ldg(K.shift + code);
-  d[0] = (ti[0] - a.x) + sh.x;
-  d[1] = (ti[1] - a.y) + sh.y;
-  d[2] = DIM == 3 ? (ti[2] - a.z) + sh.z : 0.f;
 }
 
 // compensated FP32 sum (Kahan): the rounding error of each addition is carried into the
@@ -307,7 +299,7 @@ __global__ void __launch_bounds__(256, 4) k_density(BatchView<R> B, SweepK kp) {
       auto visit = [&](int j, int code) {
         R d[3];
         if constexpr (sizeof(R) == 4)
-          pack_delta_tab<DIM>(S.k, ti, S.pa[j], code, d);  // positions packed by the drift
+          pack_delta<DIM>(S, ti, S.pa[j], code, d);  // positions packed by the drift
         else
           list_delta<R, DIM>(S, ti, j, code, d);
         R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
@@ -345,7 +337,7 @@ __global__ void __launch_bounds__(256, 4) k_density(BatchView<R> B, SweepK kp) {
             for (int q = 0; q < 4; q++) {
               if (!ok[q]) continue;
               R d[3];
-              pack_delta_tab<DIM>(K, ti, a[q], nb_cd(e[q]), d);
+              pack_delta<DIM>(K, ti, a[q], nb_cd(e[q]), d);
               R r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
               if (r2 < S.rc2R) {
                 ks.add(quintic_w<R>(pair_dist<R>(r2) * S.inv_h));
