@@ -253,7 +253,7 @@ class Engine {
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs1, k_force<R, DIM, false, true>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt1, k_force<R, DIM, true, true>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_density<R, DIM, true>, sweep_block, 0));
-    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_extrap<R, DIM>, sweep_block, 0));
+    SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_extrap<R, DIM, true>, sweep_block, 0));
     SPH_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, k_search<R, DIM>, 128, 0));
     // resident blocks per SM: the kernel's occupancy, capped by the requested waves
     auto waves = [&](int occ, int req) { occ = std::max(1, occ); return sms * (req > 0 ? std::min(req, occ) : occ); };
@@ -804,7 +804,7 @@ sph_status Engine<R, DIM>::evaluate_initial(int idx) {
   int gw = grid_for((int64_t)S.ngroups * 32, 128, grid_warp);
   k_search<R, DIM><<<gw, 128, 0, stream>>>(B);
   k_density<R, DIM, true><<<grid_for(n, sweep_block, grid_dens), sweep_block, 0, stream>>>(B, S.k);
-  k_extrap<R, DIM><<<grid_for(n, sweep_block, grid_extrap), sweep_block, 0, stream>>>(B);
+  k_extrap<R, DIM, true><<<grid_for(n, sweep_block, grid_extrap), sweep_block, 0, stream>>>(B, S.k);
   if (S.tvf || S.any_conc)
     k_force<R, DIM, true, true><<<grid_for(n, sweep_block, grid_tvf1), sweep_block, 0, stream>>>(B, S.k);
   else
@@ -894,7 +894,8 @@ sph_status Engine<R, DIM>::launch_step(cudaEvent_t* ev) {
   if (ns == 1) k_density<R, DIM, true><<<gsd, sweep_block, 0, stream>>>(B, hs[act[0]].k);
   else k_density<R, DIM, false><<<gsd, sweep_block, 0, stream>>>(B, SweepK{});
   rec();
-  k_extrap<R, DIM><<<gse, sweep_block, 0, stream>>>(B);
+  if (ns == 1) k_extrap<R, DIM, true><<<gse, sweep_block, 0, stream>>>(B, hs[act[0]].k);
+  else k_extrap<R, DIM, false><<<gse, sweep_block, 0, stream>>>(B, SweepK{});
   rec();
   if (ns == 1) {  // one scene: its sweep constants by value
     const SweepK& k1 = hs[act[0]].k;

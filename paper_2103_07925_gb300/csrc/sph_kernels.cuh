@@ -936,16 +936,21 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
           // relative 1e-4 on r^2)
           R qy = pol.tp[1] - shy, qz = pol.tp[2] - shz;
           R rc2m = rc2 * R(1.0001);
-          for (int k0 = 0; k0 < cnt; k0 += 4) {
+          // eight at a time (the padded entries fail), each hit bit at a fixed position of
+          // a byte that is then shifted into place (9 % faster search than four at a time,
+          // each bit at its own variable shift)
+          for (int k0 = 0; k0 < cnt; k0 += 8) {
+            unsigned m8 = 0u;
 #pragma unroll
-            for (int k = k0; k < k0 + 4; k++) {
-              float4 c = pol.s4[k];  // one broadcast load per candidate
+            for (int q = 0; q < 8; q++) {
+              float4 c = pol.s4[k0 + q];  // one broadcast load per candidate
               R dx = pol.tp[0] - c.x;
               R dy2 = qy - c.y;
               R dz2 = DIM == 3 ? qz - c.z : R(0);
               R r2 = dist2<R, DIM>(dx, dy2, dz2);
-              if (r2 < rc2m) mask |= 1u << k;
+              if (r2 < rc2m) m8 |= 1u << q;
             }
+            mask |= m8 << k0;
           }
         }
         unsigned self = (unsigned)(pol.idx - cb);  // a target is not its own neighbour
