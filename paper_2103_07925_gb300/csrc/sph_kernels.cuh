@@ -916,7 +916,7 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
       __syncwarp();
       unsigned mask = 0u;
       if (pol.active) {
-        // the candidates four at a time over the padded batch
+        // the candidates in groups over the padded batch (FP64 scenes four, FP32 eight)
         if constexpr (sizeof(R) == 8) {
           // FP64 scenes: an FP32 test with a margin keeps a superset of the pairs
           float shf[3] = {(float)shx, (float)shy, (float)shz};
