@@ -191,6 +191,24 @@ static sph_status footprint_of(const sph_job_desc* job, int prec, size_t* bytes)
   if (!job || !job->params || !job->particles) { set_error("incomplete job"); return SPH_ERR_INVALID; }
   const sph_params* p = job->params;
   if (p->dim != 2 && p->dim != 3) { set_error("dim must be 2 or 3"); return SPH_ERR_INVALID; }
+  if (!(p->dx > 0.0) || !(p->h > 0.0) || !(p->kernel_support > 0.0) || !std::isfinite(p->dx) ||
+      !std::isfinite(p->h * p->kernel_support)) {
+    set_error("dx, h and kernel_support must be positive and finite");
+    return SPH_ERR_INVALID;
+  }
+  if (job->particles->n < 1 || job->particles->n > (1LL << 26)) {
+    set_error("particle count must be in [1, 2^26]");
+    return SPH_ERR_INVALID;
+  }
+  if (!job->particles->material || !p->materials || p->n_materials < 1) {
+    set_error("materials and particle materials are required");
+    return SPH_ERR_INVALID;
+  }
+  for (int64_t i = 0; i < job->particles->n; i++)
+    if (job->particles->material[i] < 0 || job->particles->material[i] >= p->n_materials) {
+      set_error("particle %lld: material %d out of range", (long long)i, job->particles->material[i]);
+      return SPH_ERR_INVALID;
+    }
   double rc = p->kernel_support * p->h;
   int64_t nc = 1;
   for (int d = 0; d < p->dim; d++) {
@@ -208,7 +226,9 @@ static sph_status footprint_of(const sph_job_desc* job, int prec, size_t* bytes)
   if (trans) nr = n;
   EngineIface* e = make_engine(prec, p->dim);
   if (!e) { set_error("out of host memory"); return SPH_ERR_OOM; }
-  *bytes = e->footprint(n, nc, kcap < 1 ? 1 : kcap, nr < 1 ? 1 : nr, trans, p->p_background > 0.0);
+  double skin = p->skin > 0.0 ? p->skin : 0.0;
+  *bytes = e->footprint(n, nc, kcap < 1 ? 1 : kcap, nr < 1 ? 1 : nr, trans, p->p_background > 0.0, rc / p->dx,
+                        (rc + skin) / p->dx);
   delete e;
   return SPH_OK;
 }

@@ -398,11 +398,15 @@ class Engine {
     return SPH_OK;
   }
 
-  static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans, bool tvf) {
-    // FP32: the packed records and the in-range lists of each evaluation (capacity at r_c)
+  // rc_dx, rl_dx: r_c and r_c + skin in units of dx (the capacities of the in-range and the
+  // neighbour lists, as add_scene allocates them)
+  static size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans, bool tvf,
+                          double rc_dx, double rl_dx) {
+    // the neighbour list and its count; FP32: the packed records and the in-range lists of
+    // each evaluation (capacity at r_c)
     size_t per = 2 * (13 * sizeof(R) + 4 * sizeof(int)) + 9 * sizeof(R) + 8 * sizeof(int) + 8 * sizeof(double) +
-                 (DIM == 3 ? 192 : 64) * sizeof(int) +
-                 (sizeof(R) == 4 ? 2 * sizeof(float4) + sizeof(float2) + (size_t)(list_capacity(DIM, 3.0) + 1) * sizeof(int) : 0);
+                 (size_t)(list_capacity(DIM, rl_dx) + 1) * sizeof(int) +
+                 (sizeof(R) == 4 ? 2 * sizeof(float4) + sizeof(float2) + (size_t)(list_capacity(DIM, rc_dx) + 1) * sizeof(int) : 0);
     size_t cells = (size_t)(NCLS * ncells + 1) * 2 * sizeof(int) + (size_t)ncells * 2 * sizeof(int) +
                    (size_t)(NCLS * ncells / 1024 + 2) * sizeof(int);
     size_t bodies = (size_t)kcap * (69 * sizeof(double) + 3 * sizeof(int));

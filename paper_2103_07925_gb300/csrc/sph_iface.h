@@ -39,7 +39,8 @@ struct EngineIface {
   virtual int64_t steps_taken() = 0;
   virtual int kernels_per_step() = 0;
   virtual sph_status pairs_total(int64_t* out) = 0;  // force-sweep pairs of all resident scenes
-  virtual size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans, bool tvf) = 0;
+  virtual size_t footprint(int64_t n, int64_t ncells, int64_t kcap, int64_t nrigid, bool trans, bool tvf,
+                           double rc_dx, double rl_dx) = 0;
   virtual sph_status set_launch(const int32_t* cfg, int32_t n) = 0;
   virtual void get_launch(int32_t* cfg) = 0;
   virtual sph_status time_steps(int32_t n, double* ms) = 0;

@@ -91,8 +91,9 @@ struct EngineImpl final : EngineIface {
     }
     return SPH_OK;
   }
-  size_t footprint(int64_t n, int64_t nc, int64_t kc, int64_t nr, bool trans, bool tvf) override {
-    return Engine<R, DIM>::footprint(n, nc, kc, nr, trans, tvf);
+  size_t footprint(int64_t n, int64_t nc, int64_t kc, int64_t nr, bool trans, bool tvf, double rc_dx,
+                   double rl_dx) override {
+    return Engine<R, DIM>::footprint(n, nc, kc, nr, trans, tvf, rc_dx, rl_dx);
   }
 };
 

@@ -111,6 +111,27 @@ def test_admission_by_memory_footprint():
     B.close()
 
 
+@pytest.mark.parametrize("precision", [32, 64])
+def test_footprint_bounds_the_memory_a_job_holds(precision):
+    """The admission estimate is at least what the admitted job allocates on the device, for
+    a 3D scene at a skin of 0.7 h (the neighbour list grows with the skin; there the
+    estimate is within 1.5 times the allocation) and a 2D scene with bodies that
+    solidifies (relabel scratch and spare bodies)."""
+    from paper_2103_07925_gb300.sph import Batch
+    from tests.test_gpu_relabel import _cycle
+    s3 = S.tank3d_spheres(dx=0.05, n_spheres=3, r_range=(0.1, 0.15), size=(1.0, 1.0, 1.5), fill=0.8)
+    s3["params"]["skin"] = 0.7 * s3["params"]["h"]
+    for sc in (s3, _cycle()):
+        est = Batch.footprint(sc, precision=precision)
+        B = Batch(capacity=4, precision=precision)
+        assert B.admit(sc, 1) is not None
+        used = B.info()["bytes"]
+        B.close()
+        assert used <= est, (used, est)
+        if sc is s3:
+            assert est <= 1.5 * used, (used, est)
+
+
 def test_batch_fp32_against_oracle_on_sampled_scenes():
     """FP32 in the mix against the FP64 oracle after one step: every output field within the
     per-step tolerance (pres and vext without the edge-only boundary particles, whose weighted

@@ -69,3 +69,44 @@ def test_binding_tables_match_the_header():
     status = {int(v): "SPH_" + k for k, v in re.findall(r"SPH_(OK|ERR_[A-Z]+) = (-?\d+)", txt)}
     assert status == sph.STATUS
     assert int(re.search(r"#define SPH_PROFILE_STAGES (\d+)", txt).group(1)) == sph.PROFILE_STAGES
+
+
+def test_job_footprint_follows_the_list_capacity_and_rejects_bad_jobs():
+    """The footprint estimate is host arithmetic (no device call): it grows with the Verlet
+    skin by the neighbour-list capacity, ceil(1.3 * 4/3 pi ((r_c + skin) / dx)^3 / 32) * 32
+    entries of 4 bytes per particle in 3D, and it refuses a job whose particle material is
+    out of range or whose dx is not positive."""
+    import math
+    from paper_2103_07925_gb300 import scenes
+    sph._lib = None
+    sc = scenes.periodic_box(dim=3, n=10, dx=0.1, bodies=0)
+    h, dx = sc["params"]["h"], sc["params"]["dx"]
+    rc = sc["params"]["kernel_support"] * h
+
+    def cap(r):
+        return max(32, math.ceil(1.3 * 4.0 / 3.0 * math.pi * r ** 3 / 32.0) * 32)
+
+    fp = {}
+    for skin in (0.0, 0.5, 1.0):
+        sc["params"]["skin"] = skin * h
+        fp[skin] = sph.Batch.footprint(sc, precision=32)
+    n = len(sc["particles"]["mass"])
+    for s0, s1 in ((0.0, 0.5), (0.5, 1.0)):
+        grow = cap((rc + s1 * h) / dx) - cap((rc + s0 * h) / dx)
+        assert fp[s1] - fp[s0] == 4 * grow * n, (s0, s1)
+    bad = dict(sc, particles=dict(sc["particles"]))
+    bad["particles"]["material"] = sc["particles"]["material"].copy()
+    bad["particles"]["material"][3] = len(sc["materials"])
+    try:
+        sph.Batch.footprint(bad, precision=32)
+    except sph.SphError as e:
+        assert "out of range" in str(e)
+    else:
+        raise AssertionError("expected SphError")
+    bad = dict(sc, params=dict(sc["params"], dx=0.0))
+    try:
+        sph.Batch.footprint(bad, precision=32)
+    except sph.SphError as e:
+        assert "positive" in str(e)
+    else:
+        raise AssertionError("expected SphError")
