@@ -716,13 +716,6 @@ __device__ __forceinline__ void force_pair_packed(const Scene<float>& S, const S
 }
 
 // resident blocks per SM the force sweep is compiled for (register budget)
-// 1: the velocity and material records of a list entry are loaded with its position
-// (speculatively, before the distance test); 0: only for pairs inside the support (about
-// two thirds of the entries at a skin of 0.3 h), which measured faster once every warp's
-// targets are of one kind
-#ifndef SPH_FORCE_SPECULATE
-#define SPH_FORCE_SPECULATE 0
-#endif
 #ifndef SPH_FORCE_MIN_BLOCKS
 #define SPH_FORCE_MIN_BLOCKS 4
 #endif
@@ -832,26 +825,20 @@ __global__ void __launch_bounds__(256, TVF ? 3 : SPH_FORCE_MIN_BLOCKS) k_force(B
       } else if (cnt <= S.maxnb) {
         int k = 0;
         if constexpr (sizeof(R) == 4) {
-          // software pipeline: the next list entry is loaded while this pair is evaluated,
-          // and the three records of a neighbour are loaded together (one latency per entry)
+          // software pipeline: the next list entry is loaded while this pair is evaluated; the
+          // velocity and material records only for pairs inside the support (measured faster
+          // than loading them with the position, before the distance test)
           int e = k < cnt ? __ldg(K.nbl + nb_at(K.n, i, k)) : 0;
           for (; k < cnt; k++) {
             int en = k + 1 < cnt ? __ldg(K.nbl + nb_at(K.n, i, k + 1)) : 0;
             int j = nb_j(e);
-#if SPH_FORCE_SPECULATE
-            float4 a = K.pa[j], b = K.pb[j];
-                float2 c = K.pv[j];
-#else
             float4 a = K.pa[j];
-#endif
             float d[3];
             pack_delta<DIM>(K, ti, a, nb_cd(e), d);
             float r2 = pair_r2<R, DIM>(d[0], d[1], d[2]);
             if (r2 < K.rc2) {
-#if !SPH_FORCE_SPECULATE
               float4 b = K.pb[j];
-            float2 c = K.pv[j];
-#endif
+              float2 c = K.pv[j];
               force_pair_packed<DIM, TVF>(S, K, t, j, d, r2, a, b, c, acc, heat);
               npairs++;
             }
