@@ -869,8 +869,9 @@ __device__ __forceinline__ void for_each_run(const Scene<R>& S, int cx0, int ncx
 // without it), and for FP64 scenes FP32 copies fx/fy/fz of the staged positions and tf of
 // the target (rc2f: the FP32 pre-test radius, squared, with the margin of the rounding of
 // those copies).  With kEntry (lists of the search), sox holds each staged candidate's
-// list entry for a target of the group's first column, and every pre-test hit goes to
-// put(entry - tx) instead of pair().  Candidates come in the order of for_each_run.
+// list entry for a target of the group's first column and scol its column offset, and
+// every pre-test hit in a column next to its target's goes to put(entry - tx) instead of
+// pair().  Candidates come in the order of for_each_run.
 template <class R, int DIM, class Pol>
 __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>& G, Pol& pol, int lane, R rc2,
                                          float rc2f) {
@@ -901,11 +902,13 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
             ox = S.key[j] % S.ncell[0] - G.cx0;
           }
         }
-        if constexpr (Pol::kEntry)  // the list entry for a target of column cx0 (tx = 0): a
+        if constexpr (Pol::kEntry) {  // the list entry for a target of column cx0 (tx = 0): a
           // target of column cx0 + tx subtracts tx (the x field ox + 1 - tx lands in 0..2)
           pol.sox[lane] = (int)(((unsigned)j << 6) + (unsigned)(((dz + 1) << 4) + ((dy + 1) << 2) + (ox + 1)));
-        else
+          pol.scol[lane] = ox;
+        } else {
           pol.sox[lane] = ox;
+        }
         if constexpr (sizeof(R) == 4)
           pol.s4[lane] = make_float4(pol.sx[lane] + (R)ox * S.ellR[0], pol.sy[lane], pol.sz[lane], 0.f);
       } else if (sizeof(R) == 4) {
@@ -960,6 +963,11 @@ __device__ __forceinline__ void traverse(const Scene<R>& S, const Group<R, DIM>&
         int k = __ffs(mask) - 1;
         mask &= mask - 1;
         if constexpr (Pol::kEntry) {
+          // a candidate two columns from its target is farther than the cell edge, itself at
+          // least r_c + skin, and passes only through the pre-test's margin (a cell edge
+          // within about 1e-4 of r_c + skin); its x field would fall outside 0..2 and borrow
+          // into the other fields and the index, so it is left out of the list
+          if ((unsigned)(pol.scol[k] - pol.tx + 1) > 2u) continue;
           pol.put((int)((unsigned)pol.sox[k] - (unsigned)pol.tx));
           continue;
         }

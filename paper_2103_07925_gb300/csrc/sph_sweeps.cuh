@@ -81,6 +81,7 @@ struct SearchPol {
   R *sx, *sy, *sz;     // staged candidates (see traverse)
   float4* s4;
   int* sox;
+  int* scol;           // column offset of each staged candidate (see traverse)
   float *fx, *fy, *fz;    // FP32 copies of the staged positions (FP64 scenes)
   float tf[3];
   unsigned cmask;      // candidate kinds: a wall particle only ever reads its fluid neighbours
@@ -139,11 +140,13 @@ __global__ void __launch_bounds__(128, sizeof(R) == 8 ? SPH_SEARCH_MIN_BLOCKS_64
   __shared__ float smf[sizeof(R) == 8 ? 4 : 1][3][32];
   __shared__ float4 sm4[sizeof(R) == 4 ? 4 : 1][32];
   __shared__ int smo[4][32];
+  __shared__ int smc[4][32];
   int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   SearchPol<R, DIM> pol;
   pol.sx = sm[wib][0]; pol.sy = sm[wib][1]; pol.sz = sm[wib][2];
   pol.s4 = sm4[sizeof(R) == 4 ? wib : 0];
   pol.sox = smo[wib];
+  pol.scol = smc[wib];
   int wf = sizeof(R) == 8 ? wib : 0;
   pol.fx = smf[wf][0]; pol.fy = smf[wf][1]; pol.fz = smf[wf][2];
   int total = __ldg(B.pfx_grp + B.nsc);
