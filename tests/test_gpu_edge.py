@@ -107,3 +107,52 @@ def test_dense_clump_beyond_the_in_range_capacity():
         bad = {k: e for k, e in errs.items() if not e < tol}
         assert not bad, (precision, bad)
         g.close()
+
+
+def _two_columns_scene():
+    """3D periodic box of 8 x 8 x 8 cells whose edge exceeds r_c + skin by a relative 1e-6,
+    holding two fluid particles: one at the top corner of cell (1, 0, 0), the first particle
+    of the sorted order, and one at the bottom corner of cell (3, 1, 1), a cell edge plus
+    2e-5 of it away along x.  With two cells per search group the second is the second
+    column of its group and the first sits in the column left of the group: two columns
+    apart, farther than r_c + skin, yet inside the search pre-test's margin."""
+    dx = 0.1
+    h = dx
+    skin = dx
+    rl = 3.0 * h + skin
+    L = 8 * rl * (1.0 + 1e-6)
+    ell = L / 8
+    eps, eta = 1e-5 * ell, 2.5e-6 * ell
+    b = S._Builder(3)
+    mats = [S.material(S.FLUID, 1.0, c=10.0, eta=0.01)]
+    b.add(np.array([[2 * ell - eps, ell - eta, ell - eta]]), 0, dx ** 3, 1.0, 300.0)
+    b.add(np.array([[3 * ell + eps, ell + eta, ell + eta]]), 0, dx ** 3, 1.0, 300.0)
+    p = S.default_params(3, dx, [0.0] * 3, [L] * 3, periodic=[1, 1, 1], dt_mode=0, dt_fixed=1e-5,
+                         skin=skin, key_order=1, cells_per_group=2)
+    return b.finish(p, mats)
+
+
+def test_search_hit_two_columns_from_its_target():
+    """The pair of _two_columns_scene passes the search's pre-test through its margin.  Its
+    list entry would carry a column offset of -2, outside the two bits of the entry's x
+    field: the field would borrow from the index, which for the first sorted particle
+    wraps past the end of the arrays.  The search leaves such hits out; both precisions
+    step and match the oracle (two isolated particles: no neighbour inside r_c)."""
+    from oracle.oracle import OracleScene
+    from paper_2103_07925_gb300.sph import Scene
+    sc = _two_columns_scene()
+    x = sc["particles"]["pos"]
+    r = np.linalg.norm(x[1] - x[0])
+    rl = sc["params"]["kernel_support"] * sc["params"]["h"] + sc["params"]["skin"]
+    assert rl < r < rl * (1.0 + 5e-5)
+    o = OracleScene(sc)
+    assert np.array_equal(o.get("cell"), [1, 3 + 8 + 64])
+    o.step(1)
+    for precision, tol in ((64, 1e-12), (32, 1e-5)):
+        g = Scene(sc, precision=precision)
+        g.step(1)
+        errs = compare_fields(g, o, fields=["pos", "vel", "acc", "rho", "pres"], ints=["mat", "cell"],
+                              scales=field_scales(sc))
+        bad = {k: e for k, e in errs.items() if not e < tol}
+        assert not bad, (precision, bad)
+        g.close()
