@@ -151,6 +151,31 @@ def _arr(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+def _rows(name, a, n, dtype, cols=None):
+    """``a`` as a C-contiguous array of ``dtype`` with n rows (and ``cols`` columns; a 2D
+    vector field of n x 2 is padded with a zero third column), the layout the C ABI reads:
+    raises ValueError for any other shape, so that the library never reads past a buffer."""
+    a = np.asarray(a)
+    if cols is not None and a.ndim == 2 and a.shape == (n, 2) and cols == 3:
+        a = np.concatenate([a, np.zeros((n, 1), dtype=a.dtype)], axis=1)
+    want = (n,) if cols is None else (n, cols)
+    if a.shape != want:
+        raise ValueError("%s: shape %s, expected %s" % (name, a.shape, want))
+    return _arr(a, dtype)
+
+
+def _out_field(name, a, n):
+    """Checks a caller-supplied output array of field ``name`` for n particles: the dtype,
+    shape and contiguity the library writes (it writes whole rows, unchecked)."""
+    dtype = np.int32 if name in _INT else np.float64
+    want = (n, 3) if name in _VEC else (n,)
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or a.shape != want or not a.flags["C_CONTIGUOUS"] \
+            or not a.flags["WRITEABLE"]:
+        raise ValueError("out[%r]: need a writeable C-contiguous %s array of shape %s" % (name, np.dtype(dtype).name,
+                                                                                      want))
+    return a
+
+
 class _Inputs:
     """C structures built from a scene dictionary; keeps the arrays alive."""
 
@@ -187,13 +212,14 @@ class _Inputs:
         P.materials = C.cast(self.mats, C.POINTER(Material))
         self.params = P
         pt = scene["particles"]
-        self.keep = {k: _arr(pt[k], np.float64) for k in
-                     ("pos", "vel", "mass", "density", "temperature", "wall_velocity", "wall_temperature")}
+        n = len(pt["mass"])
+        self.keep = {k: _rows(k, pt[k], n, np.float64, 3) for k in ("pos", "vel", "wall_velocity")}
+        self.keep.update({k: _rows(k, pt[k], n, np.float64) for k in
+                          ("mass", "density", "temperature", "wall_temperature")})
         if "concentration" in pt:
-            self.keep["concentration"] = _arr(pt["concentration"], np.float64)
-        self.keep["material"] = _arr(pt["material"], np.int32)
-        self.keep["body"] = _arr(pt["body"], np.int32)
-        n = len(self.keep["mass"])
+            self.keep["concentration"] = _rows("concentration", pt["concentration"], n, np.float64)
+        self.keep["material"] = _rows("material", pt["material"], n, np.int32)
+        self.keep["body"] = _rows("body", pt["body"], n, np.int32)
         self.n = n
         PI = ParticlesIn()
         PI.n = n
@@ -201,9 +227,11 @@ class _Inputs:
             setattr(PI, k, self.keep[k].ctypes.data)
         self.parts = PI
         bd = scene["bodies"]
-        self.bkeep = {k: _arr(bd[k], np.float64).reshape(-1) for k in ("quat", "vel", "omega")}
+        K = len(bd["quat"])
+        self.bkeep = {k: _rows("bodies." + k, bd[k], K, np.float64, c).reshape(-1)
+                      for k, c in (("quat", 4), ("vel", 3), ("omega", 3))}
         BI = BodiesIn()
-        BI.k = len(bd["quat"])
+        BI.k = K
         for k in self.bkeep:
             setattr(BI, k, self.bkeep[k].ctypes.data)
         self.bodies = BI
@@ -238,7 +266,7 @@ class Scene:
     def read(self, *names, original_order=True, out=None):
         """Fields as numpy arrays (input order by default); ``out`` may supply
         preallocated (e.g. pinned) arrays keyed by field name."""
-        out = dict(out) if out else {}
+        out = {nm: _out_field(nm, a, self.n) for nm, a in (out or {}).items()}
         for nm in names:
             if nm not in out:
                 out[nm] = _alloc_field(nm, self.n)
@@ -257,7 +285,7 @@ class Scene:
         keep = []
         for nm, a in (("pos", pos), ("vel", vel), ("temp", temp)):
             if a is not None:
-                a = _arr(a, np.float64)
+                a = _rows(nm, a, self.n, np.float64, None if nm == "temp" else 3)
                 keep.append(a)
                 src[FIELDS[nm]] = a.ctypes.data
                 mask |= 1 << FIELDS[nm]

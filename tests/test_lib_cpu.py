@@ -110,3 +110,40 @@ def test_job_footprint_follows_the_list_capacity_and_rejects_bad_jobs():
         assert "positive" in str(e)
     else:
         raise AssertionError("expected SphError")
+
+
+def test_binding_checks_array_shapes_before_the_library_sees_them():
+    """The library reads and writes whole rows of the arrays it is given, unchecked: the
+    binding refuses inputs and caller-supplied outputs of any other shape, dtype or layout
+    (and pads an n x 2 vector field of a 2D caller with zeros)."""
+    import numpy as np
+    import pytest
+    from paper_2103_07925_gb300 import scenes
+    n = 5
+    a = sph._rows("pos", np.ones((n, 2)), n, np.float64, 3)
+    assert a.shape == (n, 3) and a.flags["C_CONTIGUOUS"] and np.all(a[:, 2] == 0.0)
+    for bad in (np.ones((n, 4)), np.ones((n + 1, 3)), np.ones(3 * n)):
+        with pytest.raises(ValueError):
+            sph._rows("pos", bad, n, np.float64, 3)
+    with pytest.raises(ValueError):
+        sph._rows("mass", np.ones(n - 1), n, np.float64)
+    ok = np.empty((n, 3))
+    assert sph._out_field("pos", ok, n) is ok
+    for nm, bad in (("pos", np.empty((n, 3), dtype=np.float32)), ("pos", np.empty((n, 2))),
+                    ("pos", np.empty((3, n)).T), ("rho", np.empty((n, 3))), ("mat", np.empty(n)),
+                    ("rho", [0.0] * n)):
+        with pytest.raises(ValueError):
+            sph._out_field(nm, bad, n)
+    ro = np.empty(n)
+    ro.setflags(write=False)
+    with pytest.raises(ValueError):
+        sph._out_field("rho", ro, n)
+    sc = scenes.periodic_box(dim=3, n=6, dx=0.1, bodies=1, body_radius=0.15)
+    sph._Inputs(sc, 32)  # a well-formed scene passes
+    sc["particles"]["mass"] = sc["particles"]["mass"][:-1]
+    with pytest.raises(ValueError):
+        sph._Inputs(sc, 32)
+    sc = scenes.periodic_box(dim=3, n=6, dx=0.1, bodies=1, body_radius=0.15)
+    sc["bodies"]["quat"] = np.asarray(sc["bodies"]["quat"])[:, :3]
+    with pytest.raises(ValueError):
+        sph._Inputs(sc, 32)
